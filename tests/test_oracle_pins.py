@@ -1,0 +1,336 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by the mathematics (CPU only).
+
+Each test names what it pins; together they are chosen so that a plausible
+mistake (a dropped factor, a wrong sign or index, a swapped VIP, a wrong weight)
+fails at least one of them -- test_planted_mistakes_are_caught checks that for a
+set of planted mistakes.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spl
+
+import workloads as w
+from oracle import vip_oracle as vo
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3: weight functions
+# ---------------------------------------------------------------------------
+
+def test_cubic_spline_values_and_smoothness():
+    f = vo.weight_cubic_spline
+    assert f(0.0) == pytest.approx(2.0 / 3.0, abs=1e-15)
+    assert f(0.5) == pytest.approx(1.0 / 6.0, abs=1e-15)
+    assert f(1.0) == 0.0 and f(1.5) == 0.0
+    # both branches meet with equal first and second derivatives at 1/2
+    e = 1e-6
+    d_left = (f(0.5) - f(0.5 - e)) / e
+    d_right = (f(0.5 + e) - f(0.5)) / e
+    assert d_left == pytest.approx(-1.0, abs=1e-5) and d_right == pytest.approx(-1.0, abs=1e-5)
+    # vanishes with zero slope at the edge of the support
+    assert (f(1.0 - e) - f(1.0)) / e == pytest.approx(0.0, abs=1e-5)
+    r = np.linspace(0, 1, 101)
+    assert np.all(np.diff(f(r)) <= 0)
+
+
+def test_paper_weight_values():
+    f = vo.weight_paper
+    assert f(0.0) == 1.0
+    assert f(1.0) == 0.0 and f(2.0) == 0.0
+    r = np.linspace(0, 0.999, 200)
+    assert np.all(np.diff(f(r)) <= 1e-15) and f(0.999) < 1e-6
+    # (1 - r^((1-r)^2))^4 at r = 1/2: (1 - 0.5**0.25)^4
+    assert f(0.5) == pytest.approx((1 - 0.5 ** 0.25) ** 4, rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3: neighbourhoods against brute force
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_neighbours_brute_force(periodic):
+    rng = np.random.default_rng(3)
+    L = 2.0
+    x, y = rng.uniform(0, L, 300), rng.uniform(0, L, 300)
+    qx, qy = rng.uniform(-0.2, L + 0.2, 80), rng.uniform(-0.2, L + 0.2, 80)
+    rho = rng.uniform(0.15, 0.4, 80)
+    Lp = L if periodic else 0.0
+    ptr, idx = vo.neighbours(qx, qy, rho, x, y, Lp, Lp)
+    for p in range(80):
+        dx = x - qx[p]
+        dy = y - qy[p]
+        if periodic:
+            dx = dx - L * np.round(dx / L)
+            dy = dy - L * np.round(dy / L)
+        ref = np.nonzero(dx * dx + dy * dy < rho[p] ** 2)[0]
+        assert np.array_equal(idx[ptr[p]:ptr[p + 1]], ref)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3, Eq. (fmlsrk:2): MLS derivative weights
+# ---------------------------------------------------------------------------
+
+def scattered(seed=5, n=14):
+    rng = np.random.default_rng(seed)
+    h = 1.0 / (n - 1)
+    j, i = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    x = (i * h + rng.uniform(-0.3, 0.3, i.shape) * h).ravel()
+    y = (j * h + rng.uniform(-0.3, 0.3, i.shape) * h).ravel()
+    qx = rng.uniform(0.2, 0.8, 60)
+    qy = rng.uniform(0.2, 0.8, 60)
+    rho = 2.2 * h * rng.uniform(1.0, 1.5, 60)
+    return x, y, qx, qy, rho
+
+
+def monomials(x, y):
+    """(value, {derivative: value}) of the six quadratic monomials."""
+    one = np.ones_like(x)
+    return [
+        (one, {(1, 0): 0 * x, (0, 1): 0 * x, (2, 0): 0 * x, (1, 1): 0 * x, (0, 2): 0 * x}),
+        (x, {(1, 0): one, (0, 1): 0 * x, (2, 0): 0 * x, (1, 1): 0 * x, (0, 2): 0 * x}),
+        (y, {(1, 0): 0 * x, (0, 1): one, (2, 0): 0 * x, (1, 1): 0 * x, (0, 2): 0 * x}),
+        (x * x, {(1, 0): 2 * x, (0, 1): 0 * x, (2, 0): 2 * one, (1, 1): 0 * x, (0, 2): 0 * x}),
+        (x * y, {(1, 0): y, (0, 1): x, (2, 0): 0 * x, (1, 1): one, (0, 2): 0 * x}),
+        (y * y, {(1, 0): 0 * x, (0, 1): 2 * y, (2, 0): 0 * x, (1, 1): 0 * x, (0, 2): 2 * one}),
+    ]
+
+
+@pytest.mark.parametrize("weight", ["cubic_spline", "paper"])
+def test_mls_reproduces_quadratics(weight):
+    """Sum_i q(x_i) Psi^[a,b]_i(xbar) = d^(a,b) q(xbar) for every quadratic q (1e-12)."""
+    x, y, qx, qy, rho = scattered()
+    ptr, idx = vo.neighbours(qx, qy, rho, x, y)
+    W = vo.mls_weights(qx, qy, rho, ptr, idx, x, y, weight=weight)
+    rows = np.repeat(np.arange(qx.size), np.diff(ptr))
+    # the printed weight is flat near |y| = 1, so its moment matrices are worse
+    # conditioned and rounding grows by about a decade
+    tol = 1e-12 if weight == "cubic_spline" else 1e-11
+    for (qn, _), (qq, dq) in zip(monomials(x, y), monomials(qx, qy)):
+        for d in vo.DERIVS:
+            A = sp.csr_matrix((W[d], (rows, idx)), shape=(qx.size, x.size))
+            exact = qq if d == (0, 0) else dq[d]
+            scale = np.abs(A) @ np.abs(qn) + 1.0
+            assert np.max(np.abs(A @ qn - exact) / scale) <= tol, d
+
+
+def test_mls_matches_weighted_least_squares_by_svd():
+    """The weights equal the pseudo-inverse of the sqrt(Phi)-weighted Vandermonde matrix
+    in unscaled coordinates (numpy.linalg.lstsq), times the derivative factors."""
+    x, y, qx, qy, rho = scattered(seed=9)
+    ptr, idx = vo.neighbours(qx, qy, rho, x, y)
+    W = vo.mls_weights(qx, qy, rho, ptr, idx, x, y)
+    for p in range(0, qx.size, 7):
+        nb = idx[ptr[p]:ptr[p + 1]]
+        dx, dy = x[nb] - qx[p], y[nb] - qy[p]
+        phi = vo.weight_cubic_spline(np.hypot(dx, dy) / rho[p])
+        V = np.stack([np.ones_like(dx), dx, dy, dx * dx, dx * dy, dy * dy], 1)
+        sw = np.sqrt(phi)
+        # column j of the solution = coefficients of the fit to the unit vector e_j
+        C, *_ = np.linalg.lstsq(sw[:, None] * V, np.diag(sw), rcond=None)
+        factor = {(0, 0): 1, (1, 0): 1, (0, 1): 1, (2, 0): 2, (1, 1): 1, (0, 2): 2}
+        for k, d in enumerate(vo.DERIVS):
+            got = W[d][ptr[p]:ptr[p + 1]]
+            ref = factor[d] * C[k]
+            assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref)), (p, d)
+
+
+def test_singular_stencil_is_reported():
+    x = np.array([0.0, 1.0, 2.0, 3.0, 4.0, 5.0, 6.0])  # collinear: no quadratic fit in y
+    y = np.zeros_like(x)
+    ptr, idx = vo.neighbours([3.0], [0.0], [10.0], x, y)
+    with pytest.raises(vo.SingularStencil):
+        vo.mls_weights(np.array([3.0]), np.array([0.0]), np.array([10.0]), ptr, idx, x, y)
+
+
+# ---------------------------------------------------------------------------
+# Eq. (vip:1), Sec. 4.1: operators
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def cavity_ops():
+    ns = w.cavity(17, Re=100.0)
+    return ns, vo.Operators(ns)
+
+
+@pytest.fixture(scope="module")
+def channel_ops():
+    ns = w.channel_body(1 / 8, ("circle", 0.5), Re=100.0, xlim=(-2.5, 4), ylim=(-2, 2))
+    return ns, vo.Operators(ns)
+
+
+@pytest.mark.parametrize("which", ["cavity", "channel"])
+def test_operator_invariants(which, cavity_ops, channel_ops):
+    ns, ops = cavity_ops if which == "cavity" else channel_ops
+    x, y = ns.x, ns.y
+    inner = ns.kind == vo.KIND_INTERIOR
+    one = np.ones_like(x)
+    tol = 1e-9
+    assert np.max(np.abs(ops.L @ one)) <= tol * 1e2
+    assert np.max(np.abs(ops.L @ (x * x + y * y) - 4.0)) <= tol * 1e2
+    assert np.max(np.abs(ops.L @ (x * y))) <= tol * 1e2
+    for q in (one, x, y, x * x, x * y, y * y):
+        assert np.max(np.abs(ops.D[(0, 0)] @ q - q)) <= 1e-12 * 10
+    # VIP differences: exact central differences of quadratics at interior nodes
+    assert np.max(np.abs(ops.Gx @ one)) <= 1e-10
+    assert np.max(np.abs((ops.Gx @ x)[inner] - 1.0)) <= 1e-10
+    assert np.max(np.abs((ops.Gx @ y)[inner])) <= 1e-10
+    assert np.max(np.abs((ops.Gy @ y)[inner] - 1.0)) <= 1e-10
+    assert np.max(np.abs((ops.Gx @ (x * x))[inner] - 2 * x[inner])) <= 1e-9
+    assert np.max(np.abs((ops.Gy @ (x * y))[inner] - x[inner])) <= 1e-9
+    assert np.all((ops.Gx @ x)[~inner] == 0.0)
+    # zero-normal-derivative rows: q_i - 4/3 q(x_i + h n_in) + 1/3 q(x_i + 2h n_in)
+    # equals (2/3) h dq/dn_out for every quadratic q
+    bb = ops.boundary
+    for q, gx, gy in ((x, one, 0 * x), (y * y, 0 * x, 2 * y), (x * y, y, x)):
+        dn = gx * ns.nx + gy * ns.ny
+        got = (ops.Nb @ q)[bb]
+        assert np.max(np.abs(got - (2.0 / 3.0) * ns.h[bb] * dn[bb])) <= 1e-10
+
+
+def test_convection_equals_flux_of_exact_vip_values(channel_ops):
+    """For quadratic u, v the MLS values at the VIPs are exact, so the convection term
+    equals the flux differences of the closed-form values at x_e, x_w, x_n, x_s."""
+    ns, ops = channel_ops
+    U = lambda X, Y: 0.3 + 0.2 * X - 0.1 * Y + 0.05 * X * X - 0.07 * X * Y + 0.02 * Y * Y  # noqa
+    V = lambda X, Y: -0.1 + 0.1 * X + 0.3 * Y - 0.04 * X * X + 0.03 * X * Y + 0.06 * Y * Y  # noqa
+    Nu, Nv = vo.convection(ops, U(ns.x, ns.y), V(ns.x, ns.y))
+    ii = ops.interior
+    (xe, ye), (xw, yw) = ops.vip["e"], ops.vip["w"]
+    (xn, yn), (xs, ys) = ops.vip["n"], ops.vip["s"]
+    dew, dns = xe - xw, yn - ys
+    ref_u = (U(xe, ye) ** 2 - U(xw, yw) ** 2) / dew + (U(xn, yn) * V(xn, yn) - U(xs, ys) * V(xs, ys)) / dns
+    ref_v = (U(xe, ye) * V(xe, ye) - U(xw, yw) * V(xw, yw)) / dew + (V(xn, yn) ** 2 - V(xs, ys) ** 2) / dns
+    assert np.max(np.abs(Nu[ii] - ref_u)) <= 1e-9
+    assert np.max(np.abs(Nv[ii] - ref_v)) <= 1e-9
+    bnd = ns.kind != vo.KIND_INTERIOR
+    assert np.all(Nu[bnd] == 0.0) and np.all(Nv[bnd] == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Krylov solver against a sparse direct solve
+# ---------------------------------------------------------------------------
+
+def test_bicgstab_matches_direct_solve(cavity_ops, channel_ops):
+    rng = np.random.default_rng(1)
+    n = 200
+    A = sp.random(n, n, density=0.03, random_state=1) + sp.diags(4.0 + rng.random(n))
+    b = rng.standard_normal(n)
+    x, it, res = vo.bicgstab(A.tocsr(), b, None, 1e-12, 10000)
+    assert res <= 1e-12
+    assert np.allclose(x, spl.spsolve(A.tocsc(), b), rtol=0, atol=1e-10)
+    for ns, ops in (cavity_ops, channel_ops):
+        fs = vo.FractionalStep(ops, rtol=1e-12)
+        for M in (fs.Hu, fs.Hv, fs.P):
+            b = rng.standard_normal(M.shape[0])
+            x, it, res = vo.bicgstab(M, b, None, 1e-12, 20000)
+            ref = spl.spsolve(M.tocsc(), b)
+            assert res <= 1e-12
+            assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2 + Sec. 5.1: the fractional step on the decaying vortices
+# ---------------------------------------------------------------------------
+
+def tg_error(n, T, dt, Re=1.0, **kw):
+    ns = w.periodic_box(n, Re=Re, dt=dt)
+    fs = vo.FractionalStep(vo.Operators(ns), rtol=1e-12, **kw)
+    for _ in range(int(round(T / dt))):
+        fs.step()
+    ue, ve, _ = w.taylor_green(ns.x, ns.y, T, Re)
+    return fs, np.sqrt(np.mean((fs.u - ue) ** 2 + (fs.v - ve) ** 2))
+
+
+def test_taylor_green_second_order_in_space():
+    e = [tg_error(n, 0.05, 1e-3)[1] for n in (16, 32, 64)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert min(orders) >= 1.8, orders
+
+
+def test_taylor_green_second_order_in_time():
+    """Self-convergence in dt at fixed nodes (the spatial error cancels)."""
+    T = 0.2
+    ref = tg_error(24, T, 0.2 / 160)[0]
+    errs = []
+    for dt in (0.02, 0.01, 0.005):
+        fs = tg_error(24, T, dt)[0]
+        errs.append(np.sqrt(np.mean((fs.u - ref.u) ** 2 + (fs.v - ref.v) ** 2)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) >= 1.7, orders
+
+
+def test_taylor_green_decay_rate():
+    """Kinetic energy decays like exp(-4t/Re) (the closed form of Sec. 5.1)."""
+    ns = w.periodic_box(32, Re=100.0, dt=1e-3)
+    fs = vo.FractionalStep(vo.Operators(ns), rtol=1e-12)
+    e0 = np.mean(fs.u ** 2 + fs.v ** 2)
+    for _ in range(100):
+        fs.step()
+    e1 = np.mean(fs.u ** 2 + fs.v ** 2)
+    assert e1 / e0 == pytest.approx(math.exp(-4 * 0.1 / 100.0), rel=2e-3)
+
+
+def test_projected_divergence_at_poisson_tolerance():
+    """With the composite operator D_vip G_vip in Eq. (13) the projection of Eq. (14)
+    leaves, at every interior node, dt times (Poisson residual + mu): the divergence
+    of the projected velocity is at the Poisson tolerance up to the one constant mu
+    that a closed domain's right-hand side carries outside the operator's range."""
+    ns = w.cavity(16, Re=100.0)
+    fs = vo.FractionalStep(vo.Operators(ns), rtol=1e-10, poisson="vip_divgrad")
+    for _ in range(3):
+        st = fs.step()
+    ops = fs.ops
+    div = fs.divergence()
+    DG = ops.Gx @ (ops.Gx @ fs.phi) + ops.Gy @ (ops.Gy @ fs.phi)
+    # row identity of the projection: div = dt (b - D G phi) exactly
+    assert np.max(np.abs(div - fs.dt * (fs.b_last - DG))) <= 1e-13 * max(1.0, np.max(np.abs(div)))
+    # and div - dt mu = dt * residual, bounded by the solver tolerance
+    excess = np.where(fs.inner, div - fs.dt * fs.mu, 0.0)
+    assert np.linalg.norm(excess) <= 1.01 * fs.dt * fs.rtol * st["b_norm"] + 1e-15
+
+
+def test_literal_projection_divergence_decays_second_order():
+    """With the MLS Laplacian of Eq. (vip:1) the projection is approximate: the divergence
+    left after Eq. (14) is dt (L - D G) phi = O(h^2).  L and D G share most of their
+    leading error, so the order is measured over a factor-4 refinement."""
+    d = []
+    for n in (16, 64):
+        fs, _ = tg_error(n, 0.01, 1e-3)
+        d.append(np.sqrt(np.mean(fs.divergence() ** 2)))
+    assert math.log2(d[0] / d[1]) / 2 >= 1.7, d
+
+
+def test_boundary_rows_hold(channel_ops):
+    ns, ops = channel_ops
+    fs = vo.FractionalStep(ops, rtol=1e-12)
+    for _ in range(3):
+        fs.step()
+    wall = ns.kind == vo.KIND_WALL
+    assert np.array_equal(fs.u[wall], ns.u0[wall]) and np.array_equal(fs.v[wall], ns.v0[wall])
+    slip = ns.kind == vo.KIND_SLIP
+    assert np.array_equal(fs.v[slip], ns.v0[slip])
+    # zero normal derivative of u* at slip and outlet rows, to the solver tolerance
+    neu = (ns.kind == vo.KIND_SLIP) | (ns.kind == vo.KIND_OUTLET)
+    assert np.max(np.abs((ops.Nb @ fs.ustar)[neu])) <= 1e-9
+    out = ns.kind == vo.KIND_OUTLET
+    assert np.max(np.abs((ops.Nb @ fs.vstar)[out])) <= 1e-9
+    # phi = 0 at the outlet
+    assert np.all(fs.phi[ns.kind == vo.KIND_OUTLET] == 0.0)
+
+
+def test_closed_domain_poisson_is_solvable():
+    """Bordered system: phi_k = 0 at the reference node and every Poisson row of the
+    singular operator holds up to the single scalar mu."""
+    ns = w.cavity(16, Re=100.0)
+    fs = vo.FractionalStep(vo.Operators(ns), rtol=1e-12)
+    fs.step()
+    st = fs.last
+    assert fs.bordered and fs.phi[fs.pin] == 0.0
+    inner = fs.inner
+    L = fs.ops.L
+    r = fs.b_last - (L @ fs.phi) - fs.mu * inner
+    assert np.max(np.abs(r[inner])) <= 1e-9 * max(1.0, np.max(np.abs(fs.b_last)))
+    assert st["res_p"] <= 1e-12
