@@ -1,0 +1,203 @@
+/*
+ * vip.h -- C ABI of libvip, the GPU (sm_103a) path of the virtual interpolation
+ * point (VIP) fractional-step solver of Park, Jo and Choe, "Virtual
+ * Interpolation Point Method for Viscous Flows in Complex Geometries".
+ *
+ * The calls follow the paper's statement of the problem: a node set and its
+ * geometry (Sec. 3: the node set Lambda), the moving least-squares fit (Sec. 3:
+ * quadratic basis, weight function Phi, dilation rho), the flow parameters
+ * (Sec. 2: Re, dt) and then the fractional step, Eqs. (12)-(15), per time step.
+ *
+ * Conventions for every call
+ *   - Every call returns vip_status; none aborts, traps or exits.  After an
+ *     error vip_last_error() gives a one-line diagnostic.
+ *   - Array arguments are plain pointers.  Unless stated otherwise a pointer
+ *     may be host memory (pageable or pinned) or device memory of the
+ *     context's device; the library copies from / into it (cudaMemcpyDefault).
+ *     Inputs are copied, so the caller keeps ownership and may reuse them as
+ *     soon as the call returns.  Outputs go into caller-owned buffers.
+ *   - Node arrays are in the caller's order, geometries concatenated in the
+ *     order they were added ("global node order").
+ *   - Work is issued on the stream passed to vip_create.  Calls that return
+ *     host data synchronise that stream; vip_step does not.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef VIP_H
+#define VIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vip_ctx vip_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    VIP_OK = 0,
+    VIP_ERR_ARG = 1,              /* invalid argument or call order */
+    VIP_ERR_CUDA = 2,             /* a CUDA runtime call failed */
+    VIP_ERR_SINGULAR_STENCIL = 3, /* a moment matrix failed its Cholesky test */
+    VIP_ERR_NOT_CONVERGED = 4,    /* a Krylov solve hit its iteration limit */
+    VIP_ERR_BREAKDOWN = 5,        /* BiCGSTAB could not continue (no progress) */
+    VIP_ERR_NONFINITE = 6,        /* NaN/Inf in an input or a residual */
+    VIP_ERR_TIMEOUT = 7,          /* a device-side wait ran out its spin limit */
+    VIP_ERR_OOM = 8               /* device allocation failed */
+} vip_status;
+
+/* Node kinds (one byte per node), Sec. 5 boundary conditions:
+ *   INTERIOR  momentum and Poisson equations collocated at the node;
+ *   WALL      velocity Dirichlet (value from vip_set_state, held fixed),
+ *             pressure-increment zero normal derivative (walls, lid, inflow);
+ *   SLIP      u zero normal derivative, v Dirichlet, pressure increment zero
+ *             normal derivative (channel top/bottom, "v = 0, t_x = 0");
+ *   OUTLET    velocity zero normal derivative, pressure increment = 0
+ *             (traction-free outflow). */
+enum { VIP_NODE_INTERIOR = 0, VIP_NODE_WALL = 1, VIP_NODE_SLIP = 2, VIP_NODE_OUTLET = 3 };
+
+/* Weight function Phi of Sec. 3, in r = |x_i - xbar| / rho:
+ *   CUBIC_SPLINE  2/3-4r^2+4r^3 (r<=1/2), 4/3-4r+4r^2-4r^3/3 (1/2<r<1), 0 else;
+ *   PAPER         (1 - r^((1-r)^2))^4 for r < 1, 0 else (the printed form). */
+enum { VIP_W_CUBIC_SPLINE = 0, VIP_W_PAPER = 1 };
+
+/* Precision of the Krylov solves (Eqs. 12-13):
+ *   FP64   BiCGSTAB in FP64 on FP64 operators;
+ *   MIXED  FP64 residual b - A x on FP64 operators, correction equation solved
+ *          by BiCGSTAB in FP32 on FP32 copies of the operators, repeated until
+ *          the FP64 relative residual meets the tolerance. */
+enum { VIP_PREC_FP64 = 0, VIP_PREC_MIXED = 1 };
+
+/* Identity operator wherever the paper writes I in Eq. (12):
+ *   EXACT  the identity; MLS  the MLS approximant D^[0,0] (Eq. vip:1). */
+enum { VIP_IDENTITY_EXACT = 0, VIP_IDENTITY_MLS = 1 };
+
+/* Tables and operators that can be exported (vip_get_stencil) or applied
+ * (vip_apply).  Rows are global nodes; columns are global nodes, except the
+ * column index N (total node count) of the POISSON operator, which is the
+ * extra unknown mu of a closed domain (see VIP_OP_POISSON).
+ *   NBR          neighbour lists of the nodes, value = 1           (Sec. 3)
+ *   D00..D02     node derivative approximants D^[a,b]      (Eq. fmlsrk:2)
+ *   LAPLACE      D^[2,0] + D^[0,2]                             (Eq. vip:1)
+ *   VIP_E..VIP_S MLS interpolation Psi^[0,0](x_vip) to the east, west,
+ *                north and south VIPs of interior nodes (empty rows for
+ *                boundary nodes)                                (Sec. 4.1)
+ *   GX, GY       merged VIP differences (u(x_e)-u(x_w))/|x_e-x_w| and
+ *                (u(x_n)-u(x_s))/|x_n-x_s| (Sec. 4.1 items 2 and 3)
+ *   HELM_U/V     Helmholtz operator of Eq. (12) times dt for u and v with
+ *                the boundary rows
+ *   POISSON      operator of Eq. (13) with boundary rows; for a geometry
+ *                with no OUTLET node it is bordered by one extra unknown mu
+ *                and one extra row (row N_g of the geometry's block):
+ *                [P z; e_0^T 0] with z the indicator of interior rows. */
+enum {
+    VIP_OP_NBR = 0, VIP_OP_D00 = 1, VIP_OP_D10 = 2, VIP_OP_D01 = 3, VIP_OP_D20 = 4,
+    VIP_OP_D11 = 5, VIP_OP_D02 = 6, VIP_OP_LAPLACE = 7, VIP_OP_VIP_E = 8,
+    VIP_OP_VIP_W = 9, VIP_OP_VIP_N = 10, VIP_OP_VIP_S = 11, VIP_OP_GX = 12,
+    VIP_OP_GY = 13, VIP_OP_HELM_U = 14, VIP_OP_HELM_V = 15, VIP_OP_POISSON = 16,
+    VIP_OP_COUNT = 17
+};
+
+typedef struct {
+    int64_t steps;            /* time steps taken since vip_set_state */
+    int32_t helm_iters;       /* last step: BiCGSTAB iterations, Helmholtz (max over systems) */
+    int32_t poisson_iters;    /* last step: inner BiCGSTAB iterations, Poisson (max) */
+    int32_t poisson_outer;    /* last step: FP64 refinement passes, Poisson (max) */
+    int32_t status;           /* first vip_status raised on the device, VIP_OK if none */
+    double helm_relres;       /* last step: final FP64 relative residual (max) */
+    double poisson_relres;    /* last step: final FP64 relative residual (max) */
+    int64_t total_poisson_iters; /* inner Poisson iterations summed over all steps */
+} vip_step_stats;
+
+/* Create a context on CUDA device `device`; work is issued on `cuda_stream`
+ * (a cudaStream_t, NULL = the legacy default stream). */
+vip_status vip_create(vip_ctx** out, int device, void* cuda_stream);
+void vip_destroy(vip_ctx* ctx);
+const char* vip_last_error(const vip_ctx* ctx);
+
+/* Add one geometry (node set Lambda of Sec. 3) to the context's batch.
+ * n nodes; x, y coordinates; kind per node (VIP_NODE_*); nx, ny unit outward
+ * normal of the fluid domain at boundary nodes (ignored at interior nodes);
+ * h_local > 0, the local node spacing (rho = support * h_local, VIPs at
+ * +-h_local/2, normal auxiliary points at h_local and 2 h_local); Lx, Ly > 0
+ * make the geometry periodic with that period (0 = not periodic).  All arrays
+ * are copied.  *geom_out receives the geometry index (0, 1, ...).
+ * Must precede vip_build. */
+vip_status vip_add_nodes(vip_ctx* ctx, int64_t n, const double* x, const double* y,
+                         const uint8_t* kind, const double* nx, const double* ny,
+                         const double* h_local, double Lx, double Ly, int32_t* geom_out);
+
+/* MLS fit of Sec. 3: basis_order must be 2 (the six-term quadratic basis);
+ * weight is VIP_W_*; support is the ratio rho / h_local (> 1).  Defaults:
+ * 2, VIP_W_CUBIC_SPLINE, 2.2.  Must precede vip_build. */
+vip_status vip_set_mls(vip_ctx* ctx, int basis_order, int weight, double support);
+
+/* Flow parameters of geometry `geom` (-1 = every geometry): Reynolds number
+ * and time step of Sec. 2.  Must precede vip_build (the operators depend on
+ * dt/Re). */
+vip_status vip_set_flow(vip_ctx* ctx, int32_t geom, double Re, double dt);
+
+/* Krylov settings: precision VIP_PREC_*, relative residual tolerance
+ * ||b - A x||_2 <= rtol ||b||_2 for both solves, iteration limit per solve,
+ * identity VIP_IDENTITY_*.  Defaults MIXED, 1e-8, 20000, EXACT.
+ * The identity mode must be set before vip_build. */
+vip_status vip_set_solver(vip_ctx* ctx, int precision, double rtol, int32_t max_iters,
+                          int identity);
+
+/* Build everything that depends only on the geometry and flow parameters:
+ * neighbour search (nodes, VIPs, normal auxiliary points), MLS moment
+ * matrices and weights (Eq. fmlsrk:2), merged operators (Eqs. 12-15,
+ * Sec. 4.1).  Returns VIP_ERR_SINGULAR_STENCIL if some moment matrix fails
+ * its Cholesky test (the message names the point). Synchronous. */
+vip_status vip_build(vip_ctx* ctx);
+
+/* Set u^n, v^n, p^n (N doubles each, global node order; NULL p = zero) and
+ * reset phi, the convection history and the step counter.  Velocity Dirichlet
+ * values are taken from u, v at Dirichlet nodes and held fixed. */
+vip_status vip_set_state(vip_ctx* ctx, const double* u, const double* v, const double* p);
+
+/* Advance nsteps fractional steps, Eqs. (12)-(15), for every geometry.
+ * Asynchronous on the context's stream (one CUDA graph launch per step when
+ * graphs are enabled).  Device-side failures are reported by vip_get_stats. */
+vip_status vip_step(vip_ctx* ctx, int32_t nsteps);
+
+/* Copy the state out (N doubles each; any pointer may be NULL).  phi is the
+ * last pressure increment.  Synchronises the stream. */
+vip_status vip_get_state(vip_ctx* ctx, double* u, double* v, double* p, double* phi);
+
+/* Statistics of the last step (synchronises).  Returns the device status. */
+vip_status vip_get_stats(vip_ctx* ctx, vip_step_stats* out);
+
+/* Total node count N and the number of geometries. */
+vip_status vip_get_sizes(vip_ctx* ctx, int64_t* n_nodes, int32_t* n_geoms);
+
+/* Size of an exported table: rows (N, or N + number of bordered geometries
+ * for VIP_OP_POISSON) and stored entries.  After vip_build. */
+vip_status vip_stencil_info(vip_ctx* ctx, int which, int64_t* nrows, int64_t* nnz);
+
+/* Export table `which` as CSR: row_ptr[nrows+1], col[nnz], val[nnz], columns
+ * ascending within a row.  Host or device pointers.  Synchronises. */
+vip_status vip_get_stencil(vip_ctx* ctx, int which, int64_t* row_ptr, int32_t* col,
+                           double* val);
+
+/* y = Op x for a table `which` in FP64 (x of length = columns, y = rows).
+ * Synchronises. */
+vip_status vip_apply(vip_ctx* ctx, int which, const double* x, double* y);
+
+/* Convection term of Sec. 4.1 item 1 at every node (zero at boundary nodes)
+ * for the velocity field (u, v).  Synchronises. */
+vip_status vip_convection(vip_ctx* ctx, const double* u, const double* v, double* Nu,
+                          double* Nv);
+
+/* Solve system `which` (VIP_OP_HELM_U, VIP_OP_HELM_V or VIP_OP_POISSON) for
+ * every geometry at once with the step's Krylov solver: b and x have the
+ * operator's row count; x holds the initial guess on entry and the solution
+ * on return.  iters (may be NULL) gets the iteration count, relres (may be
+ * NULL) the largest final FP64 relative residual over geometries. */
+vip_status vip_solve(vip_ctx* ctx, int which, const double* b, double* x, int precision,
+                     double rtol, int32_t max_iters, int32_t* iters, double* relres);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VIP_H */

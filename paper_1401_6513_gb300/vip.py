@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libvip (include/vip.h): argument marshalling only.
+
+Every computation happens in the library's CUDA kernels.  Functions keep the C
+names; array arguments accept numpy arrays (host memory) or any object with a
+``data_ptr()`` (device or pinned host memory, e.g. torch tensors).  If the
+library is missing the import fails with an error; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "libvip.so"
+
+VIP_OK, VIP_ERR_ARG, VIP_ERR_CUDA, VIP_ERR_SINGULAR_STENCIL = 0, 1, 2, 3
+VIP_ERR_NOT_CONVERGED, VIP_ERR_BREAKDOWN, VIP_ERR_NONFINITE, VIP_ERR_TIMEOUT, VIP_ERR_OOM = 4, 5, 6, 7, 8
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_SINGULAR_STENCIL",
+                4: "ERR_NOT_CONVERGED", 5: "ERR_BREAKDOWN", 6: "ERR_NONFINITE",
+                7: "ERR_TIMEOUT", 8: "ERR_OOM"}
+VIP_NODE_INTERIOR, VIP_NODE_WALL, VIP_NODE_SLIP, VIP_NODE_OUTLET = 0, 1, 2, 3
+VIP_W_CUBIC_SPLINE, VIP_W_PAPER = 0, 1
+VIP_PREC_FP64, VIP_PREC_MIXED = 0, 1
+VIP_IDENTITY_EXACT, VIP_IDENTITY_MLS = 0, 1
+OPS = ["NBR", "D00", "D10", "D01", "D20", "D11", "D02", "LAPLACE", "VIP_E", "VIP_W", "VIP_N",
+       "VIP_S", "GX", "GY", "HELM_U", "HELM_V", "POISSON"]
+OP = {name: i for i, name in enumerate(OPS)}
+
+# Every C entry point the header declares (checked by the CPU tests).
+EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_set_mls",
+           "vip_set_flow", "vip_set_solver", "vip_build", "vip_set_state", "vip_step",
+           "vip_get_state", "vip_get_stats", "vip_get_sizes", "vip_stencil_info",
+           "vip_get_stencil", "vip_apply", "vip_convection", "vip_solve"]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("helm_iters", C.c_int32), ("poisson_iters", C.c_int32),
+                ("poisson_outer", C.c_int32), ("status", C.c_int32), ("helm_relres", C.c_double),
+                ("poisson_relres", C.c_double), ("total_poisson_iters", C.c_int64)]
+
+
+class VipError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib(path: str | Path | None = None):
+    """Load libvip.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path else _LIB_PATH
+    if not p.exists():
+        raise ImportError(f"{p} is missing: build it with paper_1401_6513_gb300.build.build()")
+    L = C.CDLL(str(p))
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "vip_create": ([C.POINTER(vp), C.c_int, vp], C.c_int),
+        "vip_destroy": ([vp], None),
+        "vip_last_error": ([vp], C.c_char_p),
+        "vip_add_nodes": ([vp, i64, vp, vp, vp, vp, vp, vp, dbl, dbl, C.POINTER(i32)], C.c_int),
+        "vip_set_mls": ([vp, C.c_int, C.c_int, dbl], C.c_int),
+        "vip_set_flow": ([vp, i32, dbl, dbl], C.c_int),
+        "vip_set_solver": ([vp, C.c_int, dbl, i32, C.c_int], C.c_int),
+        "vip_build": ([vp], C.c_int),
+        "vip_set_state": ([vp, vp, vp, vp], C.c_int),
+        "vip_step": ([vp, i32], C.c_int),
+        "vip_get_state": ([vp, vp, vp, vp, vp], C.c_int),
+        "vip_get_stats": ([vp, C.POINTER(StepStats)], C.c_int),
+        "vip_get_sizes": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
+        "vip_stencil_info": ([vp, C.c_int, C.POINTER(i64), C.POINTER(i64)], C.c_int),
+        "vip_get_stencil": ([vp, C.c_int, vp, vp, vp], C.c_int),
+        "vip_apply": ([vp, C.c_int, vp, vp], C.c_int),
+        "vip_convection": ([vp, vp, vp, vp, vp], C.c_int),
+        "vip_solve": ([vp, C.c_int, vp, vp, C.c_int, dbl, i32, C.POINTER(i32), C.POINTER(dbl)],
+                      C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    if path is None:
+        _lib = L
+    return L
+
+
+def _ptr(a):
+    """Raw address of a numpy array or a tensor-like object (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _f64(a):
+    if hasattr(a, "data_ptr"):
+        return a
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Context:
+    """Owns one vip_ctx; methods call the C entry points of the same name."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self.L = lib()
+        h = C.c_void_p()
+        st = self.L.vip_create(C.byref(h), device, C.c_void_p(stream) if stream else None)
+        self.h = h
+        self._check(st)
+
+    def _check(self, st):
+        if st != VIP_OK:
+            msg = self.L.vip_last_error(self.h)
+            raise VipError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if self.h:
+            self.L.vip_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setup -------------------------------------------------------------
+    def vip_add_nodes(self, x, y, kind, nx, ny, h_local, Lx=0.0, Ly=0.0) -> int:
+        x, y, nx, ny, h_local = map(_f64, (x, y, nx, ny, h_local))
+        kind = kind if hasattr(kind, "data_ptr") else np.ascontiguousarray(kind, dtype=np.uint8)
+        g = C.c_int32(-1)
+        n = x.numel() if hasattr(x, "numel") else x.size
+        self._check(self.L.vip_add_nodes(self.h, n, _ptr(x), _ptr(y), _ptr(kind), _ptr(nx),
+                                         _ptr(ny), _ptr(h_local), float(Lx), float(Ly),
+                                         C.byref(g)))
+        return g.value
+
+    def add_nodeset(self, ns) -> int:
+        """Add a workloads.NodeSet and set its flow parameters."""
+        g = self.vip_add_nodes(ns.x, ns.y, ns.kind, ns.nx, ns.ny, ns.h, ns.Lx, ns.Ly)
+        self.vip_set_flow(g, ns.Re, ns.dt)
+        return g
+
+    def vip_set_mls(self, basis_order=2, weight=VIP_W_CUBIC_SPLINE, support=2.2):
+        self._check(self.L.vip_set_mls(self.h, basis_order, weight, float(support)))
+
+    def vip_set_flow(self, geom, Re, dt):
+        self._check(self.L.vip_set_flow(self.h, int(geom), float(Re), float(dt)))
+
+    def vip_set_solver(self, precision=VIP_PREC_MIXED, rtol=1e-8, max_iters=20000,
+                       identity=VIP_IDENTITY_EXACT):
+        self._check(self.L.vip_set_solver(self.h, precision, float(rtol), int(max_iters), identity))
+
+    def vip_build(self):
+        self._check(self.L.vip_build(self.h))
+
+    # -- state and stepping --------------------------------------------------
+    def vip_set_state(self, u, v, p=None):
+        u, v = _f64(u), _f64(v)
+        p = None if p is None else _f64(p)
+        self._check(self.L.vip_set_state(self.h, _ptr(u), _ptr(v), _ptr(p)))
+
+    def vip_step(self, nsteps=1):
+        self._check(self.L.vip_step(self.h, int(nsteps)))
+
+    def vip_get_state(self, u=None, v=None, p=None, phi=None):
+        """Fill the given buffers; with no buffers, return fresh numpy arrays."""
+        if u is None and v is None and p is None and phi is None:
+            n = self.sizes()[0]
+            u, v, p, phi = (np.empty(n) for _ in range(4))
+        self._check(self.L.vip_get_state(self.h, _ptr(u), _ptr(v), _ptr(p), _ptr(phi)))
+        return u, v, p, phi
+
+    def vip_get_stats(self) -> StepStats:
+        s = StepStats()
+        self._check(self.L.vip_get_stats(self.h, C.byref(s)))
+        return s
+
+    def sizes(self):
+        n = C.c_int64()
+        g = C.c_int32()
+        self._check(self.L.vip_get_sizes(self.h, C.byref(n), C.byref(g)))
+        return n.value, g.value
+
+    # -- inspection ----------------------------------------------------------
+    def vip_get_stencil(self, which):
+        """Return (row_ptr, col, val) of a table as numpy arrays."""
+        w = OP[which] if isinstance(which, str) else int(which)
+        nr, nz = C.c_int64(), C.c_int64()
+        self._check(self.L.vip_stencil_info(self.h, w, C.byref(nr), C.byref(nz)))
+        ptr = np.empty(nr.value + 1, np.int64)
+        col = np.empty(max(nz.value, 1), np.int32)
+        val = np.empty(max(nz.value, 1), np.float64)
+        self._check(self.L.vip_get_stencil(self.h, w, _ptr(ptr), _ptr(col), _ptr(val)))
+        return ptr, col[:nz.value], val[:nz.value]
+
+    def vip_apply(self, which, x, y=None):
+        w = OP[which] if isinstance(which, str) else int(which)
+        x = _f64(x)
+        if y is None:
+            y = np.empty_like(x) if isinstance(x, np.ndarray) else None
+        self._check(self.L.vip_apply(self.h, w, _ptr(x), _ptr(y)))
+        return y
+
+    def vip_convection(self, u, v):
+        u, v = _f64(u), _f64(v)
+        Nu, Nv = np.empty_like(u), np.empty_like(v)
+        self._check(self.L.vip_convection(self.h, _ptr(u), _ptr(v), _ptr(Nu), _ptr(Nv)))
+        return Nu, Nv
+
+    def vip_solve(self, which, b, x0, precision=VIP_PREC_FP64, rtol=1e-8, max_iters=20000):
+        w = OP[which] if isinstance(which, str) else int(which)
+        b = _f64(b)
+        x = np.array(x0, dtype=np.float64, copy=True)
+        it = C.c_int32()
+        rr = C.c_double()
+        self._check(self.L.vip_solve(self.h, w, _ptr(b), _ptr(x), precision, float(rtol),
+                                     int(max_iters), C.byref(it), C.byref(rr)))
+        return x, it.value, rr.value
+
+
+def solver_for(nodesets, precision=VIP_PREC_MIXED, rtol=1e-8, max_iters=20000,
+               identity=VIP_IDENTITY_EXACT, weight=VIP_W_CUBIC_SPLINE, support=2.2,
+               device=0, stream=None, set_state=True) -> Context:
+    """Create a context for one node set or a list of them, build it and set u0, v0, p0."""
+    if not isinstance(nodesets, (list, tuple)):
+        nodesets = [nodesets]
+    ctx = Context(device, stream)
+    for ns in nodesets:
+        ctx.add_nodeset(ns)
+    ctx.vip_set_mls(2, weight, support)
+    ctx.vip_set_solver(precision, rtol, max_iters, identity)
+    ctx.vip_build()
+    if set_state:
+        ctx.vip_set_state(np.concatenate([ns.u0 for ns in nodesets]),
+                          np.concatenate([ns.v0 for ns in nodesets]),
+                          np.concatenate([ns.p0 for ns in nodesets]))
+    return ctx
