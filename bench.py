@@ -1,0 +1,326 @@
+#!/usr/bin/env python3
+"""Benchmark of the VIP fractional-step solver on one or more GPUs.
+
+Metric: fractional-step node-updates/s with every Poisson solve converged to a
+1e-8 relative residual (nodes x steps / seconds), plus the HBM roofline of the
+dominant kernel (the Poisson BiCGSTAB launch).
+
+Workload (default): flow past the bumpy cylinder r = 1 + 0.05 sin 12t + 0.02 sin 31t
+in the channel [-8,24]x[-8,8] at h = 1/64 (about 2.1M nodes), Re = 200, dt = h/10,
+FP32-inner / FP64-refinement Krylov solves, synthetic (generated) node set and an
+impulsively started uniform inflow.  Its working set (several GB) exceeds the
+129 MB L2, so no flush is needed between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (under torch.distributed.run) each rank runs an independent replica
+of the workload on its own GPU (the single-geometry path has no exchange step);
+value = all ranks' node updates / max-over-ranks time ("weak" scaling).
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "fractional-step node-updates/s at 1e-8 Poisson residual"
+UNIT = "node-updates/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="bumpy_h64")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    import workloads as w
+    if name == "bumpy_h64":
+        h = 1.0 / 64
+        ns = w.channel_body(h, ("sines", 1.0, [(0.05, 12), (0.02, 31)]), Re=200.0, dt=0.1 * h,
+                            name="bumpy_h64")
+        cfg = {"workload": "bumpy cylinder r=1+0.05sin12t+0.02sin31t in channel "
+                           "[-8,24]x[-8,8], h=1/64", "nodes": ns.n, "Re": 200.0, "dt": 0.1 * h}
+        return ns, cfg
+    if name == "cylinder_h32":
+        h = 1.0 / 32
+        ns = w.channel_body(h, ("circle", 0.5), Re=100.0, dt=0.2 * h)
+        return ns, {"workload": "circular cylinder D=1 in channel [-8,24]x[-8,8], h=1/32",
+                    "nodes": ns.n, "Re": 100.0, "dt": 0.2 * h}
+    if name == "cavity_256":
+        ns = w.cavity(256, Re=1000.0)
+        return ns, {"workload": "lid-driven cavity 256x256, Re=1000", "nodes": ns.n,
+                    "Re": 1000.0, "dt": ns.dt}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def cpu_sample(name):
+    """The bounded sample of the workload that the CPU oracle is timed on."""
+    import workloads as w
+    if name == "bumpy_h64":
+        h = 1.0 / 64
+        ns = w.channel_body(h, ("sines", 1.0, [(0.05, 12), (0.02, 31)]), Re=200.0, dt=0.1 * h,
+                            xlim=(-2.0, 3.0), ylim=(-1.5, 1.5))
+        return ns, "same body, h, Re and dt on the channel cropped to [-2,3]x[-1.5,1.5]"
+    ns, _ = make_workload(name)
+    return ns, "full workload"
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200",
+                                       "-i", str(gpu_id)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_oracle(name, steps, warmup=0):
+    """Time the CPU oracle, as it stands, on the bounded sample (node-updates/s)."""
+    from oracle import vip_oracle as vo
+    ns, desc = cpu_sample(name)
+    t0 = time.perf_counter()
+    fs = vo.FractionalStep(vo.Operators(ns), rtol=1e-8)
+    setup = time.perf_counter() - t0
+    for _ in range(warmup):
+        fs.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fs.step()
+    sec = time.perf_counter() - t0
+    iters = [s["it_p"] for s in fs.stats[warmup:]]
+    return {"value": ns.n * steps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} step(s) after {warmup} warm-up step(s) from the impulsive start, "
+                      f"{ns.n} nodes ({desc}); FP64 NumPy/SciPy, single thread; setup "
+                      f"{setup:.1f}s not timed; Poisson iterations {iters}"}
+
+
+def run_reference(args, rank, ws):
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    ref = time_oracle(args.workload, max(1, args.steps), args.warmup)
+    _, cfg = make_workload(args.workload)
+    line = {"impl": "reference", "metric": METRIC, "value": ref["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": ref["value"], "unit": UNIT, "cores": ref["cores"],
+                             "kind": "oracle", "sample": ref["sample"]},
+            "e2e": {"value": ref["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, ws)
+        return
+    import numpy as np
+    import torch
+
+    import paper_1401_6513_gb300 as pkg
+    pkg.build()
+    vip = pkg.load()
+    dev = local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    ns, cfg = make_workload(args.workload)
+    prec = vip.VIP_PREC_MIXED if args.precision == "mixed" else vip.VIP_PREC_FP64
+    t0 = time.perf_counter()
+    ctx = vip.solver_for(ns, precision=prec, rtol=1e-8, max_iters=50000, device=dev,
+                         stream=stream.cuda_stream)
+    setup_s = time.perf_counter() - t0
+    N = ns.n
+    ctx.vip_step(args.warmup)
+    torch.cuda.synchronize()
+    s0 = ctx.vip_get_stats()
+    # ---- timed region: K steps, device time by CUDA events on the library's stream
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = str(dev)
+    clocks = Clocks(uuid)
+    ctx.vip_set_profiling(True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.vip_step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ctx.vip_set_profiling(False)
+    prof, nprof = ctx.vip_get_profile()
+    s1 = ctx.vip_get_stats()
+    ms_max = max_over_ranks(ms, ws)
+    value = N * args.steps * ws / (ms_max / 1e3)
+    # ---- roofline of the Poisson BiCGSTAB launch (one per step)
+    it_p = s1.total_poisson_iters - s0.total_poisson_iters
+    out_p = s1.total_poisson_outer - s0.total_poisson_outer
+    it_h = s1.total_helm_iters - s0.total_helm_iters
+    ptr, _, _ = ctx.vip_get_stencil("POISSON")
+    nnz_p = int(ptr[-1])
+    rows_p = int(ptr.size - 1)
+    tb = 4 if prec == vip.VIP_PREC_MIXED else 8
+    # per inner iteration: 2 SpMVs over the stored entries (value + int32 column) and
+    # 20 vector accesses per row; per refinement pass: one FP64 SpMV and 14 FP64-sized
+    # row accesses (x gather, b, five inits, correction read/write)
+    bytes_p = it_p * (2 * nnz_p * (tb + 4) + 20 * tb * rows_p) + \
+        out_p * (nnz_p * 12 + rows_p * (8 + 8 + 5 * tb + 8 + 8 + tb))
+    t_pois = prof["poisson"] / 1e3
+    pk, pk_src = peaks()
+    hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    achieved = bytes_p / t_pois / 1e9 if t_pois > 0 else 0.0
+    # ---- end to end through the C ABI with pinned host buffers
+    k2 = args.e2e_steps or max(1, min(args.steps, 5))
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    u, v, p, phi = ctx.vip_get_state()
+    hu, hv, hp = pin(u), pin(v), pin(p)
+    ou, ov, op, oph = (torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(4))
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(k2):
+        ctx.vip_load_state(hu, hv, hp)
+        ctx.vip_step(1)
+        ctx.vip_get_state(ou, ov, op, oph)
+    e2e_s = time.perf_counter() - t0
+    barrier(ws)
+    e2e_s = max_over_ranks(e2e_s, ws)
+    st = ctx.vip_get_stats()
+    ctx.close()
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        cpu = time_oracle(args.workload, 1, 0)
+    cfg.update({"global_batch": 1, "parallelism": f"replicas x{ws}", "precision": args.precision,
+                "l2": "working set > L2 (no flush needed)", "setup_s": round(setup_s, 2),
+                "poisson_iters_per_step": it_p / max(args.steps, 1),
+                "poisson_outer_per_step": out_p / max(args.steps, 1),
+                "helmholtz_iters_per_step": it_h / max(args.steps, 1),
+                "phase_ms_per_step": {k: round(v / max(nprof, 1), 3) for k, v in prof.items()},
+                "last_poisson_relres": st.poisson_relres, "status": st.status})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-inner/f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "k_bicgstab (Poisson)",
+                         "peak_source": f"hbm_gbs {pk_src}",
+                         "bytes_per_step": bytes_p / max(args.steps, 1)},
+            "e2e": {"value": N * k2 * ws / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 4 * 8 * N},
+            "gpu_launches": 6 * args.steps,
+            "clocks": clk}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

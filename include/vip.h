@@ -88,8 +88,10 @@ enum { VIP_IDENTITY_EXACT = 0, VIP_IDENTITY_MLS = 1 };
  *                the boundary rows
  *   POISSON      operator of Eq. (13) with boundary rows; for a geometry
  *                with no OUTLET node it is bordered by one extra unknown mu
- *                and one extra row (row N_g of the geometry's block):
- *                [P z; e_0^T 0] with z the indicator of interior rows. */
+ *                (column and row N + k for the k-th such geometry): interior
+ *                rows i carry + mu, the first interior node k0 of the geometry
+ *                gets the row (-4/h^2) phi_k0 = 0, and row N + k holds node k0's
+ *                own equation plus mu. */
 enum {
     VIP_OP_NBR = 0, VIP_OP_D00 = 1, VIP_OP_D10 = 2, VIP_OP_D01 = 3, VIP_OP_D20 = 4,
     VIP_OP_D11 = 5, VIP_OP_D02 = 6, VIP_OP_LAPLACE = 7, VIP_OP_VIP_E = 8,
@@ -107,7 +109,14 @@ typedef struct {
     double helm_relres;       /* last step: final FP64 relative residual (max) */
     double poisson_relres;    /* last step: final FP64 relative residual (max) */
     int64_t total_poisson_iters; /* inner Poisson iterations summed over all steps */
+    int64_t total_poisson_outer; /* FP64 refinement passes of the Poisson solves, summed */
+    int64_t total_helm_iters;    /* Helmholtz iterations (max over systems), summed */
 } vip_step_stats;
+
+/* Phases of one fractional step, timed with CUDA events recorded on the
+ * context's stream inside each step (see vip_set_profiling). */
+enum { VIP_PHASE_RHS = 0, VIP_PHASE_HELMHOLTZ = 1, VIP_PHASE_DIVERGENCE = 2,
+       VIP_PHASE_POISSON = 3, VIP_PHASE_PROJECT = 4, VIP_PHASE_COUNT = 5 };
 
 /* Create a context on CUDA device `device`; work is issued on `cuda_stream`
  * (a cudaStream_t, NULL = the legacy default stream). */
@@ -156,6 +165,12 @@ vip_status vip_build(vip_ctx* ctx);
  * values are taken from u, v at Dirichlet nodes and held fixed. */
 vip_status vip_set_state(vip_ctx* ctx, const double* u, const double* v, const double* p);
 
+/* Overwrite u^n, v^n, p^n (N doubles each, global node order) and continue:
+ * unlike vip_set_state, phi, the convection history, the step counter and
+ * the Dirichlet values are kept.  For callers that change the fields between
+ * steps.  Asynchronous for device pointers and pinned host memory. */
+vip_status vip_load_state(vip_ctx* ctx, const double* u, const double* v, const double* p);
+
 /* Advance nsteps fractional steps, Eqs. (12)-(15), for every geometry.
  * Asynchronous on the context's stream (one CUDA graph launch per step when
  * graphs are enabled).  Device-side failures are reported by vip_get_stats. */
@@ -164,6 +179,15 @@ vip_status vip_step(vip_ctx* ctx, int32_t nsteps);
 /* Copy the state out (N doubles each; any pointer may be NULL).  phi is the
  * last pressure increment.  Synchronises the stream. */
 vip_status vip_get_state(vip_ctx* ctx, double* u, double* v, double* p, double* phi);
+
+/* enable != 0: vip_step waits for each step and adds the CUDA-event time of
+ * every phase (VIP_PHASE_*) to a running total; 0 stops it.  Enabling resets
+ * the totals. */
+vip_status vip_set_profiling(vip_ctx* ctx, int enable);
+
+/* Phase times summed over the profiled steps (ms, VIP_PHASE_COUNT doubles)
+ * and the number of profiled steps. */
+vip_status vip_get_profile(vip_ctx* ctx, double* phase_ms, int64_t* nsteps);
 
 /* Statistics of the last step (synchronises).  Returns the device status. */
 vip_status vip_get_stats(vip_ctx* ctx, vip_step_stats* out);
@@ -196,6 +220,46 @@ vip_status vip_convection(vip_ctx* ctx, const double* u, const double* v, double
  * NULL) the largest final FP64 relative residual over geometries. */
 vip_status vip_solve(vip_ctx* ctx, int which, const double* b, double* x, int precision,
                      double rtol, int32_t max_iters, int32_t* iters, double* relres);
+
+/* ---- learned warm start of the pressure-increment solve ------------------
+ * Not part of the paper's method: a 6-layer 3x3 convolutional network (BF16
+ * tensor-core kernels, FP32 accumulation) on each geometry's regular background
+ * lattice predicts phi^{n+1} - phi^n from u*, v*, the divergence right-hand
+ * side, phi^n and node masks.  The Poisson solve then starts from
+ * phi^n + S * prediction and runs to the same tolerance (Eq. 13 unchanged).
+ * The untrained network predicts 0, i.e. the previous-increment guess. */
+typedef struct {
+    int32_t epochs;     /* passes over the collected samples */
+    double lr;          /* Adam step size */
+    uint64_t seed;      /* sample order */
+    double first_loss;  /* out: mean loss of the first epoch */
+    double final_loss;  /* out: mean loss of the last epoch */
+} vip_train_cfg;
+
+/* enable != 0: from the next step on, store (network input, solved increment
+ * change) of every step, up to max_samples (device memory, owned by the context);
+ * steps run without the CUDA graph while collecting.  0 stops collecting. */
+vip_status vip_ws_collect(vip_ctx* ctx, int enable, int32_t max_samples);
+
+/* Train the network on the collected samples (Adam, one sample per update,
+ * mean squared error over interior lattice nodes).  Synchronous. */
+vip_status vip_ws_train(vip_ctx* ctx, vip_train_cfg* cfg);
+
+/* enable != 0: use the network's guess in vip_step. */
+vip_status vip_ws_enable(vip_ctx* ctx, int enable);
+
+/* direction 0: copy the FP32 parameters out to buf; 1: load them from buf.
+ * *count receives the parameter count (buf may be NULL to query it).  Layout:
+ * for each layer, weights [3][3][cin][cout] then bias [cout]; widths
+ * 16 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1. */
+vip_status vip_ws_params(vip_ctx* ctx, int direction, float* buf, int64_t* count);
+
+/* Evaluate the network on one H x W lattice image x[H][W][16] (FP32, converted
+ * to BF16); y[H][W] (may be NULL) receives the output.  With target, mask and
+ * grads non-NULL also the mean squared error over mask != 0 (*loss) and its
+ * parameter gradients (grads, parameter layout).  Synchronous. */
+vip_status vip_ws_eval(vip_ctx* ctx, int32_t H, int32_t W, const float* x, float* y, float* grads,
+                       const float* target, const float* mask, double* loss);
 
 #ifdef __cplusplus
 }

@@ -368,11 +368,11 @@ class FractionalStep:
       pressure  'incremental': r^n carries -G p^n so that phi is the pressure
                 increment of Eq. (15), p^{n+1} = p^n + phi - (dt/2Re) L phi;
                 'kim_moin': r^n as printed, p^{n+1} = phi - (dt/2Re) L phi.
-    Boundary rows: velocity Dirichlet rows hold the node's initial value; Neumann
-    rows set n . grad = 0 with the MLS weights D^[1,0], D^[0,1] at the node;
-    pressure-increment Dirichlet rows (outlet) set phi = 0.  Problems without any
-    such row (periodic box, closed cavities) pin phi = 0 at node 0 to remove the
-    constant null space.  AB2 starts with N^{-1} = N^0.
+    Boundary rows: velocity Dirichlet rows hold the node's initial value; zero
+    normal derivatives are imposed through the two MLS points on the inward normal
+    (Operators.Nb); pressure-increment Dirichlet rows (outlet) set phi = 0.
+    Problems without such a row (periodic box, closed cavities) use the bordered
+    system described at the construction of P.  AB2 starts with N^{-1} = N^0.
     """
 
     def __init__(self, ops: Operators, Re=None, dt=None, rtol=1e-8, maxit=200000,

@@ -25,12 +25,16 @@ __global__ void k_check_finite(const double* __restrict__ a, const int8_t* __res
     if (i < n && rt[i] == ROW_NODE && !isfinite(a[i])) set_status(status, VIP_ERR_NONFINITE);
 }
 
-__global__ void k_stats(const int32_t* __restrict__ it, int nsys, int64_t* __restrict__ tot) {
+__global__ void k_stats(const int32_t* __restrict__ it, const int32_t* __restrict__ outer, int nsys,
+                        const int32_t* __restrict__ hit, int nhsys, int64_t* __restrict__ tot) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        int m = 0;
-        for (int g = 0; g < nsys; ++g) m = max(m, it[g]);
+        int m = 0, o = 0, hm = 0;
+        for (int g = 0; g < nsys; ++g) { m = max(m, it[g]); o = max(o, outer[g]); }
+        for (int g = 0; g < nhsys; ++g) hm = max(hm, hit[g]);
         tot[0] += m;
         tot[1] += 1;
+        tot[2] += o;
+        tot[3] += hm;
     }
 }
 
@@ -43,15 +47,6 @@ bool finite_host(const double* a, int64_t n) {
     for (int64_t i = 0; i < n; ++i)
         if (!std::isfinite(a[i])) return false;
     return true;
-}
-
-bool is_device_ptr(const void* p) {
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 // copy caller-order node data (length N) into padded rows, or back
@@ -69,19 +64,28 @@ vip_status gather_out(vip_ctx* c, const double* src_padded, double* dst) {
 }
 
 vip_status do_step(vip_ctx* c, cudaStream_t s) {
+    VIP_CUDA(cudaEventRecord(c->ev[0], s));
     launch_conv_rhs(c, s);
     VIP_CUDA(cudaGetLastError());
+    VIP_CUDA(cudaEventRecord(c->ev[1], s));
     vip_status st = krylov_solve(c, c->plan_helm, c->T.helm, c->hrhs, c->hsol, c->precision, c->rtol,
                                  c->max_iters, c->inner_rtol);
     if (st != VIP_OK) return st;
+    VIP_CUDA(cudaEventRecord(c->ev[2], s));
     launch_div(c, s);
     VIP_CUDA(cudaGetLastError());
+    if ((st = cnn_warm_start(c, s)) != VIP_OK) return st;
+    VIP_CUDA(cudaEventRecord(c->ev[3], s));
     st = krylov_solve(c, c->plan_pois, c->T.pois, c->prhs, c->phi, c->precision, c->rtol,
-                      c->max_iters, c->inner_rtol);
+                      c->max_iters, c->inner_rtol, c->use_mg ? &c->mg : nullptr);
     if (st != VIP_OK) return st;
-    k_stats<<<1, 32, 0, s>>>(c->plan_pois.out_iters, c->plan_pois.nsys, c->d_stats);
+    if ((st = cnn_after_solve(c, s)) != VIP_OK) return st;
+    VIP_CUDA(cudaEventRecord(c->ev[4], s));
+    k_stats<<<1, 32, 0, s>>>(c->plan_pois.out_iters, c->plan_pois.out_outer, c->plan_pois.nsys,
+                             c->plan_helm.out_iters, c->plan_helm.nsys, c->d_stats);
     launch_project(c, s);
     VIP_CUDA(cudaGetLastError());
+    VIP_CUDA(cudaEventRecord(c->ev[5], s));
     return VIP_OK;
 }
 
@@ -107,6 +111,7 @@ vip_status vip_create(vip_ctx** out, int device, void* cuda_stream) {
     VIP_CUDA(dalloc(c, &c->d_status, 1));
     VIP_CUDA(dalloc(c, &c->d_step, 1));
     VIP_CUDA(dalloc(c, &c->d_stats, 4));
+    for (int i = 0; i <= VIP_PHASE_COUNT; ++i) VIP_CUDA(cudaEventCreate(&c->ev[i]));
     VIP_CUDA(cudaMemsetAsync(c->d_status, 0, 4, c->stream));
     VIP_CUDA(cudaMemsetAsync(c->d_step, 0, 8, c->stream));
     VIP_CUDA(cudaMemsetAsync(c->d_stats, 0, 32, c->stream));
@@ -119,6 +124,9 @@ void vip_destroy(vip_ctx* c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     cudaStreamSynchronize(c->stream);
     for (void* p : c->allocs) cudaFree(p);
+    cnn_free(c);
+    for (int i = 0; i <= VIP_PHASE_COUNT; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     delete c;
 }
 
@@ -291,6 +299,15 @@ vip_status vip_build(vip_ctx* c) {
             *q = m;
         }
     }
+    if ((s = cnn_setup(c, 20140126)) != VIP_OK) return s;
+    if (c->use_mg) {
+        if ((s = mg_build(c, c->mg)) != VIP_OK) return s;
+        char* m = nullptr;
+        VIP_CUDA(dalloc(c, &m, (size_t)2 * R * 8));
+        c->phat = m;
+        VIP_CUDA(dalloc(c, &m, (size_t)2 * R * 8));
+        c->shat = m;
+    }
     double** fields[] = {&c->u, &c->v, &c->p, &c->phi, &c->ubc, &c->vbc, &c->nu_prev, &c->nv_prev,
                          &c->prhs, &c->lphi};
     for (double** f : fields) {
@@ -340,7 +357,8 @@ vip_status vip_step(vip_ctx* c, int32_t nsteps) {
     if (nsteps < 0) return fail(c, VIP_ERR_ARG, "nsteps < 0");
     VIP_CUDA(cudaSetDevice(c->device));
     for (int32_t k = 0; k < nsteps; ++k) {
-        if (c->use_graph && !c->graph) {
+        const bool direct = cnn_collecting(c);  // sample slots advance every step
+        if (c->use_graph && !c->graph && !direct) {
             cudaGraph_t g = nullptr;
             cudaStream_t cs = c->stream;
             bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -357,14 +375,51 @@ vip_status vip_step(vip_ctx* c, int32_t nsteps) {
                 c->use_graph = false;
             }
         }
-        if (c->graph) {
+        if (c->graph && !direct) {
             VIP_CUDA(cudaGraphLaunch(c->graph, c->stream));
         } else {
             vip_status s = do_step(c, c->stream);
             if (s != VIP_OK) return s;
         }
         c->host_steps++;
+        if (c->profiling) {
+            VIP_CUDA(cudaEventSynchronize(c->ev[VIP_PHASE_COUNT]));
+            for (int ph = 0; ph < VIP_PHASE_COUNT; ++ph) {
+                float ms = 0.f;
+                VIP_CUDA(cudaEventElapsedTime(&ms, c->ev[ph], c->ev[ph + 1]));
+                c->prof_ms[ph] += ms;
+            }
+            c->prof_steps++;
+        }
     }
+    return VIP_OK;
+}
+
+vip_status vip_load_state(vip_ctx* c, const double* u, const double* v, const double* p) {
+    if (!c) return VIP_ERR_ARG;
+    if (!c->built) return fail(c, VIP_ERR_ARG, "vip_load_state before vip_build");
+    vip_status s;
+    if (u && (s = scatter(c, u, c->u)) != VIP_OK) return s;
+    if (v && (s = scatter(c, v, c->v)) != VIP_OK) return s;
+    if (p && (s = scatter(c, p, c->p)) != VIP_OK) return s;
+    return VIP_OK;
+}
+
+vip_status vip_set_profiling(vip_ctx* c, int enable) {
+    if (!c) return VIP_ERR_ARG;
+    c->profiling = enable != 0;
+    if (c->profiling) {
+        for (double& m : c->prof_ms) m = 0.0;
+        c->prof_steps = 0;
+    }
+    return VIP_OK;
+}
+
+vip_status vip_get_profile(vip_ctx* c, double* phase_ms, int64_t* nsteps) {
+    if (!c) return VIP_ERR_ARG;
+    if (phase_ms)
+        for (int i = 0; i < VIP_PHASE_COUNT; ++i) phase_ms[i] = c->prof_ms[i];
+    if (nsteps) *nsteps = c->prof_steps;
     return VIP_OK;
 }
 
@@ -412,6 +467,8 @@ vip_status vip_get_stats(vip_ctx* c, vip_step_stats* out) {
     VIP_CUDA(cudaStreamSynchronize(st));
     out->total_poisson_iters = tot[0];
     out->steps = tot[1];
+    out->total_poisson_outer = tot[2];
+    out->total_helm_iters = tot[3];
     out->status = hs;
     if (hs) {
         c->err = "device reported status " + std::to_string(hs);
@@ -660,7 +717,8 @@ vip_status vip_solve(vip_ctx* c, int which, const double* b, double* x, int prec
     }
     const KrylovPlan& P = pois ? c->plan_pois : c->plan_helm;
     if (s == VIP_OK) s = krylov_solve(c, P, pois ? c->T.pois : c->T.helm, bp, xp, precision, rtol,
-                                      max_iters, c->inner_rtol);
+                                      max_iters, c->inner_rtol,
+                                      (pois && c->use_mg) ? &c->mg : nullptr);
     if (s == VIP_OK) s = gather_out(c, xp + off, x);
     if (s == VIP_OK && pois) {
         int64_t k = 0;

@@ -1,0 +1,724 @@
+// Learned warm start of the pressure-increment solve (Eq. 13): a 6-layer 3x3
+// convolutional network on the regular background lattice of each geometry
+// predicts the change of the increment, phi^{n+1} - phi^n, from the intermediate
+// velocity, the divergence right-hand side, the previous increment and node
+// masks.  The Krylov solve then runs from phi^n + S * prediction to the same
+// residual as without the network.
+//
+// Inputs per lattice cell (BF16, 16 channels): u*, v*, b / s_b, phi^n / S, 1 at a
+// node, 1 at a boundary node, zeros.  s_b = RMS of b over the geometry's interior
+// rows, S = RMS of phi^n (s_b h^2 before the first increment exists).
+//
+// Forward and data-gradient convolutions run on the tensor cores (vip_cnn_conv.cu);
+// the weight gradients are reduced in FP32 with fixed-order block partials; Adam
+// updates an FP32 master copy from which the BF16 MMA operands are repacked.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+
+#include "vip_cnn.cuh"
+
+namespace vip {
+
+constexpr int WG_THREADS = 256;
+
+// parameter offsets of layer l: weights [3][3][cin][cout_real] then bias [cout_real]
+struct ParamLayout {
+    int64_t w[CNN_LAYERS], b[CNN_LAYERS], total;
+    int cin[CNN_LAYERS], cout[CNN_LAYERS], creal[CNN_LAYERS];
+};
+static ParamLayout param_layout() {
+    ParamLayout p;
+    int64_t o = 0;
+    for (int l = 0; l < CNN_LAYERS; ++l) {
+        CnnLayerDims d = cnn_dims(l);
+        p.cin[l] = d.cin;
+        p.cout[l] = d.cout;
+        p.creal[l] = (l == CNN_LAYERS - 1) ? 1 : d.cout;
+        p.w[l] = o;
+        o += 9LL * d.cin * p.creal[l];
+        p.b[l] = o;
+        o += p.creal[l];
+    }
+    p.total = o;
+    return p;
+}
+
+// pack FP32 weights [3][3][cin][creal] into the MMA layout [tap][cin/8][cout][8]
+// (transpose = 1: the data-gradient operator, taps flipped, roles of cin/cout swapped)
+__global__ void k_pack(const float* __restrict__ w, int cin, int cout, int creal, int transpose,
+                       __nv_bfloat16* __restrict__ out) {
+    // forward: K = cin, N = cout; transposed: K = cout, N = cin
+    const int K = transpose ? cout : cin;
+    const int N = transpose ? cin : cout;
+    const int total = 9 * K * N;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        int tap = i / (K * N);
+        int rem = i - tap * K * N;
+        int chunk = rem / (N * 8);
+        int rem2 = rem - chunk * N * 8;
+        int n = rem2 / 8;
+        int kk = chunk * 8 + (rem2 % 8);
+        float v = 0.0f;
+        if (!transpose) {
+            if (n < creal) v = w[((int64_t)tap * cin + kk) * creal + n];
+        } else {  // W'[tap][co = kk][ci = n] = W[8 - tap][ci][co]
+            if (kk < creal) v = w[((int64_t)(8 - tap) * cin + n) * creal + kk];
+        }
+        out[i] = __float2bfloat16(v);
+    }
+}
+
+__global__ void k_pack_bias(const float* __restrict__ b, int creal, int cout, float* __restrict__ out) {
+    int i = threadIdx.x;
+    if (i < cout) out[i] = i < creal ? b[i] : 0.0f;
+}
+
+// per-geometry scales (one block per geometry, fixed order)
+__global__ void k_ws_scales(const GeomDev* __restrict__ g, const int8_t* __restrict__ rt,
+                            const uint8_t* __restrict__ kind, const double* __restrict__ b,
+                            const double* __restrict__ phi, const double* __restrict__ hlat,
+                            double* __restrict__ scales) {
+    __shared__ double sb[1024], sp[1024], sn[1024];
+    const GeomDev& G = g[blockIdx.x];
+    double a = 0, p = 0, n = 0;
+    for (int64_t r = G.row0 + threadIdx.x; r < G.row0 + G.n; r += blockDim.x) {
+        if (rt[r] != ROW_NODE) continue;
+        if (kind[r] == VIP_NODE_INTERIOR) { a += b[r] * b[r]; n += 1.0; }
+        p += phi[r] * phi[r];
+    }
+    sb[threadIdx.x] = a; sp[threadIdx.x] = p; sn[threadIdx.x] = n;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            sb[threadIdx.x] += sb[threadIdx.x + s];
+            sp[threadIdx.x] += sp[threadIdx.x + s];
+            sn[threadIdx.x] += sn[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double nn = fmax(sn[0], 1.0);
+        double s_b = sqrt(sb[0] / nn) + 1e-300;
+        double rp = sqrt(sp[0] / (double)G.n);
+        double S = rp > 0.0 ? rp : s_b * hlat[blockIdx.x] * hlat[blockIdx.x];
+        scales[2 * blockIdx.x] = s_b;
+        scales[2 * blockIdx.x + 1] = S;
+    }
+}
+
+// assemble the network input of every lattice cell (cells without a node stay zero)
+__global__ void k_ws_scatter(int64_t R, const int8_t* __restrict__ rt, const uint8_t* __restrict__ kind,
+                             const int32_t* __restrict__ rg, const int32_t* __restrict__ node_cell,
+                             const double* __restrict__ us, const double* __restrict__ vs,
+                             const double* __restrict__ b, const double* __restrict__ phi,
+                             const double* __restrict__ scales, __nv_bfloat16* __restrict__ x) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    int32_t c = node_cell[r];
+    if (c < 0 || rt[r] != ROW_NODE) return;
+    int g = rg[r];
+    double s_b = scales[2 * g], S = scales[2 * g + 1];
+    float v[CNN_CIN];
+    for (int i = 0; i < CNN_CIN; ++i) v[i] = 0.0f;
+    v[0] = (float)us[r];
+    v[1] = (float)vs[r];
+    v[2] = (float)(b[r] / s_b);
+    v[3] = (float)(phi[r] / S);
+    v[4] = 1.0f;
+    v[5] = kind[r] != VIP_NODE_INTERIOR ? 1.0f : 0.0f;
+    __nv_bfloat16* dst = x + (int64_t)c * CNN_CIN;
+    for (int i = 0; i < CNN_CIN; ++i) dst[i] = __float2bfloat16(v[i]);
+}
+
+// phi guess = phi^n + S * prediction at lattice nodes
+__global__ void k_ws_gather(int64_t R, const int8_t* __restrict__ rt, const int32_t* __restrict__ rg,
+                            const int32_t* __restrict__ node_cell, const float* __restrict__ y,
+                            const double* __restrict__ scales, double* __restrict__ phi) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    int32_t c = node_cell[r];
+    if (c < 0 || rt[r] != ROW_NODE) return;
+    phi[r] += scales[2 * rg[r] + 1] * (double)y[c];
+}
+
+// training target (phi^{n+1} - phi^n) / S and loss mask (interior lattice nodes)
+__global__ void k_ws_target(int64_t R, const int8_t* __restrict__ rt, const uint8_t* __restrict__ kind,
+                            const int32_t* __restrict__ rg, const int32_t* __restrict__ node_cell,
+                            const double* __restrict__ phi_new, const double* __restrict__ phi_old,
+                            const double* __restrict__ scales, float* __restrict__ tgt,
+                            float* __restrict__ mask) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    int32_t c = node_cell[r];
+    if (c < 0 || rt[r] != ROW_NODE) return;
+    tgt[c] = (float)((phi_new[r] - phi_old[r]) / scales[2 * rg[r] + 1]);
+    mask[c] = kind[r] == VIP_NODE_INTERIOR ? 1.0f : 0.0f;
+}
+
+// MSE loss and its gradient wrt the output channel 0: gy = 2 (y - t) m / count.
+// Block partials of the loss in fixed order.
+__global__ void k_loss(int64_t n, const float* __restrict__ y, const float* __restrict__ t,
+                       const float* __restrict__ m, double inv_cnt, __nv_bfloat16* __restrict__ gy,
+                       double* __restrict__ part) {
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        double d = (double)m[c] * ((double)y[c] - (double)t[c]);
+        acc += d * d;
+        __nv_bfloat16* g = gy + c * CNN_COUT;
+        g[0] = __float2bfloat16((float)(2.0 * d * inv_cnt));
+        for (int k = 1; k < CNN_COUT; ++k) g[k] = __float2bfloat16(0.0f);
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// Weight and bias gradients of one layer:
+//   dW[tap][ci][co] = sum_p x[p + off(tap)][ci] gy[p][co],  db[co] = sum_p gy[p][co].
+// Each block reduces its tiles into FP32 partials; k_wgrad_sum adds the partials.
+__global__ void __launch_bounds__(WG_THREADS) k_wgrad(const __nv_bfloat16* __restrict__ x,
+                                                      const __nv_bfloat16* __restrict__ gy,
+                                                      const CnnImage* __restrict__ img, int nimg,
+                                                      int64_t ntiles, int cin, int cout,
+                                                      float* __restrict__ part) {
+    __shared__ __nv_bfloat16 sx[3][CNN_TILE + 2][CNN_CH];
+    __shared__ __nv_bfloat16 sg[CNN_TILE][CNN_CH];
+    const int nent = 9 * cin * cout;
+    float acc[36];
+    float bacc = 0.0f;
+    for (int i = 0; i < 36; ++i) acc[i] = 0.0f;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int im = 0;
+        while (im + 1 < nimg && img[im + 1].tile0 <= tile) ++im;
+        const CnnImage I = img[im];
+        const int64_t tl = tile - I.tile0;
+        const int tpr = (I.W + CNN_TILE - 1) / CNN_TILE;
+        const int y = (int)(tl / tpr), x0 = (int)(tl % tpr) * CNN_TILE;
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * (CNN_TILE + 2) * cin; i += blockDim.x) {
+            int r = i / ((CNN_TILE + 2) * cin);
+            int rem = i - r * (CNN_TILE + 2) * cin;
+            int col = rem / cin, ci = rem % cin;
+            int yy = y - 1 + r, xx = x0 - 1 + col;
+            __nv_bfloat16 v = __float2bfloat16(0.0f);
+            if (yy >= 0 && yy < I.H && xx >= 0 && xx < I.W) v = x[(I.off + (int64_t)yy * I.W + xx) * cin + ci];
+            sx[r][col][ci] = v;
+        }
+        for (int i = threadIdx.x; i < CNN_TILE * cout; i += blockDim.x) {
+            int p = i / cout, co = i % cout;
+            int xx = x0 + p;
+            sg[p][co] = (xx < I.W) ? gy[(I.off + (int64_t)y * I.W + xx) * cout + co] : __float2bfloat16(0.0f);
+        }
+        __syncthreads();
+        for (int j = 0; j < 36; ++j) {
+            int e = threadIdx.x + j * WG_THREADS;
+            if (e >= nent) break;
+            int tap = e / (cin * cout);
+            int rem = e - tap * cin * cout;
+            int ci = rem / cout, co = rem % cout;
+            int dy = tap / 3, dx = tap % 3;
+            float s = 0.0f;
+            for (int p = 0; p < CNN_TILE; ++p)
+                s += __bfloat162float(sx[dy][p + dx][ci]) * __bfloat162float(sg[p][co]);
+            acc[j] += s;
+        }
+        if ((int)threadIdx.x < cout)
+            for (int p = 0; p < CNN_TILE; ++p) bacc += __bfloat162float(sg[p][threadIdx.x]);
+    }
+    float* dst = part + (int64_t)blockIdx.x * (nent + cout);
+    for (int j = 0; j < 36; ++j) {
+        int e = threadIdx.x + j * WG_THREADS;
+        if (e < nent) dst[e] = acc[j];
+    }
+    if ((int)threadIdx.x < cout) dst[nent + threadIdx.x] = bacc;
+}
+
+// sum block partials in block order into the gradient slots of the layer
+__global__ void k_wgrad_sum(const float* __restrict__ part, int nblocks, int cin, int cout, int creal,
+                            float* __restrict__ gw, float* __restrict__ gb) {
+    const int nent = 9 * cin * cout;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent + cout; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * (nent + cout) + e];
+        if (e < nent) {
+            int tap = e / (cin * cout);
+            int rem = e - tap * cin * cout;
+            int ci = rem / cout, co = rem % cout;
+            if (co < creal) gw[((int64_t)tap * cin + ci) * creal + co] = (float)s;
+        } else if (e - nent < creal) {
+            gb[e - nent] = (float)s;
+        }
+    }
+}
+
+__global__ void k_adam(int64_t n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.0f - b1) * gi;
+    float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+struct Cnn {
+    ParamLayout L;
+    float *params = nullptr, *grads = nullptr, *am = nullptr, *av = nullptr;
+    int adam_t = 0;
+    __nv_bfloat16* wp[CNN_LAYERS] = {};   // forward operands
+    __nv_bfloat16* wt[CNN_LAYERS] = {};   // data-gradient operands
+    float* bias[CNN_LAYERS] = {};         // padded to the MMA width
+    // lattice of the context's geometries
+    std::vector<CnnImage> himg;
+    CnnImage* img = nullptr;
+    int64_t ncells = 0, ntiles = 0;
+    int32_t* node_cell = nullptr;
+    double* hlat = nullptr;
+    double* scales = nullptr;
+    // activations of one pass: act[0] input, act[1..5] hidden, out (FP32), grads
+    __nv_bfloat16* act[CNN_LAYERS] = {};
+    float* out = nullptr;
+    __nv_bfloat16 *g0 = nullptr, *g1 = nullptr, *gl = nullptr;
+    float* wg_part = nullptr;
+    int wg_blocks = 0;
+    double* loss_part = nullptr;
+    int loss_blocks = 0;
+    double* phi_prev = nullptr;
+    // samples
+    int max_samples = 0, nsamples = 0;
+    int64_t loss_cnt = 0;           // interior lattice nodes (cells of the loss)
+    bool collect = false, enable = false;
+    __nv_bfloat16* s_in = nullptr;
+    float *s_tgt = nullptr, *s_mask = nullptr;
+    // test images (vip_cnn_forward / vip_cnn_grads)
+    CnnImage* timg = nullptr;
+};
+
+}  // namespace vip
+
+using namespace vip;
+
+namespace {
+
+Cnn* cnn_of(vip_ctx* c) { return reinterpret_cast<Cnn*>(c->cnn); }
+
+vip_status fail(vip_ctx* c, vip_status s, const char* m) {
+    c->err = m;
+    return s;
+}
+
+vip_status repack(vip_ctx* c, Cnn& N) {
+    for (int l = 0; l < CNN_LAYERS; ++l) {
+        k_pack<<<64, 256, 0, c->stream>>>(N.params + N.L.w[l], N.L.cin[l], N.L.cout[l], N.L.creal[l], 0,
+                                          N.wp[l]);
+        k_pack<<<64, 256, 0, c->stream>>>(N.params + N.L.w[l], N.L.cin[l], N.L.cout[l], N.L.creal[l], 1,
+                                          N.wt[l]);
+        k_pack_bias<<<1, 32, 0, c->stream>>>(N.params + N.L.b[l], N.L.creal[l], N.L.cout[l], N.bias[l]);
+    }
+    VIP_CUDA(cudaGetLastError());
+    return VIP_OK;
+}
+
+// forward over images `img` (ntiles tiles): act[0] holds the input
+vip_status forward(vip_ctx* c, Cnn& N, const CnnImage* img, int nimg, int64_t ntiles, __nv_bfloat16* in,
+                   cudaStream_t s) {
+    const __nv_bfloat16* x = in;
+    for (int l = 0; l < CNN_LAYERS; ++l) {
+        CnnConvArgs a;
+        memset(&a, 0, sizeof(a));
+        a.x = x;
+        a.wpack = N.wp[l];
+        a.bias = N.bias[l];
+        a.img = img;
+        a.nimg = nimg;
+        a.ntiles = ntiles;
+        a.cin = N.L.cin[l];
+        a.cout = N.L.cout[l];
+        a.status = c->d_status;
+        if (l == CNN_LAYERS - 1) {
+            a.epi = EPI_F32_CH0;
+            a.y32 = N.out;
+        } else {
+            a.epi = EPI_RELU_BF16;
+            a.y = N.act[l + 1];
+        }
+        VIP_CUDA(cnn_conv_fwd(a, c->num_sms, s));
+        x = N.act[l + 1];
+    }
+    return VIP_OK;
+}
+
+// gradients of the loss for the current act[] and out; fills N.grads
+vip_status backward(vip_ctx* c, Cnn& N, const CnnImage* img, int nimg, int64_t ntiles, __nv_bfloat16* in,
+                    cudaStream_t s) {
+    __nv_bfloat16* gy = N.gl;  // [cells][16] gradient wrt the last layer's output
+    __nv_bfloat16* bufs[2] = {N.g0, N.g1};
+    for (int l = CNN_LAYERS - 1; l >= 0; --l) {
+        const __nv_bfloat16* xin = (l == 0) ? in : N.act[l];
+        int cin = N.L.cin[l], cout = N.L.cout[l];
+        int nb = (int)std::min<int64_t>(ntiles, N.wg_blocks);
+        k_wgrad<<<nb, WG_THREADS, 0, s>>>(xin, gy, img, nimg, ntiles, cin, cout, N.wg_part);
+        k_wgrad_sum<<<64, 256, 0, s>>>(N.wg_part, nb, cin, cout, N.L.creal[l], N.grads + N.L.w[l],
+                                       N.grads + N.L.b[l]);
+        VIP_CUDA(cudaGetLastError());
+        if (l > 0) {  // gradient wrt the pre-activation of layer l-1
+            CnnConvArgs a;
+            memset(&a, 0, sizeof(a));
+            a.x = gy;
+            a.wpack = N.wt[l];
+            a.mask = N.act[l];
+            a.img = img;
+            a.nimg = nimg;
+            a.ntiles = ntiles;
+            a.cin = cout;
+            a.cout = cin;
+            a.epi = EPI_MASK_BF16;
+            a.y = bufs[l & 1];
+            a.status = c->d_status;
+            VIP_CUDA(cnn_conv_fwd(a, c->num_sms, s));
+            gy = bufs[l & 1];
+        }
+    }
+    return VIP_OK;
+}
+
+vip_status loss_grad(vip_ctx* c, Cnn& N, int64_t off, int64_t n, const float* tgt, const float* mask,
+                     double cnt, double* loss_out, cudaStream_t s) {
+    int nb = N.loss_blocks;
+    k_loss<<<nb, 256, 0, s>>>(n, N.out + off, tgt, mask, 1.0 / std::max(cnt, 1.0), N.gl + off * CNN_COUT,
+                              N.loss_part);
+    VIP_CUDA(cudaGetLastError());
+    if (loss_out) {
+        std::vector<double> part(nb);
+        VIP_CUDA(cudaMemcpyAsync(part.data(), N.loss_part, nb * 8, cudaMemcpyDeviceToHost, s));
+        VIP_CUDA(cudaStreamSynchronize(s));
+        double L = 0;
+        for (double v : part) L += v;
+        *loss_out = L / std::max(cnt, 1.0);
+    }
+    return VIP_OK;
+}
+
+vip_status adam(vip_ctx* c, Cnn& N, double lr, cudaStream_t s) {
+    N.adam_t++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    float c1 = 1.0f - powf(b1, (float)N.adam_t), c2 = 1.0f - powf(b2, (float)N.adam_t);
+    k_adam<<<nblk(N.L.total, 256), 256, 0, s>>>(N.L.total, N.params, N.grads, N.am, N.av, (float)lr, b1, b2,
+                                                1e-8f, c1, c2);
+    VIP_CUDA(cudaGetLastError());
+    return repack(c, N);
+}
+
+vip_status ensure_act(vip_ctx* c, Cnn& N, int64_t ncells) {
+    // activation buffers sized for max(ncells of the context, test images)
+    static_assert(CNN_CH >= CNN_COUT, "");
+    if (N.ncells >= ncells && N.act[0]) return VIP_OK;
+    N.ncells = std::max(N.ncells, ncells);
+    for (int l = 0; l < CNN_LAYERS; ++l) VIP_CUDA(dalloc(c, &N.act[l], (size_t)N.ncells * CNN_CH));
+    VIP_CUDA(dalloc(c, &N.out, N.ncells));
+    VIP_CUDA(dalloc(c, &N.g0, (size_t)N.ncells * CNN_CH));
+    VIP_CUDA(dalloc(c, &N.g1, (size_t)N.ncells * CNN_CH));
+    VIP_CUDA(dalloc(c, &N.gl, (size_t)N.ncells * CNN_COUT));
+    return VIP_OK;
+}
+
+}  // namespace
+
+namespace vip {
+
+// Create the network state (random init with the given seed) and the lattice of
+// the context's geometries.  Called from vip_build.
+vip_status cnn_setup(vip_ctx* c, uint64_t seed) {
+    Cnn* N = new Cnn();
+    c->cnn = N;
+    N->L = param_layout();
+    const int64_t P = N->L.total;
+    VIP_CUDA(dalloc(c, &N->params, P));
+    VIP_CUDA(dalloc(c, &N->grads, P));
+    VIP_CUDA(dalloc(c, &N->am, P));
+    VIP_CUDA(dalloc(c, &N->av, P));
+    VIP_CUDA(cudaMemsetAsync(N->am, 0, P * 4, c->stream));
+    VIP_CUDA(cudaMemsetAsync(N->av, 0, P * 4, c->stream));
+    VIP_CUDA(cudaMemsetAsync(N->grads, 0, P * 4, c->stream));
+    {   // He-style initialisation, last layer zero so that the untrained network
+        // reproduces the previous-increment guess exactly
+        std::vector<float> h(P, 0.0f);
+        std::mt19937_64 rng(seed);
+        std::normal_distribution<float> nd(0.0f, 1.0f);
+        for (int l = 0; l < CNN_LAYERS - 1; ++l) {
+            float sd = sqrtf(2.0f / (9.0f * N->L.cin[l]));
+            for (int64_t i = 0; i < 9LL * N->L.cin[l] * N->L.creal[l]; ++i) h[N->L.w[l] + i] = sd * nd(rng);
+        }
+        VIP_CUDA(cudaMemcpy(N->params, h.data(), P * 4, cudaMemcpyHostToDevice));
+    }
+    for (int l = 0; l < CNN_LAYERS; ++l) {
+        VIP_CUDA(dalloc(c, &N->wp[l], 9 * N->L.cin[l] * N->L.cout[l]));
+        VIP_CUDA(dalloc(c, &N->wt[l], 9 * N->L.cin[l] * N->L.cout[l]));
+        VIP_CUDA(dalloc(c, &N->bias[l], CNN_CH));
+    }
+    VIP_CUDA(cnn_conv_init());
+    vip_status st = repack(c, *N);
+    if (st != VIP_OK) return st;
+    // lattice per geometry: spacing = smallest local spacing, origin = lower-left node
+    const int G = (int)c->geoms.size();
+    int64_t off = 0, tile0 = 0;
+    std::vector<double> hl(G);
+    std::vector<int32_t> cell(c->R, -1);
+    for (int g = 0; g < G; ++g) {
+        const Geom& gg = c->geoms[g];
+        double h = 1e300, x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
+        for (int64_t i = gg.off; i < gg.off + gg.n; ++i) {
+            h = std::min(h, c->hh[i]);
+            x0 = std::min(x0, c->hx[i]); x1 = std::max(x1, c->hx[i]);
+            y0 = std::min(y0, c->hy[i]); y1 = std::max(y1, c->hy[i]);
+        }
+        int W = (int)llround((x1 - x0) / h) + 1, H = (int)llround((y1 - y0) / h) + 1;
+        CnnImage I;
+        I.off = off;
+        I.H = H;
+        I.W = W;
+        I.tile0 = tile0;
+        N->himg.push_back(I);
+        hl[g] = h;
+        for (int64_t i = 0; i < gg.n; ++i) {
+            double fx = (c->hx[gg.off + i] - x0) / h, fy = (c->hy[gg.off + i] - y0) / h;
+            long long ix = llround(fx), iy = llround(fy);
+            if (std::fabs(fx - ix) < 1e-6 && std::fabs(fy - iy) < 1e-6 && ix >= 0 && ix < W && iy >= 0 &&
+                iy < H) {
+                cell[gg.row0 + i] = (int32_t)(off + iy * W + ix);
+                if (c->hkind[gg.off + i] == VIP_NODE_INTERIOR) N->loss_cnt++;
+            }
+        }
+        off += (int64_t)W * H;
+        tile0 += (int64_t)H * ((W + CNN_TILE - 1) / CNN_TILE);
+    }
+    N->ntiles = tile0;
+    VIP_CUDA(dalloc(c, &N->img, G));
+    VIP_CUDA(cudaMemcpy(N->img, N->himg.data(), G * sizeof(CnnImage), cudaMemcpyHostToDevice));
+    VIP_CUDA(dalloc(c, &N->node_cell, c->R));
+    VIP_CUDA(cudaMemcpy(N->node_cell, cell.data(), c->R * 4, cudaMemcpyHostToDevice));
+    VIP_CUDA(dalloc(c, &N->hlat, G));
+    VIP_CUDA(cudaMemcpy(N->hlat, hl.data(), G * 8, cudaMemcpyHostToDevice));
+    VIP_CUDA(dalloc(c, &N->scales, 2 * G));
+    VIP_CUDA(dalloc(c, &N->phi_prev, c->R));
+    st = ensure_act(c, *N, off);
+    if (st != VIP_OK) return st;
+    N->ncells = off;
+    N->wg_blocks = std::max(1, c->num_sms * 2);
+    VIP_CUDA(dalloc(c, &N->wg_part, (size_t)N->wg_blocks * (9 * CNN_CH * CNN_CH + CNN_CH)));
+    N->loss_blocks = 256;
+    VIP_CUDA(dalloc(c, &N->loss_part, N->loss_blocks));
+    VIP_CUDA(dalloc(c, &N->timg, 1));
+    VIP_CUDA(cudaStreamSynchronize(c->stream));
+    return VIP_OK;
+}
+
+void cnn_free(vip_ctx* c) {
+    delete cnn_of(c);
+    c->cnn = nullptr;
+}
+
+// Warm start of the Poisson solve: called inside the step after the divergence.
+vip_status cnn_warm_start(vip_ctx* c, cudaStream_t s) {
+    Cnn* N = cnn_of(c);
+    if (!N || (!N->enable && !N->collect)) return VIP_OK;
+    const int64_t R = c->R;
+    VIP_CUDA(cudaMemcpyAsync(N->phi_prev, c->phi, R * 8, cudaMemcpyDeviceToDevice, s));
+    k_ws_scales<<<(unsigned)c->geoms.size(), 1024, 0, s>>>(c->gdev, c->row_type, c->kind, c->prhs, c->phi,
+                                                          N->hlat, N->scales);
+    VIP_CUDA(cudaMemsetAsync(N->act[0], 0, (size_t)N->ncells * CNN_CIN * 2, s));
+    k_ws_scatter<<<nblk(R, 256), 256, 0, s>>>(R, c->row_type, c->kind, c->row_geom, N->node_cell, c->hsol,
+                                               c->hsol + R, c->prhs, c->phi, N->scales, N->act[0]);
+    VIP_CUDA(cudaGetLastError());
+    if (N->enable) {
+        vip_status st = forward(c, *N, N->img, (int)N->himg.size(), N->ntiles, N->act[0], s);
+        if (st != VIP_OK) return st;
+        k_ws_gather<<<nblk(R, 256), 256, 0, s>>>(R, c->row_type, c->row_geom, N->node_cell, N->out, N->scales,
+                                                  c->phi);
+        VIP_CUDA(cudaGetLastError());
+    }
+    return VIP_OK;
+}
+
+// After the solve: store (input, target) when collecting.
+vip_status cnn_after_solve(vip_ctx* c, cudaStream_t s) {
+    Cnn* N = cnn_of(c);
+    if (!N || !N->collect || N->nsamples >= N->max_samples) return VIP_OK;
+    const int64_t nc = N->ncells;
+    const int k = N->nsamples;
+    VIP_CUDA(cudaMemcpyAsync(N->s_in + (int64_t)k * nc * CNN_CIN, N->act[0], nc * CNN_CIN * 2,
+                             cudaMemcpyDeviceToDevice, s));
+    VIP_CUDA(cudaMemsetAsync(N->s_tgt + (int64_t)k * nc, 0, nc * 4, s));
+    VIP_CUDA(cudaMemsetAsync(N->s_mask + (int64_t)k * nc, 0, nc * 4, s));
+    k_ws_target<<<nblk(c->R, 256), 256, 0, s>>>(c->R, c->row_type, c->kind, c->row_geom, N->node_cell, c->phi,
+                                                 N->phi_prev, N->scales, N->s_tgt + (int64_t)k * nc,
+                                                 N->s_mask + (int64_t)k * nc);
+    VIP_CUDA(cudaGetLastError());
+    N->nsamples++;
+    return VIP_OK;
+}
+
+bool cnn_collecting(vip_ctx* c) {
+    Cnn* N = cnn_of(c);
+    return N && N->collect;
+}
+
+}  // namespace vip
+
+extern "C" {
+
+vip_status vip_ws_collect(vip_ctx* c, int enable, int32_t max_samples) {
+    if (!c) return VIP_ERR_ARG;
+    if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_collect before vip_build");
+    Cnn& N = *cnn_of(c);
+    if (enable) {
+        if (max_samples < 1) return fail(c, VIP_ERR_ARG, "max_samples must be >= 1");
+        if (max_samples > N.max_samples) {
+            VIP_CUDA(dalloc(c, &N.s_in, (size_t)max_samples * N.ncells * CNN_CIN));
+            VIP_CUDA(dalloc(c, &N.s_tgt, (size_t)max_samples * N.ncells));
+            VIP_CUDA(dalloc(c, &N.s_mask, (size_t)max_samples * N.ncells));
+            N.max_samples = max_samples;
+        }
+        N.nsamples = 0;
+    }
+    N.collect = enable != 0;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return VIP_OK;
+}
+
+vip_status vip_ws_enable(vip_ctx* c, int enable) {
+    if (!c) return VIP_ERR_ARG;
+    if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_enable before vip_build");
+    cnn_of(c)->enable = enable != 0;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+    return VIP_OK;
+}
+
+vip_status vip_ws_train(vip_ctx* c, vip_train_cfg* cfg) {
+    if (!c || !cfg) return VIP_ERR_ARG;
+    if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_train before vip_build");
+    Cnn& N = *cnn_of(c);
+    if (N.nsamples < 1) return fail(c, VIP_ERR_ARG, "no collected samples");
+    if (cfg->epochs < 1 || !(cfg->lr > 0)) return fail(c, VIP_ERR_ARG, "bad training settings");
+    cudaStream_t s = c->stream;
+    std::mt19937_64 rng(cfg->seed);
+    std::vector<int> order(N.nsamples);
+    for (int i = 0; i < N.nsamples; ++i) order[i] = i;
+    const int64_t nc = N.ncells;
+    const CnnImage* img = N.img;
+    const int nimg = (int)N.himg.size();
+    double last = 0.0;
+    for (int ep = 0; ep < cfg->epochs; ++ep) {
+        std::shuffle(order.begin(), order.end(), rng);
+        double sum = 0.0;
+        for (int k : order) {
+            __nv_bfloat16* in = N.s_in + (int64_t)k * nc * CNN_CIN;
+            vip_status st = forward(c, N, img, nimg, N.ntiles, in, s);
+            if (st != VIP_OK) return st;
+            double cnt = (double)N.loss_cnt;
+            double L = 0.0;
+            st = loss_grad(c, N, 0, nc, N.s_tgt + (int64_t)k * nc, N.s_mask + (int64_t)k * nc, cnt, &L, s);
+            if (st != VIP_OK) return st;
+            st = backward(c, N, img, nimg, N.ntiles, in, s);
+            if (st != VIP_OK) return st;
+            st = adam(c, N, cfg->lr, s);
+            if (st != VIP_OK) return st;
+            sum += L;
+        }
+        last = sum / N.nsamples;
+        if (ep == 0) cfg->first_loss = last;
+    }
+    cfg->final_loss = last;
+    VIP_CUDA(cudaStreamSynchronize(s));
+    int32_t hs = 0;
+    VIP_CUDA(cudaMemcpy(&hs, c->d_status, 4, cudaMemcpyDeviceToHost));
+    if (hs) return fail(c, (vip_status)hs, "device error during training");
+    return VIP_OK;
+}
+
+vip_status vip_ws_params(vip_ctx* c, int direction, float* buf, int64_t* count) {
+    if (!c) return VIP_ERR_ARG;
+    if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_params before vip_build");
+    Cnn& N = *cnn_of(c);
+    if (count) *count = N.L.total;
+    if (!buf) return VIP_OK;
+    if (direction == 0) {
+        VIP_CUDA(cudaMemcpy(buf, N.params, N.L.total * 4, cudaMemcpyDefault));
+    } else {
+        VIP_CUDA(cudaMemcpy(N.params, buf, N.L.total * 4, cudaMemcpyDefault));
+        N.adam_t = 0;
+        VIP_CUDA(cudaMemset(N.am, 0, N.L.total * 4));
+        VIP_CUDA(cudaMemset(N.av, 0, N.L.total * 4));
+        vip_status st = repack(c, N);
+        if (st != VIP_OK) return st;
+        VIP_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    return VIP_OK;
+}
+
+vip_status vip_ws_eval(vip_ctx* c, int32_t H, int32_t W, const float* x, float* y, float* grads,
+                       const float* target, const float* mask, double* loss) {
+    if (!c || !x || H < 1 || W < 1) return VIP_ERR_ARG;
+    if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_eval before vip_build");
+    Cnn& N = *cnn_of(c);
+    const int64_t n = (int64_t)H * W;
+    vip_status st = ensure_act(c, N, n);
+    if (st != VIP_OK) return st;
+    cudaStream_t s = c->stream;
+    CnnImage I;
+    I.off = 0; I.H = H; I.W = W; I.tile0 = 0;
+    VIP_CUDA(cudaMemcpyAsync(N.timg, &I, sizeof(I), cudaMemcpyHostToDevice, s));
+    int64_t ntiles = (int64_t)H * ((W + CNN_TILE - 1) / CNN_TILE);
+    // input: FP32 [H][W][16] -> BF16
+    std::vector<float> hx(n * CNN_CIN);
+    VIP_CUDA(cudaMemcpy(hx.data(), x, n * CNN_CIN * 4, cudaMemcpyDefault));
+    std::vector<__nv_bfloat16> hb(n * CNN_CIN);
+    for (int64_t i = 0; i < n * CNN_CIN; ++i) hb[i] = __float2bfloat16(hx[i]);
+    __nv_bfloat16* in = nullptr;
+    VIP_CUDA(cudaMalloc(&in, n * CNN_CIN * 2));
+    VIP_CUDA(cudaMemcpyAsync(in, hb.data(), n * CNN_CIN * 2, cudaMemcpyHostToDevice, s));
+    st = forward(c, N, N.timg, 1, ntiles, in, s);
+    if (st == VIP_OK && y) VIP_CUDA(cudaMemcpyAsync(y, N.out, n * 4, cudaMemcpyDefault, s));
+    if (st == VIP_OK && grads && target && mask) {
+        float *dt = nullptr, *dm = nullptr;
+        VIP_CUDA(cudaMalloc(&dt, n * 4));
+        VIP_CUDA(cudaMalloc(&dm, n * 4));
+        VIP_CUDA(cudaMemcpyAsync(dt, target, n * 4, cudaMemcpyDefault, s));
+        VIP_CUDA(cudaMemcpyAsync(dm, mask, n * 4, cudaMemcpyDefault, s));
+        std::vector<float> hmk(n);
+        VIP_CUDA(cudaMemcpy(hmk.data(), mask, n * 4, cudaMemcpyDefault));
+        double cnt = 0;
+        for (float v : hmk) cnt += v != 0.0f;
+        st = loss_grad(c, N, 0, n, dt, dm, cnt, loss, s);
+        if (st == VIP_OK) st = backward(c, N, N.timg, 1, ntiles, in, s);
+        if (st == VIP_OK) VIP_CUDA(cudaMemcpyAsync(grads, N.grads, N.L.total * 4, cudaMemcpyDefault, s));
+        VIP_CUDA(cudaStreamSynchronize(s));
+        cudaFree(dt);
+        cudaFree(dm);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    cudaFree(in);
+    if (st != VIP_OK) return st;
+    if (e != cudaSuccess) return fail(c, VIP_ERR_CUDA, cudaGetErrorString(e));
+    int32_t hs = 0;
+    VIP_CUDA(cudaMemcpy(&hs, c->d_status, 4, cudaMemcpyDeviceToHost));
+    if (hs) return fail(c, (vip_status)hs, "device error in the network kernels");
+    return VIP_OK;
+}
+
+}  // extern "C"

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/vip.h"
+#include "vip_mg.cuh"
 
 namespace vip {
 
@@ -153,10 +154,20 @@ struct vip_ctx {
     // Krylov plans and workspaces
     vip::KrylovPlan plan_helm, plan_pois;
     vip::KrylovWork work64, work32;
+    vip::Multigrid mg;             // preconditioner of the pressure-increment solve
+    bool use_mg = true;
+    void* cnn = nullptr;           // warm-start network state (vip_cnn.cu)
+    void* phat = nullptr;          // preconditioned search directions [2R] (FP64 size)
+    void* shat = nullptr;
     // per-step statistics on the device
-    int64_t* d_stats = nullptr;     // [4] total inner iters (poisson), steps, ...
+    int64_t* d_stats = nullptr;     // [4] poisson inner iters, steps, poisson outer, helm iters
     cudaGraphExec_t graph = nullptr;
     int64_t host_steps = 0;
+    // phase events recorded inside every step (also inside the graph)
+    cudaEvent_t ev[VIP_PHASE_COUNT + 1] = {};
+    bool profiling = false;
+    double prof_ms[VIP_PHASE_COUNT] = {0, 0, 0, 0, 0};
+    int64_t prof_steps = 0;
     std::vector<void*> allocs;
 };
 
@@ -168,7 +179,15 @@ vip_status krylov_plan(vip_ctx* c, KrylovPlan& plan, const Sell& A,
                        const std::vector<int64_t>& sys_row0, const std::vector<int64_t>& sys_rows);
 vip_status krylov_solve(vip_ctx* c, const KrylovPlan& plan, const Sell& A, const double* b,
                         double* x, int precision, double rtol, int32_t max_iters,
-                        double inner_rtol);
+                        double inner_rtol, const Multigrid* mg = nullptr);
+// multigrid (vip_mg.cu)
+vip_status mg_build(vip_ctx* c, Multigrid& M);
+// warm-start network (vip_cnn.cu)
+vip_status cnn_setup(vip_ctx* c, uint64_t seed);
+void cnn_free(vip_ctx* c);
+vip_status cnn_warm_start(vip_ctx* c, cudaStream_t s);
+vip_status cnn_after_solve(vip_ctx* c, cudaStream_t s);
+bool cnn_collecting(vip_ctx* c);
 // step kernels (vip_step.cu)
 void launch_conv_rhs(vip_ctx* c, cudaStream_t s);
 void launch_div(vip_ctx* c, cudaStream_t s);

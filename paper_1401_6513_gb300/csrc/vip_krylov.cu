@@ -18,13 +18,14 @@
 // block order by every block, so all blocks hold identical scalars.  Blocks
 // meet at a grid barrier whose wait is bounded (2 s, then VIP_ERR_TIMEOUT).
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "vip_internal.cuh"
 
 namespace vip {
 
-constexpr int KTHREADS = 512;
+constexpr int KTHREADS = 1024;
 constexpr int KWARPS = KTHREADS / 32;
 constexpr int MAXSYS = 128;
 
@@ -86,21 +87,25 @@ struct KArgs {
     const int32_t* blk_s0;
     const int32_t* blk_s1;
     const int32_t* blk_g0;
+    const int32_t* blk_ng;
     const int32_t* sys_b0;
     const int32_t* sys_b1;
-    double* partial;
+    double* partial;     // [nsys][NQ][nblocks], zero where a block has no rows of a system
     uint32_t* bar;
     int nsys;
     const double* b;
     double* x;
     T *r, *rhat, *p, *v, *s, *t, *dx;
     double rtol, inner_rtol;
-    int max_iters, max_outer;
+    int max_iters, max_outer, max_pass;
     int32_t* out_iters;
     int32_t* out_outer;
     double* out_relres;
     int32_t* out_status;
     int32_t* status;
+    int use_mg;          // right preconditioning by one multigrid V-cycle
+    MgDev<T> mg;
+    T *phat, *shat;      // M^{-1} p and M^{-1} s (alias p and s without a preconditioner)
 };
 
 struct SysState {
@@ -109,8 +114,15 @@ struct SysState {
     int inner_active;  // inside a BiCGSTAB pass
     int s_conv;        // ||s|| met the inner tolerance this iteration
     int zero_x;        // b == 0: set x = 0
+    int pass_bad;      // the pass produced a non-finite or diverging correction: discard it
+    int bad_passes;    // consecutive discarded passes
+    double r0_in;      // ||r|| at the start of the pass
+    int pass_cap;      // iteration cap of the current pass (halved after a discarded pass)
     int iters, outer, pass_iters, status;
 };
+
+// A reduced value is usable if finite.
+__device__ __forceinline__ bool fin(double v) { return isfinite(v); }
 
 template <class T>
 __device__ __forceinline__ T ldv(const T* p) { return __ldcg(p); }
@@ -124,6 +136,9 @@ __device__ __forceinline__ double wsum(double v) {
 
 template <class T>
 __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
+    // |r_hat . r| below this fraction of ||r_hat|| ||r|| is rounding noise in T
+    // (FP32 vectors of ~1e6 rows: ~6e-8 / sqrt(n) relative noise in a dot product)
+    const double bd_tol = sizeof(T) == 8 ? 1e-14 : 1e-9;
     __shared__ double sacc[KWARPS][MAXSYS_PB][NQ];
     __shared__ double stot[MAXSYS][NQ];
     __shared__ SysState S[MAXSYS];
@@ -146,22 +161,27 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
             if (lane == 0) sacc[warp][j][k] += w;
         }
     };
-    // block partials -> global, barrier, totals of every system -> stot
+    // block partials -> global, barrier, totals of every system -> stot.
+    // Layout partial[(g * NQ + k) * nb + block]: the blocks of one system are a
+    // contiguous run, summed by one warp (lanes stride over blocks, then a fixed
+    // butterfly), so the order is fixed and the loads are independent.
+    const int ng_blk = a.blk_ng[bid];
     auto reduce = [&](int nq) -> bool {
         __syncthreads();
-        for (int i = threadIdx.x; i < MAXSYS_PB * nq; i += KTHREADS) {
+        for (int i = threadIdx.x; i < ng_blk * nq; i += KTHREADS) {
             int j = i / nq, k = i % nq;
             double sum = 0.0;
             for (int w = 0; w < KWARPS; ++w) sum += sacc[w][j][k];
-            __stcg(&a.partial[((int64_t)bid * MAXSYS_PB + j) * NQ + k], sum);
+            __stcg(&a.partial[((int64_t)(g0 + j) * NQ + k) * nb + bid], sum);
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
-        for (int i = threadIdx.x; i < nsys * nq; i += KTHREADS) {
+        for (int i = warp; i < nsys * nq; i += KWARPS) {
             int g = i / nq, k = i % nq;
+            const double* src = a.partial + ((int64_t)g * NQ + k) * nb;
             double sum = 0.0;
-            for (int bb = a.sys_b0[g]; bb < a.sys_b1[g]; ++bb)
-                sum += __ldcg(&a.partial[((int64_t)bb * MAXSYS_PB + (g - a.blk_g0[bb])) * NQ + k]);
-            stot[g][k] = sum;
+            for (int bb = a.sys_b0[g] + lane; bb < a.sys_b1[g]; bb += 32) sum += __ldcg(src + bb);
+            sum = wsum(sum);
+            if (lane == 0) stot[g][k] = sum;
         }
         __syncthreads();
         return true;
@@ -187,11 +207,117 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
         return sum;
     };
 
+    // One V-cycle z = M^{-1} v of the aggregation multigrid: damped Jacobi from zero on
+    // the fine rows, fine residual, restriction (sum over the cell's rows), then on each
+    // coarse level a Jacobi step from zero, its residual and restriction; Jacobi sweeps
+    // on the coarsest level by block 0; back up with piecewise-constant prolongation
+    // and one Jacobi post-smoothing step per level.  Only rows of systems still in
+    // their inner pass are touched on the fine level.
+    const int64_t gtid = (int64_t)blockIdx.x * KTHREADS + threadIdx.x;
+    const int64_t gstride = (int64_t)nb * KTHREADS;
+    auto coarse_res = [&](int l, int64_t c, const T* xv) -> double {
+        const MgDev<T>& M = a.mg;
+        const int64_t n = M.n[l];
+        double acc = (double)ldv(M.b[l] + c);
+        for (int o = 0; o < 25; ++o) {
+            int32_t j = __ldg(M.nbr[l] + (int64_t)o * n + c);
+            if (j >= 0) acc -= (double)__ldg(M.coef[l] + (int64_t)o * n + c) * (double)ldv(xv + j);
+        }
+        return acc;
+    };
+    auto vcycle = [&](const T* in, T* out) -> bool {
+        const MgDev<T>& M = a.mg;
+        const double w = M.omega;
+        const int L = M.nlev;
+        for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+            int g = a.slice_sys[sl];
+            int64_t row = (int64_t)sl * 32 + lane;
+            T z = (T)0;
+            if (S[g].inner_active) z = (T)(w * (double)__ldg(M.fdinv + row) * (double)ldv(in + row));
+            M.fx[row] = z;
+        }
+        if (!grid_sync(a.bar, nb, a.status)) return false;
+        for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+            int g = a.slice_sys[sl];
+            int64_t row = (int64_t)sl * 32 + lane;
+            T res = (T)0;
+            if (S[g].inner_active) res = (T)((double)ldv(in + row) - spmv_row(sl, a.aT, M.fx));
+            M.fr[row] = res;
+        }
+        if (!grid_sync(a.bar, nb, a.status)) return false;
+        for (int64_t c = gtid; c < M.n[1]; c += gstride) {
+            double sum = 0.0;
+            for (int64_t q = __ldg(M.cptr + c); q < __ldg(M.cptr + c + 1); ++q)
+                sum += (double)ldv(M.fr + __ldg(M.crow + q));
+            M.b[1][c] = (T)sum;
+            M.x[1][c] = (T)(w * (double)__ldg(M.dinv[1] + c) * sum);
+        }
+        if (!grid_sync(a.bar, nb, a.status)) return false;
+        for (int l = 1; l < L; ++l) {
+            for (int64_t c = gtid; c < M.n[l]; c += gstride) M.y[l][c] = (T)coarse_res(l, c, M.x[l]);
+            if (!grid_sync(a.bar, nb, a.status)) return false;
+            const int64_t nc = M.n[l + 1];
+            for (int64_t C = gtid; C < nc; C += gstride) {
+                double sum = 0.0;
+                for (int k = 0; k < 4; ++k) {
+                    int64_t ch = __ldg(M.child[l + 1] + (int64_t)k * nc + C);
+                    if (ch >= 0) sum += (double)ldv(M.y[l] + ch);
+                }
+                M.b[l + 1][C] = (T)sum;
+                M.x[l + 1][C] = (T)(w * (double)__ldg(M.dinv[l + 1] + C) * sum);
+            }
+            if (!grid_sync(a.bar, nb, a.status)) return false;
+        }
+        // coarsest level: exact solve x_L = A_L^{-1} b_L with each geometry's dense FP64
+        // inverse (one row per thread of the grid)
+        for (int gg = 0; gg < M.ngeom; ++gg) {
+            const int64_t c0 = __ldg(M.coff + gg);
+            const int64_t m = ((gg + 1 < M.ngeom) ? __ldg(M.coff + gg + 1) : M.n[L]) - c0;
+            const double* Ai = M.cinv + __ldg(M.cinv_off + gg);
+            for (int64_t i = gtid; i < m; i += gstride) {
+                double sum = 0.0;
+                for (int64_t j = 0; j < m; ++j) sum += __ldg(Ai + i * m + j) * (double)ldv(M.b[L] + c0 + j);
+                M.x[L][c0 + i] = (T)sum;
+            }
+        }
+        if (!grid_sync(a.bar, nb, a.status)) return false;
+        // the corrected solution of level l is x_L on the coarsest level, y_l above it
+        for (int l = L - 1; l >= 1; --l) {
+            const T* sol = (l + 1 == L) ? M.x[l + 1] : M.y[l + 1];
+            for (int64_t c = gtid; c < M.n[l]; c += gstride)
+                M.x[l][c] = (T)((double)ldv(M.x[l] + c) +
+                                (double)M.corr * (double)ldv(sol + __ldg(M.parent[l] + c)));
+            if (!grid_sync(a.bar, nb, a.status)) return false;
+            for (int64_t c = gtid; c < M.n[l]; c += gstride)
+                M.y[l][c] = (T)((double)ldv(M.x[l] + c) +
+                                w * (double)__ldg(M.dinv[l] + c) * coarse_res(l, c, M.x[l]));
+            if (!grid_sync(a.bar, nb, a.status)) return false;
+        }
+        const T* sol1 = (L == 1) ? M.x[1] : M.y[1];
+        for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+            int g = a.slice_sys[sl];
+            if (!S[g].inner_active) continue;
+            int64_t row = (int64_t)sl * 32 + lane;
+            int32_t c = __ldg(M.agg + row);
+            if (c >= 0) M.fx[row] = (T)((double)ldv(M.fx + row) + (double)M.corr * (double)ldv(sol1 + c));
+        }
+        if (!grid_sync(a.bar, nb, a.status)) return false;
+        for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+            int g = a.slice_sys[sl];
+            if (!S[g].inner_active) continue;
+            int64_t row = (int64_t)sl * 32 + lane;
+            double r = (double)ldv(in + row) - spmv_row(sl, a.aT, M.fx);
+            out[row] = (T)((double)ldv(M.fx + row) + w * (double)__ldg(M.fdinv + row) * r);
+        }
+        return grid_sync(a.bar, nb, a.status);
+    };
+
     if (threadIdx.x < nsys) {
         SysState& st = S[threadIdx.x];
         st.bnorm = -1.0; st.rnorm = 0; st.tol = 0; st.rho = st.rho_old = st.alpha = st.omega = 1.0;
         st.beta = 0; st.rhat_norm = 0; st.relres = 0;
         st.outer_active = 1; st.inner_active = 0; st.s_conv = 0; st.zero_x = 0;
+        st.pass_bad = 0; st.bad_passes = 0; st.r0_in = 0; st.pass_cap = a.max_pass;
         st.iters = 0; st.outer = 0; st.pass_iters = 0; st.status = 0;
     }
     __syncthreads();
@@ -204,7 +330,8 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 int g = a.slice_sys[sl];
                 int64_t row = (int64_t)sl * 32 + lane;
                 if (S[g].zero_x) a.x[row] = 0.0;
-                else if (S[g].outer_active) a.x[row] = __ldcg(a.x + row) + (double)ldv(a.dx + row);
+                else if (S[g].outer_active && !S[g].pass_bad)
+                    a.x[row] = __ldcg(a.x + row) + (double)ldv(a.dx + row);
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
         }
@@ -245,17 +372,24 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                         st.outer_active = 0;
                     } else if (st.iters >= a.max_iters || st.outer >= a.max_outer) {
                         st.status = VIP_ERR_NOT_CONVERGED; st.outer_active = 0;
-                    } else if (st.outer > 0 && st.pass_iters == 0) {
+                    } else if (st.outer > 0 && st.pass_iters == 0 && !st.pass_bad) {
                         st.status = VIP_ERR_BREAKDOWN; st.outer_active = 0;
+                    } else if (st.bad_passes >= 3) {
+                        st.status = VIP_ERR_NONFINITE; st.outer_active = 0;
                     } else {
                         st.inner_active = 1;
                         st.outer += 1;
-                        st.pass_iters = 0;
                         double t_abs = 0.5 * a.rtol * st.bnorm;
                         st.tol = (sizeof(T) == 8) ? t_abs : fmax(a.inner_rtol * st.rnorm, t_abs);
                         st.rho = stot[threadIdx.x][2];
                         st.rhat_norm = sqrt(st.rho);
+                        st.r0_in = st.rhat_norm;
                         st.rho_old = st.alpha = st.omega = 1.0;
+                        st.bad_passes = st.pass_bad ? st.bad_passes + 1 : 0;
+                        st.pass_cap = st.pass_bad ? max(st.pass_iters / 2, 20)
+                                                  : min(2 * st.pass_cap, a.max_pass);
+                        st.pass_bad = 0;
+                        st.pass_iters = 0;
                     }
                 }
             }
@@ -296,13 +430,14 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 a.p[row] = (T)pn;
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
-            // B: v = A p, rhat . v
+            if (a.use_mg && !vcycle(a.p, a.phat)) { alive = false; break; }
+            // B: v = A phat, rhat . v
             clear_acc();
             for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
-                double vi = spmv_row(sl, a.aT, a.p);
+                double vi = spmv_row(sl, a.aT, a.phat);
                 a.v[row] = (T)vi;
                 double q[2] = {(double)ldv(a.rhat + row) * (double)(T)vi, (double)(T)vi * (double)(T)vi};
                 acc(g - g0, 2, q);
@@ -312,7 +447,10 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 SysState& st = S[threadIdx.x];
                 if (st.inner_active) {
                     double rv = stot[threadIdx.x][0];
-                    if (!(fabs(rv) > 1e-12 * st.rhat_norm * sqrt(stot[threadIdx.x][1]))) {
+                    if (!fin(rv) || !fin(stot[threadIdx.x][1])) {
+                        st.inner_active = 0;
+                        st.pass_bad = 1;
+                    } else if (!(fabs(rv) > bd_tol * st.rhat_norm * sqrt(stot[threadIdx.x][1]))) {
                         st.inner_active = 0;  // restart from the current x
                     } else {
                         st.alpha = st.rho / rv;
@@ -328,13 +466,14 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 a.s[row] = (T)((double)ldv(a.r + row) - S[g].alpha * (double)ldv(a.v + row));
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
-            // D: t = A s; t.s, t.t, s.s
+            if (a.use_mg && !vcycle(a.s, a.shat)) { alive = false; break; }
+            // D: t = A shat; t.s, t.t, s.s
             clear_acc();
             for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
-                T ti = (T)spmv_row(sl, a.aT, a.s);
+                T ti = (T)spmv_row(sl, a.aT, a.shat);
                 a.t[row] = ti;
                 double si = (double)ldv(a.s + row);
                 double q[3] = {(double)ti * si, (double)ti * (double)ti, si * si};
@@ -348,7 +487,11 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                     st.iters += 1;
                     st.pass_iters += 1;
                     double ts = stot[threadIdx.x][0], tt = stot[threadIdx.x][1];
-                    if (sqrt(stot[threadIdx.x][2]) <= st.tol || tt == 0.0) {
+                    if (!fin(ts) || !fin(tt) || !fin(stot[threadIdx.x][2])) {
+                        st.s_conv = 1;      // stop the pass after E and discard it
+                        st.omega = 0.0;
+                        st.pass_bad = 1;
+                    } else if (sqrt(stot[threadIdx.x][2]) <= st.tol || tt == 0.0) {
                         st.s_conv = 1;
                         st.omega = 0.0;
                     } else {
@@ -365,7 +508,8 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 int64_t row = (int64_t)sl * 32 + lane;
                 double al = S[g].alpha, om = S[g].omega;
                 double si = (double)ldv(a.s + row);
-                double d = (double)ldv(a.dx + row) + al * (double)ldv(a.p + row) + om * si;
+                double d = (double)ldv(a.dx + row) + al * (double)ldv(a.phat + row) +
+                           om * (double)ldv(a.shat + row);
                 a.dx[row] = (T)d;
                 T rn = (T)(si - om * (double)ldv(a.t + row));
                 a.r[row] = rn;
@@ -377,9 +521,13 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 SysState& st = S[threadIdx.x];
                 if (st.inner_active) {
                     double rho = stot[threadIdx.x][0], rr = sqrt(stot[threadIdx.x][1]);
-                    if (st.s_conv || rr <= st.tol || st.omega == 0.0 || st.iters >= a.max_iters) {
+                    if (!fin(rho) || !fin(rr) || rr > 1e8 * st.r0_in) {
+                        st.inner_active = 0;  // diverging in precision T: discard the pass
+                        st.pass_bad = 1;
+                    } else if (st.s_conv || rr <= st.tol || st.omega == 0.0 || st.iters >= a.max_iters ||
+                               st.pass_iters >= st.pass_cap) {
                         st.inner_active = 0;
-                    } else if (!(fabs(rho) > 1e-12 * st.rhat_norm * rr)) {
+                    } else if (!(fabs(rho) > bd_tol * st.rhat_norm * rr)) {
                         st.inner_active = 0;  // restart
                     } else {
                         st.rho_old = st.rho;
@@ -414,7 +562,7 @@ vip_status krylov_plan(vip_ctx* c, KrylovPlan& P, const Sell& A, const std::vect
     int occ64 = 0, occ32 = 0;
     VIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_bicgstab<double>, KTHREADS, 0));
     VIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_bicgstab<float>, KTHREADS, 0));
-    int occ = std::max(1, std::min(std::min(occ64, occ32), 2));
+    int occ = std::max(1, std::min(std::min(occ64, occ32), 1));
     const int64_t nsl = A.nslices;
     std::vector<int32_t> slice_sys(nsl, -1);
     for (int g = 0; g < nsys; ++g) {
@@ -448,7 +596,8 @@ vip_status krylov_plan(vip_ctx* c, KrylovPlan& P, const Sell& A, const std::vect
     VIP_CUDA(dalloc(c, &P.blk_s0, nb)); VIP_CUDA(dalloc(c, &P.blk_s1, nb));
     VIP_CUDA(dalloc(c, &P.blk_g0, nb)); VIP_CUDA(dalloc(c, &P.blk_ng, nb));
     VIP_CUDA(dalloc(c, &P.sys_b0, nsys)); VIP_CUDA(dalloc(c, &P.sys_b1, nsys));
-    VIP_CUDA(dalloc(c, &P.partial, (size_t)nb * MAXSYS_PB * NQ));
+    VIP_CUDA(dalloc(c, &P.partial, (size_t)nb * nsys * NQ));
+    VIP_CUDA(cudaMemsetAsync(P.partial, 0, (size_t)nb * nsys * NQ * sizeof(double), c->stream));
     VIP_CUDA(dalloc(c, &P.flags, nb));
     VIP_CUDA(dalloc(c, &P.bar, 2));
     VIP_CUDA(dalloc(c, &P.out_iters, nsys)); VIP_CUDA(dalloc(c, &P.out_outer, nsys));
@@ -466,21 +615,60 @@ vip_status krylov_plan(vip_ctx* c, KrylovPlan& P, const Sell& A, const std::vect
 }
 
 template <class T>
+static MgDev<T> mg_view(const Multigrid& M) {
+    MgDev<T> d;
+    memset(&d, 0, sizeof(d));
+    const bool f32 = sizeof(T) == 4;
+    d.nlev = M.nlev;
+    d.agg = M.agg; d.cptr = M.cptr; d.crow = M.crow;
+    d.fdinv = f32 ? (const T*)M.fdinv32 : (const T*)M.fdinv;
+    d.fr = (T*)M.fr; d.fx = (T*)M.fx;
+    for (int l = 1; l <= M.nlev; ++l) {
+        const MgLevel& v = M.lev[l];
+        d.n[l] = v.n; d.nbr[l] = v.nbr; d.parent[l] = v.parent; d.child[l] = v.child;
+        d.coef[l] = f32 ? (const T*)v.coef32 : (const T*)v.coef;
+        d.dinv[l] = f32 ? (const T*)v.dinv32 : (const T*)v.dinv;
+        d.x[l] = (T*)v.x; d.b[l] = (T*)v.b; d.y[l] = (T*)v.y;
+    }
+    d.omega = 0.8f;
+    d.corr = 1.5f;
+    d.cinv = M.cinv;
+    d.cinv_off = M.cinv_off;
+    d.coff = M.lev[M.nlev].off;
+    d.ngeom = M.ngeom;
+    return d;
+}
+
+template <class T>
 static vip_status launch(vip_ctx* c, const KrylovPlan& P, const Sell& A, const double* b, double* x,
-                         double rtol, int32_t max_iters, double inner_rtol) {
+                         double rtol, int32_t max_iters, double inner_rtol, const Multigrid* mg) {
     KrylovWork& W = sizeof(T) == 8 ? c->work64 : c->work32;
     if (W.n < A.nrows) { c->err = "Krylov workspace too small"; return VIP_ERR_ARG; }
     KArgs<T> a;
     a.sptr = A.sptr; a.width = A.width; a.col = A.col; a.a64 = A.v64;
     a.aT = sizeof(T) == 8 ? (const T*)A.v64 : (const T*)A.v32;
     a.slice_sys = P.slice_sys; a.blk_s0 = P.blk_s0; a.blk_s1 = P.blk_s1; a.blk_g0 = P.blk_g0;
+    a.blk_ng = P.blk_ng;
     a.sys_b0 = P.sys_b0; a.sys_b1 = P.sys_b1; a.partial = P.partial; a.bar = P.bar;
     a.nsys = P.nsys; a.b = b; a.x = x;
     a.r = (T*)W.r; a.rhat = (T*)W.rhat; a.p = (T*)W.p; a.v = (T*)W.v; a.s = (T*)W.s;
     a.t = (T*)W.t; a.dx = (T*)W.dx;
-    a.rtol = rtol; a.inner_rtol = inner_rtol; a.max_iters = max_iters; a.max_outer = 200;
+    a.rtol = rtol; a.inner_rtol = inner_rtol; a.max_iters = max_iters;
+    // FP32 passes are re-anchored on the FP64 residual at least every 4000 iterations
+    a.max_outer = 1000;
+    a.max_pass = sizeof(T) == 8 ? max_iters : 4000;
     a.out_iters = P.out_iters; a.out_outer = P.out_outer; a.out_relres = P.out_relres;
     a.out_status = P.out_status; a.status = c->d_status;
+    a.use_mg = (mg && mg->built) ? 1 : 0;
+    if (a.use_mg) {
+        a.mg = mg_view<T>(*mg);
+        a.phat = (T*)c->phat;
+        a.shat = (T*)c->shat;
+    } else {
+        memset(&a.mg, 0, sizeof(a.mg));
+        a.phat = a.p;
+        a.shat = a.s;
+    }
     VIP_CUDA(cudaMemsetAsync(P.bar, 0, 2 * sizeof(uint32_t), c->stream));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(P.nblocks);
@@ -497,10 +685,11 @@ static vip_status launch(vip_ctx* c, const KrylovPlan& P, const Sell& A, const d
 }
 
 vip_status krylov_solve(vip_ctx* c, const KrylovPlan& P, const Sell& A, const double* b, double* x,
-                        int precision, double rtol, int32_t max_iters, double inner_rtol) {
+                        int precision, double rtol, int32_t max_iters, double inner_rtol,
+                        const Multigrid* mg) {
     if (precision == VIP_PREC_MIXED)
-        return launch<float>(c, P, A, b, x, rtol, max_iters, inner_rtol);
-    return launch<double>(c, P, A, b, x, rtol, max_iters, inner_rtol);
+        return launch<float>(c, P, A, b, x, rtol, max_iters, inner_rtol, mg);
+    return launch<double>(c, P, A, b, x, rtol, max_iters, inner_rtol, mg);
 }
 
 }  // namespace vip

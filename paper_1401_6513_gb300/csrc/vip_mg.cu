@@ -1,0 +1,395 @@
+// Aggregation multigrid preconditioner for the pressure-increment solve (Eq. 13).
+//
+// The node sets live on a regular background lattice (plus boundary nodes on
+// curves).  Level 1 aggregates the nodes of each 2h x 2h cell of that lattice;
+// level l+1 aggregates 2 x 2 cells of level l.  Prolongation is piecewise
+// constant, restriction its transpose, and every coarse operator is the Galerkin
+// product P^T A P of the level above, so the coarse levels inherit the MLS
+// stencils and the boundary rows of the fine operator.  Because the aggregates are
+// lattice cells, every coarse operator is a structured 5 x 5 stencil on a cell
+// lattice (25 coefficients per cell, neighbour table precomputed).  All sums are
+// formed in a fixed order, so the hierarchy is deterministic.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "vip_internal.cuh"
+#include "vip_mg.cuh"
+
+namespace vip {
+
+// cell of a fine row at level 1 (-1: not a node)
+__global__ void k_mg_agg(int64_t R, const int8_t* __restrict__ rt, const int32_t* __restrict__ rg,
+                         const double* __restrict__ x, const double* __restrict__ y,
+                         const MgGeom* __restrict__ mg, const int64_t* __restrict__ off1,
+                         int32_t* __restrict__ agg) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    if (rt[r] != ROW_NODE) { agg[r] = -1; return; }
+    const MgGeom& G = mg[rg[r]];
+    long long ix = llrint((x[r] - G.x0) / G.h);
+    long long iy = llrint((y[r] - G.y0) / G.h);
+    int cx = (int)(ix >> 1), cy = (int)(iy >> 1);
+    const int nx = G.nx[1], ny = G.ny[1];
+    if (G.periodic_x) { cx %= nx; if (cx < 0) cx += nx; } else cx = min(max(cx, 0), nx - 1);
+    if (G.periodic_y) { cy %= ny; if (cy < 0) cy += ny; } else cy = min(max(cy, 0), ny - 1);
+    agg[r] = (int32_t)(off1[rg[r]] + (int64_t)cy * nx + cx);
+}
+
+// neighbour table, parent and children of the cells of one level
+__global__ void k_mg_topology(int64_t ncells, const int32_t* __restrict__ cgeom,
+                              const int32_t* __restrict__ cx_, const int32_t* __restrict__ cy_,
+                              const MgGeom* __restrict__ mg, const int64_t* __restrict__ offl,
+                              const int64_t* __restrict__ offp, int level, int has_parent,
+                              int32_t* __restrict__ nbr, int32_t* __restrict__ parent) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    int g = cgeom[c];
+    const MgGeom& G = mg[g];
+    int nx = G.nx[level], ny = G.ny[level];
+    int x = cx_[c], y = cy_[c];
+    for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx) {
+            int xx = x + dx, yy = y + dy;
+            bool ok = true;
+            if (G.periodic_x) { xx %= nx; if (xx < 0) xx += nx; } else ok &= xx >= 0 && xx < nx;
+            if (G.periodic_y) { yy %= ny; if (yy < 0) yy += ny; } else ok &= yy >= 0 && yy < ny;
+            int o = (dy + 2) * 5 + (dx + 2);
+            nbr[(int64_t)o * ncells + c] = ok ? (int32_t)(offl[g] + (int64_t)yy * nx + xx) : -1;
+        }
+    if (has_parent) {
+        int px = x >> 1, py = y >> 1;
+        parent[c] = (int32_t)(offp[g] + (int64_t)py * G.nx[level + 1] + px);
+    }
+}
+
+// canonical 5x5 offset index of target cell t seen from cell c (wrap-aware), -1 if none
+__device__ __forceinline__ int offset_of(const int32_t* __restrict__ nbr, int64_t ncells, int64_t c,
+                                         int32_t t) {
+    for (int o = 0; o < 25; ++o)
+        if (nbr[(int64_t)o * ncells + c] == t) return o;
+    return -1;
+}
+
+// level-1 Galerkin coefficients from the fine SELL operator (rows of a cell in
+// ascending order, entries in stored order)
+__global__ void k_mg_galerkin1(int64_t ncells, const int64_t* __restrict__ cptr,
+                               const int32_t* __restrict__ crow, Sell A,
+                               const int32_t* __restrict__ agg, const int32_t* __restrict__ nbr,
+                               double* __restrict__ coef) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    double acc[25];
+    for (int o = 0; o < 25; ++o) acc[o] = 0.0;
+    for (int64_t q = cptr[c]; q < cptr[c + 1]; ++q) {
+        int64_t r = crow[q];
+        int64_t s = r >> 5;
+        int64_t base = A.sptr[s] + (r & 31);
+        int len = A.rowlen[r];
+        for (int k = 0; k < len; ++k) {
+            int64_t e = base + (int64_t)k * SLICE;
+            int32_t j = A.col[e];
+            int32_t t = agg[j];
+            if (t < 0) continue;  // border (mu) and padding columns stay on the fine level
+            int o = offset_of(nbr, ncells, c, t);
+            if (o >= 0) acc[o] += A.v64[e];
+        }
+    }
+    for (int o = 0; o < 25; ++o) coef[(int64_t)o * ncells + c] = acc[o];
+}
+
+// level l+1 from level l: sum over the (up to 4) children in fixed order
+__global__ void k_mg_galerkin(int64_t nc, const int64_t* __restrict__ child,  // [4][nc]
+                              int64_t nf, const int32_t* __restrict__ fnbr,
+                              const double* __restrict__ fcoef, const int32_t* __restrict__ fparent,
+                              const int32_t* __restrict__ cnbr, double* __restrict__ ccoef) {
+    int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (C >= nc) return;
+    double acc[25];
+    for (int o = 0; o < 25; ++o) acc[o] = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        int64_t c = child[(int64_t)k * nc + C];
+        if (c < 0) continue;
+        for (int o = 0; o < 25; ++o) {
+            int32_t j = fnbr[(int64_t)o * nf + c];
+            if (j < 0) continue;
+            double a = fcoef[(int64_t)o * nf + c];
+            if (a == 0.0) continue;
+            int oc = offset_of(cnbr, nc, C, fparent[j]);
+            if (oc >= 0) acc[oc] += a;
+        }
+    }
+    for (int o = 0; o < 25; ++o) ccoef[(int64_t)o * nc + C] = acc[o];
+}
+
+__global__ void k_mg_finish(int64_t n, const double* __restrict__ coef, float* __restrict__ coef32,
+                            double* __restrict__ dinv, float* __restrict__ dinv32) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    for (int o = 0; o < 25; ++o) coef32[(int64_t)o * n + c] = (float)coef[(int64_t)o * n + c];
+    double d = coef[(int64_t)12 * n + c];
+    double di = (d != 0.0) ? 1.0 / d : 0.0;
+    dinv[c] = di;
+    dinv32[c] = (float)di;
+}
+
+// fine-level inverse diagonal
+__global__ void k_mg_fine_diag(Sell A, double* __restrict__ dinv, float* __restrict__ dinv32) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= A.nrows) return;
+    int64_t base = A.sptr[r >> 5] + (r & 31);
+    double d = 0.0;
+    for (int k = 0; k < A.rowlen[r]; ++k) {
+        int64_t e = base + (int64_t)k * SLICE;
+        if (A.col[e] == r) d += A.v64[e];
+    }
+    double di = d != 0.0 ? 1.0 / d : 0.0;
+    dinv[r] = di;
+    dinv32[r] = (float)di;
+}
+
+// Dense inverse of each geometry's coarsest operator (Gauss-Jordan with partial
+// pivoting in shared memory, one block per geometry).  Cells without a row
+// (empty cells) are decoupled: their unknown stays 0.
+__global__ void k_mg_coarse_inv(const double* __restrict__ coef, const int32_t* __restrict__ nbr, int64_t n,
+                                const int64_t* __restrict__ off, const MgGeom* __restrict__ mg, int L,
+                                const int64_t* __restrict__ ioff, double* __restrict__ inv) {
+    extern __shared__ double sm[];
+    const int g = blockIdx.x;
+    const int m = mg[g].nx[L] * mg[g].ny[L];
+    const int64_t c0 = off[g];
+    double* A = sm;              // [m][2m]
+    const int w = 2 * m;
+    for (int i = threadIdx.x; i < m * w; i += blockDim.x) A[i] = 0.0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        bool empty = true;
+        for (int o = 0; o < 25; ++o) {
+            int32_t j = nbr[(int64_t)o * n + c0 + r];
+            double a = coef[(int64_t)o * n + c0 + r];
+            if (j >= 0 && a != 0.0) {
+                A[r * w + (int)(j - c0)] += a;
+                empty = false;
+            }
+        }
+        if (empty) A[r * w + r] = 1.0;
+        A[r * w + m + r] = 1.0;
+    }
+    __syncthreads();
+    __shared__ int piv;
+    for (int k = 0; k < m; ++k) {
+        if (threadIdx.x == 0) {
+            int best = k;
+            for (int i = k + 1; i < m; ++i)
+                if (fabs(A[i * w + k]) > fabs(A[best * w + k])) best = i;
+            piv = best;
+        }
+        __syncthreads();
+        if (piv != k)
+            for (int j = threadIdx.x; j < w; j += blockDim.x) {
+                double t = A[k * w + j]; A[k * w + j] = A[piv * w + j]; A[piv * w + j] = t;
+            }
+        __syncthreads();
+        double d = A[k * w + k];
+        double di = fabs(d) > 1e-300 ? 1.0 / d : 0.0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < w; j += blockDim.x) A[k * w + j] *= di;
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            if (i == k) continue;
+            double f = A[i * w + k];
+            if (f != 0.0)
+                for (int j = 0; j < w; ++j) A[i * w + j] -= f * A[k * w + j];
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < m * m; i += blockDim.x)
+        inv[ioff[g] + i] = A[(i / m) * w + m + (i % m)];
+}
+
+vip_status mg_build(vip_ctx* c, Multigrid& M) {
+    cudaStream_t st = c->stream;
+    const int G = (int)c->geoms.size();
+    const Sell& A = c->T.pois;
+    // lattice of each geometry
+    std::vector<MgGeom> hg(G);
+    int L = 1;
+    for (int g = 0; g < G; ++g) {
+        const Geom& gg = c->geoms[g];
+        double hmin = 1e300, x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
+        for (int64_t i = gg.off; i < gg.off + gg.n; ++i) {
+            hmin = std::min(hmin, c->hh[i]);
+            x0 = std::min(x0, c->hx[i]); x1 = std::max(x1, c->hx[i]);
+            y0 = std::min(y0, c->hy[i]); y1 = std::max(y1, c->hy[i]);
+        }
+        MgGeom& m = hg[g];
+        memset(&m, 0, sizeof(m));
+        m.h = hmin;
+        m.periodic_x = gg.Lx > 0;
+        m.periodic_y = gg.Ly > 0;
+        m.x0 = m.periodic_x ? 0.0 : x0;
+        m.y0 = m.periodic_y ? 0.0 : y0;
+        int NX = m.periodic_x ? (int)llround(gg.Lx / hmin) : (int)llround((x1 - x0) / hmin) + 1;
+        int NY = m.periodic_y ? (int)llround(gg.Ly / hmin) : (int)llround((y1 - y0) / hmin) + 1;
+        m.nx[0] = NX;
+        m.ny[0] = NY;
+        int l = 0;
+        while (l + 1 < MG_MAXLEV) {
+            int nx = (m.nx[l] + 1) / 2, ny = (m.ny[l] + 1) / 2;
+            m.nx[l + 1] = nx;
+            m.ny[l + 1] = ny;
+            ++l;
+            if ((int64_t)nx * ny <= MG_COARSEST) break;
+        }
+        L = std::max(L, l);
+    }
+    // every geometry gets the same number of levels (tiny ones keep halving to 1 x 1)
+    for (int g = 0; g < G; ++g)
+        for (int l = 1; l <= L; ++l)
+            if (hg[g].nx[l] == 0) {
+                hg[g].nx[l] = (hg[g].nx[l - 1] + 1) / 2;
+                hg[g].ny[l] = (hg[g].ny[l - 1] + 1) / 2;
+            }
+    M.nlev = L;  // coarse levels 1..L
+    VIP_CUDA(dalloc(c, &M.geom, G));
+    VIP_CUDA(cudaMemcpyAsync(M.geom, hg.data(), G * sizeof(MgGeom), cudaMemcpyHostToDevice, st));
+    // per level: cell offsets, coordinates
+    std::vector<std::vector<int64_t>> offs(L + 2, std::vector<int64_t>(G));
+    for (int l = 1; l <= L; ++l) {
+        MgLevel& lv = M.lev[l];
+        int64_t n = 0;
+        for (int g = 0; g < G; ++g) { offs[l][g] = n; n += (int64_t)hg[g].nx[l] * hg[g].ny[l]; }
+        lv.n = n;
+        std::vector<int32_t> cg(n), cx(n), cy(n);
+        for (int g = 0; g < G; ++g)
+            for (int yy = 0; yy < hg[g].ny[l]; ++yy)
+                for (int xx = 0; xx < hg[g].nx[l]; ++xx) {
+                    int64_t id = offs[l][g] + (int64_t)yy * hg[g].nx[l] + xx;
+                    cg[id] = g; cx[id] = xx; cy[id] = yy;
+                }
+        VIP_CUDA(dalloc(c, &lv.cgeom, n)); VIP_CUDA(dalloc(c, &lv.cx, n)); VIP_CUDA(dalloc(c, &lv.cy, n));
+        VIP_CUDA(dalloc(c, &lv.off, G));
+        VIP_CUDA(cudaMemcpyAsync(lv.cgeom, cg.data(), n * 4, cudaMemcpyHostToDevice, st));
+        VIP_CUDA(cudaMemcpyAsync(lv.cx, cx.data(), n * 4, cudaMemcpyHostToDevice, st));
+        VIP_CUDA(cudaMemcpyAsync(lv.cy, cy.data(), n * 4, cudaMemcpyHostToDevice, st));
+        VIP_CUDA(cudaMemcpyAsync(lv.off, offs[l].data(), G * 8, cudaMemcpyHostToDevice, st));
+        VIP_CUDA(dalloc(c, &lv.nbr, 25 * n));
+        VIP_CUDA(dalloc(c, &lv.parent, n));
+        VIP_CUDA(dalloc(c, &lv.coef, 25 * n));
+        VIP_CUDA(dalloc(c, &lv.coef32, 25 * n));
+        VIP_CUDA(dalloc(c, &lv.dinv, n));
+        VIP_CUDA(dalloc(c, &lv.dinv32, n));
+        for (void** v : {&lv.x, &lv.b, &lv.y}) {
+            char* m = nullptr;
+            VIP_CUDA(dalloc(c, &m, n * 8));
+            *v = m;
+        }
+        cudaStreamSynchronize(st);
+    }
+    const int TB = 256;
+    for (int l = 1; l <= L; ++l) {
+        MgLevel& lv = M.lev[l];
+        k_mg_topology<<<(unsigned)((lv.n + TB - 1) / TB), TB, 0, st>>>(
+            lv.n, lv.cgeom, lv.cx, lv.cy, M.geom, lv.off, l < L ? M.lev[l + 1].off : lv.off, l,
+            l < L ? 1 : 0, lv.nbr, lv.parent);
+        VIP_CUDA(cudaGetLastError());
+    }
+    // children lists of levels 2..L
+    for (int l = 2; l <= L; ++l) {
+        MgLevel& lv = M.lev[l];
+        std::vector<int32_t> par(M.lev[l - 1].n);
+        VIP_CUDA(cudaMemcpy(par.data(), M.lev[l - 1].parent, par.size() * 4, cudaMemcpyDeviceToHost));
+        std::vector<int64_t> ch(4 * lv.n, -1);
+        std::vector<int> cnt(lv.n, 0);
+        for (int64_t f = 0; f < (int64_t)par.size(); ++f) {
+            int32_t p = par[f];
+            ch[(int64_t)cnt[p] * lv.n + p] = f;
+            cnt[p]++;
+        }
+        VIP_CUDA(dalloc(c, &lv.child, 4 * lv.n));
+        VIP_CUDA(cudaMemcpyAsync(lv.child, ch.data(), ch.size() * 8, cudaMemcpyHostToDevice, st));
+        cudaStreamSynchronize(st);
+    }
+    // fine rows -> level-1 cells; rows of each cell in ascending order
+    const int64_t R = c->R;
+    VIP_CUDA(dalloc(c, &M.agg, R));
+    k_mg_agg<<<(unsigned)((R + TB - 1) / TB), TB, 0, st>>>(R, c->row_type, c->row_geom, c->x, c->y,
+                                                          M.geom, M.lev[1].off, M.agg);
+    VIP_CUDA(cudaGetLastError());
+    {
+        std::vector<int32_t> agg(R);
+        VIP_CUDA(cudaMemcpy(agg.data(), M.agg, R * 4, cudaMemcpyDeviceToHost));
+        const int64_t n1 = M.lev[1].n;
+        std::vector<int64_t> ptr(n1 + 1, 0);
+        for (int64_t r = 0; r < R; ++r)
+            if (agg[r] >= 0) ptr[agg[r] + 1]++;
+        for (int64_t i = 0; i < n1; ++i) ptr[i + 1] += ptr[i];
+        std::vector<int32_t> rows(std::max<int64_t>(ptr[n1], 1));
+        std::vector<int64_t> cur(ptr.begin(), ptr.end() - 1);
+        for (int64_t r = 0; r < R; ++r)
+            if (agg[r] >= 0) rows[cur[agg[r]]++] = (int32_t)r;
+        VIP_CUDA(dalloc(c, &M.cptr, n1 + 1));
+        VIP_CUDA(dalloc(c, &M.crow, rows.size()));
+        VIP_CUDA(cudaMemcpyAsync(M.cptr, ptr.data(), (n1 + 1) * 8, cudaMemcpyHostToDevice, st));
+        VIP_CUDA(cudaMemcpyAsync(M.crow, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, st));
+        cudaStreamSynchronize(st);
+    }
+    // Galerkin coefficients
+    {
+        MgLevel& l1 = M.lev[1];
+        k_mg_galerkin1<<<(unsigned)((l1.n + TB - 1) / TB), TB, 0, st>>>(l1.n, M.cptr, M.crow, A, M.agg,
+                                                                       l1.nbr, l1.coef);
+        VIP_CUDA(cudaGetLastError());
+        for (int l = 2; l <= L; ++l) {
+            MgLevel& lc = M.lev[l];
+            MgLevel& lf = M.lev[l - 1];
+            k_mg_galerkin<<<(unsigned)((lc.n + TB - 1) / TB), TB, 0, st>>>(
+                lc.n, lc.child, lf.n, lf.nbr, lf.coef, lf.parent, lc.nbr, lc.coef);
+            VIP_CUDA(cudaGetLastError());
+        }
+        for (int l = 1; l <= L; ++l) {
+            MgLevel& lv = M.lev[l];
+            k_mg_finish<<<(unsigned)((lv.n + TB - 1) / TB), TB, 0, st>>>(lv.n, lv.coef, lv.coef32, lv.dinv,
+                                                                        lv.dinv32);
+            VIP_CUDA(cudaGetLastError());
+        }
+    }
+    {   // exact solve on the coarsest level: dense inverses, one per geometry
+        MgLevel& lc = M.lev[L];
+        std::vector<int64_t> ioff(G);
+        int64_t tot = 0;
+        int mmax = 1;
+        for (int g = 0; g < G; ++g) {
+            int m = hg[g].nx[L] * hg[g].ny[L];
+            ioff[g] = tot;
+            tot += (int64_t)m * m;
+            mmax = std::max(mmax, m);
+        }
+        VIP_CUDA(dalloc(c, &M.cinv, tot));
+        VIP_CUDA(dalloc(c, &M.cinv_off, G));
+        VIP_CUDA(cudaMemcpyAsync(M.cinv_off, ioff.data(), G * 8, cudaMemcpyHostToDevice, st));
+        size_t smem = (size_t)mmax * 2 * mmax * sizeof(double);
+        VIP_CUDA(cudaFuncSetAttribute(k_mg_coarse_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)std::max<size_t>(smem, 1024)));
+        k_mg_coarse_inv<<<G, 256, smem, st>>>(lc.coef, lc.nbr, lc.n, lc.off, M.geom, L, M.cinv_off,
+                                               M.cinv);
+        VIP_CUDA(cudaGetLastError());
+        M.ngeom = G;
+    }
+    VIP_CUDA(dalloc(c, &M.fdinv, R));
+    VIP_CUDA(dalloc(c, &M.fdinv32, R));
+    k_mg_fine_diag<<<(unsigned)((R + TB - 1) / TB), TB, 0, st>>>(A, M.fdinv, M.fdinv32);
+    VIP_CUDA(cudaGetLastError());
+    {
+        char* m = nullptr;
+        VIP_CUDA(dalloc(c, &m, R * 8));
+        M.fr = m;
+        VIP_CUDA(dalloc(c, &m, R * 8));
+        M.fx = m;
+    }
+    VIP_CUDA(cudaStreamSynchronize(st));
+    M.built = true;
+    return VIP_OK;
+}
+
+}  // namespace vip

@@ -31,13 +31,22 @@ OP = {name: i for i, name in enumerate(OPS)}
 EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_set_mls",
            "vip_set_flow", "vip_set_solver", "vip_build", "vip_set_state", "vip_step",
            "vip_get_state", "vip_get_stats", "vip_get_sizes", "vip_stencil_info",
-           "vip_get_stencil", "vip_apply", "vip_convection", "vip_solve"]
+           "vip_get_stencil", "vip_apply", "vip_convection", "vip_solve", "vip_load_state",
+           "vip_set_profiling", "vip_get_profile", "vip_ws_collect", "vip_ws_train",
+           "vip_ws_enable", "vip_ws_params", "vip_ws_eval"]
+PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
 
 
 class StepStats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("helm_iters", C.c_int32), ("poisson_iters", C.c_int32),
                 ("poisson_outer", C.c_int32), ("status", C.c_int32), ("helm_relres", C.c_double),
-                ("poisson_relres", C.c_double), ("total_poisson_iters", C.c_int64)]
+                ("poisson_relres", C.c_double), ("total_poisson_iters", C.c_int64),
+                ("total_poisson_outer", C.c_int64), ("total_helm_iters", C.c_int64)]
+
+
+class TrainCfg(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64),
+                ("first_loss", C.c_double), ("final_loss", C.c_double)]
 
 
 class VipError(RuntimeError):
@@ -79,6 +88,14 @@ def lib(path: str | Path | None = None):
         "vip_convection": ([vp, vp, vp, vp, vp], C.c_int),
         "vip_solve": ([vp, C.c_int, vp, vp, C.c_int, dbl, i32, C.POINTER(i32), C.POINTER(dbl)],
                       C.c_int),
+        "vip_load_state": ([vp, vp, vp, vp], C.c_int),
+        "vip_set_profiling": ([vp, C.c_int], C.c_int),
+        "vip_get_profile": ([vp, C.POINTER(dbl), C.POINTER(i64)], C.c_int),
+        "vip_ws_collect": ([vp, C.c_int, i32], C.c_int),
+        "vip_ws_train": ([vp, C.POINTER(TrainCfg)], C.c_int),
+        "vip_ws_enable": ([vp, C.c_int], C.c_int),
+        "vip_ws_params": ([vp, C.c_int, C.POINTER(C.c_float), C.POINTER(i64)], C.c_int),
+        "vip_ws_eval": ([vp, i32, i32, vp, vp, vp, vp, vp, C.POINTER(dbl)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -169,6 +186,43 @@ class Context:
         u, v = _f64(u), _f64(v)
         p = None if p is None else _f64(p)
         self._check(self.L.vip_set_state(self.h, _ptr(u), _ptr(v), _ptr(p)))
+
+    def vip_load_state(self, u, v, p):
+        self._check(self.L.vip_load_state(self.h, _ptr(u), _ptr(v), _ptr(p)))
+
+    def vip_set_profiling(self, enable=True):
+        self._check(self.L.vip_set_profiling(self.h, 1 if enable else 0))
+
+    def vip_get_profile(self):
+        ms = (C.c_double * 5)()
+        n = C.c_int64()
+        self._check(self.L.vip_get_profile(self.h, ms, C.byref(n)))
+        return dict(zip(PHASES, list(ms))), n.value
+
+    # -- learned warm start ------------------------------------------------------
+    def vip_ws_collect(self, enable=True, max_samples=0):
+        self._check(self.L.vip_ws_collect(self.h, 1 if enable else 0, int(max_samples)))
+
+    def vip_ws_enable(self, enable=True):
+        self._check(self.L.vip_ws_enable(self.h, 1 if enable else 0))
+
+    def vip_ws_train(self, epochs=10, lr=1e-3, seed=0) -> TrainCfg:
+        cfg = TrainCfg(epochs=int(epochs), lr=float(lr), seed=int(seed))
+        self._check(self.L.vip_ws_train(self.h, C.byref(cfg)))
+        return cfg
+
+    def vip_ws_params(self, params=None):
+        """Return the FP32 parameters; with `params`, load them instead."""
+        n = C.c_int64()
+        self._check(self.L.vip_ws_params(self.h, 0, None, C.byref(n)))
+        if params is None:
+            out = np.empty(n.value, np.float32)
+            self._check(self.L.vip_ws_params(self.h, 0, out.ctypes.data_as(C.POINTER(C.c_float)), None))
+            return out
+        buf = np.ascontiguousarray(params, np.float32)
+        assert buf.size == n.value
+        self._check(self.L.vip_ws_params(self.h, 1, buf.ctypes.data_as(C.POINTER(C.c_float)), None))
+        return buf
 
     def vip_step(self, nsteps=1):
         self._check(self.L.vip_step(self.h, int(nsteps)))
