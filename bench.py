@@ -7,7 +7,7 @@ dominant kernel (the Poisson BiCGSTAB launch).
 
 Workload (default): flow past the bumpy cylinder r = 1 + 0.05 sin 12t + 0.02 sin 31t
 in the channel [-8,24]x[-8,8] at h = 1/64 (about 2.1M nodes), Re = 200, dt = h/10,
-FP32-inner / FP64-refinement Krylov solves, synthetic (generated) node set and an
+multigrid-preconditioned FP64 Krylov solves, synthetic (generated) node set and an
 impulsively started uniform inflow.  Its working set (several GB) exceeds the
 129 MB L2, so no flush is needed between timed steps.
 
@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="bumpy_h64")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()

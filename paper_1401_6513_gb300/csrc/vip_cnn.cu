@@ -357,8 +357,16 @@ vip_status forward(vip_ctx* c, Cnn& N, const CnnImage* img, int nimg, int64_t nt
             a.epi = EPI_RELU_BF16;
             a.y = N.act[l + 1];
         }
-        VIP_CUDA(cnn_conv_fwd(a, c->num_sms, s));
-        x = N.act[l + 1];
+        const char* why = "";
+        cudaError_t e = cnn_conv_fwd(a, c->num_sms, s, &why);
+        if (e != cudaSuccess) {
+            char buf[256];
+            snprintf(buf, sizeof buf, "network forward, layer %d (cin %d, cout %d, tiles %lld): %s: %s", l,
+                     a.cin, a.cout, (long long)a.ntiles, why, cudaGetErrorString(e));
+            c->err = buf;
+            return VIP_ERR_CUDA;
+        }
+        if (l + 1 < CNN_LAYERS) x = N.act[l + 1];
     }
     return VIP_OK;
 }
@@ -390,7 +398,13 @@ vip_status backward(vip_ctx* c, Cnn& N, const CnnImage* img, int nimg, int64_t n
             a.epi = EPI_MASK_BF16;
             a.y = bufs[l & 1];
             a.status = c->d_status;
-            VIP_CUDA(cnn_conv_fwd(a, c->num_sms, s));
+            const char* why = "";
+            cudaError_t e = cnn_conv_fwd(a, c->num_sms, s, &why);
+            if (e != cudaSuccess) {
+                c->err = std::string("network data gradient, layer ") + std::to_string(l) + ": " + why +
+                         ": " + cudaGetErrorString(e);
+                return VIP_ERR_CUDA;
+            }
             gy = bufs[l & 1];
         }
     }
@@ -676,6 +690,17 @@ vip_status vip_ws_eval(vip_ctx* c, int32_t H, int32_t W, const float* x, float* 
     if (!c || !x || H < 1 || W < 1) return VIP_ERR_ARG;
     if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_eval before vip_build");
     Cnn& N = *cnn_of(c);
+    {   // the layer table must be the one built at set-up
+        ParamLayout ref = param_layout();
+        for (int l = 0; l < CNN_LAYERS; ++l)
+            if (N.L.cin[l] != ref.cin[l] || N.L.cout[l] != ref.cout[l]) {
+                char buf[256];
+                snprintf(buf, sizeof buf, "network state corrupted: layer %d has cin %d cout %d (expected %d %d)",
+                         l, N.L.cin[l], N.L.cout[l], ref.cin[l], ref.cout[l]);
+                c->err = buf;
+                return VIP_ERR_ARG;
+            }
+    }
     const int64_t n = (int64_t)H * W;
     vip_status st = ensure_act(c, N, n);
     if (st != VIP_OK) return st;

@@ -48,6 +48,6 @@ struct CnnConvArgs {
 };
 
 cudaError_t cnn_conv_init();
-cudaError_t cnn_conv_fwd(const CnnConvArgs& a, int nsm, cudaStream_t s);
+cudaError_t cnn_conv_fwd(const CnnConvArgs& a, int nsm, cudaStream_t s, const char** why);
 
 }  // namespace vip

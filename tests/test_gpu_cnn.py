@@ -1,9 +1,15 @@
 """Warm-start network on the GPU vs the FP64 CPU reference (oracle/cnn_oracle.py).
 
-Tolerances: the GPU keeps activations and gradients in BF16 (8-bit mantissa,
-relative rounding 2^-9 ~ 2e-3 per value) and accumulates in FP32; through six
-layers the relative L2 error of the output stays below ~2e-2 and that of the
-parameter gradients below ~5e-2.  The bars are set there.
+Tolerances: the GPU keeps weights, activations and gradients in BF16 (8-bit
+mantissa, relative rounding 2^-9 ~ 2e-3 per value) and accumulates in FP32;
+through six layers the relative L2 error of the output stays below ~2e-2.  The
+gradients of the lower layers drift further from the FP64 values (ReLU masks
+that flip where a pre-activation is within rounding of zero, compounded layer by
+layer: ~1e-1 at the first layer for random weights), so the gradient test
+compares with the FP64 reference evaluated on the same BF16-rounded weights,
+activations and back-propagated gradients (the GPU's storage points), where
+only the FP32 summation order differs: bar 1e-2.  Against the pure FP64
+gradients only the last two layers are held, at 5e-2.
 """
 import numpy as np
 import pytest
@@ -92,6 +98,29 @@ def test_forward_matches_reference(ctx, shape):
     assert err < 2e-2, err
 
 
+def bf16_reference_grads(layers, x, t, m):
+    """FP64 forward/backward of the oracle with BF16 rounding where the GPU stores
+    BF16: packed weights, ReLU outputs, the loss gradient and each data gradient."""
+    wq = [(bf16(wt).astype(np.float64), b) for wt, b in layers]
+    acts, h = [x], x
+    for k, (wt, b) in enumerate(wq):
+        h = co.conv3x3(h, wt, b)
+        if k < len(wq) - 1:
+            h = bf16(np.maximum(h, 0.0)).astype(np.float64)
+            acts.append(h)
+    y = h[..., 0].astype(np.float32).astype(np.float64)
+    d = (y - t) * m
+    gy = np.zeros(h.shape)
+    gy[..., 0] = bf16(2.0 * d / max(m.sum(), 1.0))
+    out = [None] * len(wq)
+    for k in range(len(wq) - 1, -1, -1):
+        gx, gw, gb = co.conv3x3_backward(acts[k], wq[k][0], gy)
+        out[k] = (gw, gb)
+        if k > 0:
+            gy = bf16(gx * (acts[k] > 0)).astype(np.float64)
+    return out
+
+
 def test_gradients_match_reference(ctx):
     flat = random_params(ctx, 3)
     rng = np.random.default_rng(4)
@@ -103,18 +132,25 @@ def test_gradients_match_reference(ctx):
     m = (rng.random((H, W)) > 0.2).astype(np.float32)
     _, g, loss = eval_gpu(ctx, x, t, m, flat.size)
     layers = to_layers(flat)
-    L, ref = co.loss_and_grads(layers, x.astype(np.float64), t.astype(np.float64), m)
+    x64, t64, m64 = x.astype(np.float64), t.astype(np.float64), m.astype(np.float64)
+    L, ref = co.loss_and_grads(layers, x64, t64, m64)
+    emu = bf16_reference_grads(layers, x64, t64, m64)
     assert abs(loss - L) <= 2e-2 * abs(L)
     o = 0
-    for (gw, gb), (ci, cout) in zip(ref, zip(CH[:-1], CH[1:])):
+    for k, (ci, cout) in enumerate(zip(CH[:-1], CH[1:])):
         n = 9 * ci * cout
-        got_w = g[o:o + n].reshape(gw.shape)
+        got_w = g[o:o + n].reshape(ref[k][0].shape)
         o += n
         got_b = g[o:o + cout]
         o += cout
-        ew = np.linalg.norm(got_w - gw) / max(np.linalg.norm(gw), 1e-30)
-        eb = np.linalg.norm(got_b - gb) / max(np.linalg.norm(gb), 1e-30)
-        assert ew < 5e-2 and eb < 5e-2, (ci, cout, ew, eb)
+
+        def rel(a, b):
+            return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        ew, eb = rel(got_w, emu[k][0]), rel(got_b, emu[k][1])
+        assert ew < 1e-2 and eb < 1e-2, (k, ci, cout, ew, eb)
+        if k >= len(CH) - 3:
+            ew, eb = rel(got_w, ref[k][0]), rel(got_b, ref[k][1])
+            assert ew < 5e-2 and eb < 5e-2, (k, ci, cout, ew, eb)
 
 
 def test_untrained_network_reproduces_previous_increment_guess(vip):
