@@ -261,6 +261,40 @@ vip_status vip_ws_params(vip_ctx* ctx, int direction, float* buf, int64_t* count
 vip_status vip_ws_eval(vip_ctx* ctx, int32_t H, int32_t W, const float* x, float* y, float* grads,
                        const float* target, const float* mask, double* loss);
 
+/* ---- BiCGSTAB without device allocation -----------------------------------
+ * An addition of this library; the paper has no counterpart.  For callers that
+ * must not allocate device memory while they run: a process whose device memory
+ * belongs to another framework's caching allocator (a cudaMalloc behind its back
+ * can fail or fragment its pool), a real-time loop, or code under a fixed memory
+ * budget.  vip_solve needs a context (vip_create/vip_build allocate); this call
+ * needs none.
+ *
+ * Solves A x = b in FP64 with unpreconditioned BiCGSTAB for a general square
+ * sparse A given as CSR (row_ptr[n+1], col[nnz] in [0, n), val[nnz]); all five
+ * arrays are DEVICE pointers owned by the caller, on `device`.  x holds the
+ * initial guess on entry and the solution on return.  Stops when
+ * ||b - A x|| <= rtol ||b|| (the recursive residual) or after max_iters
+ * iterations (VIP_ERR_NOT_CONVERGED, x = last iterate).  iters (may be NULL)
+ * gets the iteration count, relres (may be NULL) the true relative residual of
+ * the returned x.  The call runs on cuda_stream (NULL = the legacy default
+ * stream) of `device`, synchronises with it, and leaves the caller's current
+ * device as it was.
+ *
+ * Workspace: file-scope static device memory, at most VIP_STATIC_MAX_ROWS rows;
+ * larger n returns VIP_ERR_ARG before any device work.  Each call clears the
+ * barrier words and result record it uses (on cuda_stream); nothing needs to be
+ * zero beforehand.  The first call on a device looks up the workspace's device
+ * address (and loads the module there): make it before any stream capture on
+ * that device.  All calls on one device share the one workspace, so calls that
+ * overlap in time on that device (other streams, other host threads) race and
+ * must be serialised by the caller.  Errors: VIP_ERR_ARG (bad size, tolerance,
+ * NULL or host pointer), VIP_ERR_CUDA, VIP_ERR_BREAKDOWN, VIP_ERR_NOT_CONVERGED,
+ * VIP_ERR_TIMEOUT (a grid-barrier wait ran out; the result is not valid). */
+#define VIP_STATIC_MAX_ROWS 131072
+vip_status vip_bicgstab_static(int device, void* cuda_stream, int64_t n, const int64_t* row_ptr,
+                               const int32_t* col, const double* val, const double* b, double* x,
+                               double rtol, int32_t max_iters, int32_t* iters, double* relres);
+
 #ifdef __cplusplus
 }
 #endif

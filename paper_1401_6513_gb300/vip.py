@@ -33,7 +33,8 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_get_state", "vip_get_stats", "vip_get_sizes", "vip_stencil_info",
            "vip_get_stencil", "vip_apply", "vip_convection", "vip_solve", "vip_load_state",
            "vip_set_profiling", "vip_get_profile", "vip_ws_collect", "vip_ws_train",
-           "vip_ws_enable", "vip_ws_params", "vip_ws_eval"]
+           "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static"]
+VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
 
 
@@ -96,6 +97,8 @@ def lib(path: str | Path | None = None):
         "vip_ws_enable": ([vp, C.c_int], C.c_int),
         "vip_ws_params": ([vp, C.c_int, C.POINTER(C.c_float), C.POINTER(i64)], C.c_int),
         "vip_ws_eval": ([vp, i32, i32, vp, vp, vp, vp, vp, C.POINTER(dbl)], C.c_int),
+        "vip_bicgstab_static": ([C.c_int, vp, i64, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(i32),
+                                 C.POINTER(dbl)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -281,6 +284,18 @@ class Context:
         self._check(self.L.vip_solve(self.h, w, _ptr(b), _ptr(x), precision, float(rtol),
                                      int(max_iters), C.byref(it), C.byref(rr)))
         return x, it.value, rr.value
+
+
+def vip_bicgstab_static(device, stream, n, row_ptr, col, val, b, x, rtol=1e-10, max_iters=20000):
+    """FP64 BiCGSTAB on a caller-owned device CSR matrix without any device
+    allocation (workspace in static device memory, n <= VIP_STATIC_MAX_ROWS).
+    All arrays are device tensors; x is the initial guess and is overwritten.
+    Returns (status, iterations, true relative residual)."""
+    it, rr = C.c_int32(0), C.c_double(0.0)
+    st = lib().vip_bicgstab_static(int(device), C.c_void_p(stream) if stream else None, int(n),
+                                   _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x),
+                                   float(rtol), int(max_iters), C.byref(it), C.byref(rr))
+    return st, it.value, rr.value
 
 
 def solver_for(nodesets, precision=VIP_PREC_MIXED, rtol=1e-8, max_iters=20000,
