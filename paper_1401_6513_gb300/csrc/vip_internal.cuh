@@ -75,7 +75,7 @@ struct KrylovPlan {
     int32_t* blk_ng = nullptr;      // [nblocks] number of systems of the block
     int32_t* sys_b0 = nullptr;      // [nsys] block range of a system
     int32_t* sys_b1 = nullptr;
-    double* partial = nullptr;      // [nblocks][MAXSYS_PB][NQ]
+    double* partial = nullptr;      // [2][nsys][NQ][nblocks]: two sets, alternate reductions
     int32_t* flags = nullptr;       // [nblocks]
     uint32_t* bar = nullptr;        // [2] barrier count / generation
     // per-system outputs

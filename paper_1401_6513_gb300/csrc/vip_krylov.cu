@@ -43,32 +43,46 @@ __device__ __forceinline__ uint64_t gtimer() {
     return t;
 }
 
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid barrier for a cooperative launch; returns false after a timeout.
+// bar[0] counts arrivals, bar[1] is the generation.  Thread 0 of each block
+// arrives with an acquire-release add (publishing the block's writes, which the
+// CTA barrier has ordered before it); the last arrival resets the count and
+// releases the next generation; the others poll it with acquire loads.  So every
+// write before the barrier happens before every read after it, for weak loads too.
+// The wait gives up after 2 s (VIP_ERR_TIMEOUT).
 __device__ bool grid_sync(uint32_t* bar, unsigned nblocks, int32_t* status) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = ld_volatile_i(status) != VIP_ERR_TIMEOUT;
         if (ok) {
-            unsigned gen = ld_acquire(bar + 1);
-            __threadfence();
-            unsigned arrived = atomicAdd(bar, 1u);
+            const unsigned gen = ld_acquire(bar + 1);
+            const unsigned arrived = atom_add_acq_rel(bar, 1u);
             if (arrived == nblocks - 1) {
-                atomicExch(bar, 0u);
-                __threadfence();
-                atomicAdd(bar + 1, 1u);
+                st_relaxed(bar, 0u);
+                st_release(bar + 1, gen + 1u);
             } else {
-                uint64_t t0 = gtimer();
+                const uint64_t t0 = gtimer();
                 while (ld_acquire(bar + 1) == gen) {
                     if (gtimer() - t0 > 2000000000ull) {
                         set_status(status, VIP_ERR_TIMEOUT);
                         ok = 0;
                         break;
                     }
-                    __nanosleep(32);
                 }
             }
-            __threadfence();
         }
         s_ok = ok;
     }
@@ -90,7 +104,7 @@ struct KArgs {
     const int32_t* blk_ng;
     const int32_t* sys_b0;
     const int32_t* sys_b1;
-    double* partial;     // [nsys][NQ][nblocks], zero where a block has no rows of a system
+    double* partial;     // [2][nsys][NQ][nblocks], zero where a block has no rows of a system
     uint32_t* bar;
     int nsys;
     const double* b;
@@ -124,14 +138,57 @@ struct SysState {
 // A reduced value is usable if finite.
 __device__ __forceinline__ bool fin(double v) { return isfinite(v); }
 
+// Loads of vectors that the launch itself writes: plain (weak) global loads, which
+// may hit in L1.  They are ordered after the writes of the previous phase by the
+// grid barrier (a GPU-scope acquire in thread 0, then a CTA barrier), which the
+// memory model requires to make those writes visible to weak loads; the
+// non-coherent read-only path (__ldg) is used only for data no phase writes.
 template <class T>
-__device__ __forceinline__ T ldv(const T* p) { return __ldcg(p); }
+__device__ __forceinline__ T ldv(const T* p) { return *p; }
+
+// Operator entries are streamed once per pass: evict-first, so they do not push the
+// gathered vectors out of the caches.
+template <class T>
+__device__ __forceinline__ T ldm(const T* p) { return __ldcs(p); }
 
 // warp sum (fixed butterfly order)
 __device__ __forceinline__ double wsum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// sum_k A[row, k] f(col[row, k]) over the SELL entries of one row (lane of the
+// slice's warp), in entry order.  The column indices and values of U entries are
+// loaded before their U gathers, so each warp keeps several loads in flight.
+template <int U, class TA, class F>
+__device__ __forceinline__ double sell_row(const int64_t* __restrict__ sptr,
+                                           const int32_t* __restrict__ width,
+                                           const int32_t* __restrict__ col, const TA* __restrict__ A,
+                                           int64_t sl, int lane, F&& f) {
+    const int64_t base = __ldg(sptr + sl) + lane;
+    const int w = __ldg(width + sl);
+    double sum = 0.0;
+    int k = 0;
+    for (; k + U <= w; k += U) {
+        int c[U];
+        double av[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = base + (int64_t)(k + u) * SLICE;
+            c[u] = ldm(col + e);
+            av[u] = (double)ldm(A + e);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = f(c[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) sum += av[u] * xv[u];
+    }
+    for (; k < w; ++k) {
+        const int64_t e = base + (int64_t)k * SLICE;
+        sum += (double)ldm(A + e) * f(ldm(col + e));
+    }
+    return sum;
 }
 
 template <class T>
@@ -142,6 +199,7 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
     __shared__ double sacc[KWARPS][MAXSYS_PB][NQ];
     __shared__ double stot[MAXSYS][NQ];
     __shared__ SysState S[MAXSYS];
+    __shared__ double s_tile[36][36];  // multigrid: a coarse tile and its halo
     __shared__ int s_any;
     const int bid = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -165,19 +223,25 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
     // Layout partial[(g * NQ + k) * nb + block]: the blocks of one system are a
     // contiguous run, summed by one warp (lanes stride over blocks, then a fixed
     // butterfly), so the order is fixed and the loads are independent.
+    // Two partial sets used by alternate reductions: a block that has read one
+    // reduction's totals and runs ahead into the next one writes the other set, so
+    // it never overwrites a partial that a slower block is still reading.
     const int ng_blk = a.blk_ng[bid];
+    int pset = 0;
     auto reduce = [&](int nq) -> bool {
         __syncthreads();
+        double* part = a.partial + (int64_t)pset * nsys * NQ * nb;
+        pset ^= 1;
         for (int i = threadIdx.x; i < ng_blk * nq; i += KTHREADS) {
             int j = i / nq, k = i % nq;
             double sum = 0.0;
             for (int w = 0; w < KWARPS; ++w) sum += sacc[w][j][k];
-            __stcg(&a.partial[((int64_t)(g0 + j) * NQ + k) * nb + bid], sum);
+            __stcg(&part[((int64_t)(g0 + j) * NQ + k) * nb + bid], sum);
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int i = warp; i < nsys * nq; i += KWARPS) {
             int g = i / nq, k = i % nq;
-            const double* src = a.partial + ((int64_t)g * NQ + k) * nb;
+            const double* src = part + ((int64_t)g * NQ + k) * nb;
             double sum = 0.0;
             for (int bb = a.sys_b0[g] + lane; bb < a.sys_b1[g]; bb += 32) sum += __ldcg(src + bb);
             sum = wsum(sum);
@@ -197,117 +261,181 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
     };
     // y_row = sum_k A[row,k] * vec[col] for the warp's slice (lane = row)
     auto spmv_row = [&](int64_t sl, const auto* A, const auto* vec) -> double {
-        int64_t base = a.sptr[sl] + lane;
-        int w = a.width[sl];
-        double sum = 0.0;
-        for (int k = 0; k < w; ++k) {
-            int64_t e = base + (int64_t)k * 32;
-            sum += (double)__ldg(A + e) * (double)ldv(vec + __ldg(a.col + e));
-        }
-        return sum;
+        return sell_row<4>(a.sptr, a.width, a.col, A, sl, lane,
+                           [&](int j) { return (double)ldv(vec + j); });
     };
 
-    // One V-cycle z = M^{-1} v of the aggregation multigrid: damped Jacobi from zero on
-    // the fine rows, fine residual, restriction (sum over the cell's rows), then on each
-    // coarse level a Jacobi step from zero, its residual and restriction; Jacobi sweeps
-    // on the coarsest level by block 0; back up with piecewise-constant prolongation
-    // and one Jacobi post-smoothing step per level.  Only rows of systems still in
-    // their inner pass are touched on the fine level.
+    // One V-cycle z = M^{-1} v of the aggregation multigrid: a V(1,1)-cycle with
+    // damped Jacobi smoothing from zero, summed restriction, piecewise-constant
+    // prolongation and a scaled coarse correction:
+    //   fine, down:   f = w Df^{-1} v (written by the Krylov update that produces v),
+    //                 fr = v - A f,  b_1 = sum of fr over the rows of each cell
+    //   level l+1:    b_{l+1}(C) = sum over the children c of C of (b_l - A_l x_l)(c),
+    //                 x_l = w D_l^{-1} b_l
+    //   coarsest:     x_L = A_L^{-1} b_L (dense FP64 inverse of each geometry)
+    //   level l, up:  y_l = x_l + w D_l^{-1} (b_l - A_l x_l),
+    //                 x_l = w D_l^{-1} b_l + corr s_{l+1}(parent),  s = x_L or y_{l+1}
+    //   fine, up:     f += corr s_1(agg),  z = f + w Df^{-1} (v - A f)
+    // A coarse level is processed in 32 x 32 tiles of its cell lattice, one CTA per
+    // tile: the smoothing iterate x_l of the tile and a two-cell halo is formed once
+    // in shared memory, then each thread applies its cell's 25-point stencil (warp =
+    // lattice row, coefficients read as one contiguous slice per warp).  Going down,
+    // the tile's residuals are summed over 2 x 2 children straight into b_{l+1}.
+    // Only rows of systems still in their inner pass are touched on the fine level.
     const int64_t gtid = (int64_t)blockIdx.x * KTHREADS + threadIdx.x;
     const int64_t gstride = (int64_t)nb * KTHREADS;
-    auto coarse_res = [&](int l, int64_t c, const T* xv) -> double {
-        const MgDev<T>& M = a.mg;
-        const int64_t n = M.n[l];
-        double acc = (double)ldv(M.b[l] + c);
-        for (int o = 0; o < 25; ++o) {
-            int32_t j = __ldg(M.nbr[l] + (int64_t)o * n + c);
-            if (j >= 0) acc -= (double)__ldg(M.coef[l] + (int64_t)o * n + c) * (double)ldv(xv + j);
+    const double mw = (double)a.mg.omega;
+    const double mcorr = (double)a.mg.corr;
+    // s_tile[r][c] = f(cell, x, y) for the tile at (x0, y0) and its halo (0 outside a
+    // non-periodic lattice; periodic directions wrap)
+    auto stage = [&](const MgLevGeom& q, int x0, int y0, auto&& f) {
+        double v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = threadIdx.x + h * KTHREADS;
+            v[h] = 0.0;
+            if (k < 36 * 36) {
+                int xx = x0 - 2 + k % 36, yy = y0 - 2 + k / 36;
+                bool ok = true;
+                if (q.px) { xx %= q.nx; if (xx < 0) xx += q.nx; } else ok = xx >= 0 && xx < q.nx;
+                if (q.py) { yy %= q.ny; if (yy < 0) yy += q.ny; } else ok = ok && yy >= 0 && yy < q.ny;
+                if (ok) v[h] = f(q.off + (int64_t)yy * q.sx + xx, xx, yy);
+            }
         }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = threadIdx.x + h * KTHREADS;
+            if (k < 36 * 36) s_tile[k / 36][k % 36] = v[h];
+        }
+    };
+    // sum_o A_l[c, o] s_tile[warp + dy][lane + dx] for the thread's cell c
+    auto stencil = [&](int l, int64_t c) -> double {
+        const double* cp = a.mg.coefs[l] + (c >> 5) * 800 + (c & 31);
+        double acc = 0.0;
+#pragma unroll
+        for (int o = 0; o < 25; ++o) acc += ldm(cp + o * 32) * s_tile[warp + o / 5][lane + o % 5];
         return acc;
     };
-    auto vcycle = [&](const T* in, T* out) -> bool {
+    // z = M^{-1} v, given v and f = w Df^{-1} v on the rows of active systems
+    auto vcycle = [&](const T* v, T* z) -> bool {
         const MgDev<T>& M = a.mg;
-        const double w = M.omega;
         const int L = M.nlev;
         for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
-            int g = a.slice_sys[sl];
-            int64_t row = (int64_t)sl * 32 + lane;
-            T z = (T)0;
-            if (S[g].inner_active) z = (T)(w * (double)__ldg(M.fdinv + row) * (double)ldv(in + row));
-            M.fx[row] = z;
-        }
-        if (!grid_sync(a.bar, nb, a.status)) return false;
-        for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
-            int g = a.slice_sys[sl];
-            int64_t row = (int64_t)sl * 32 + lane;
+            const int g = a.slice_sys[sl];
+            const int64_t row = (int64_t)sl * 32 + lane;
             T res = (T)0;
-            if (S[g].inner_active) res = (T)((double)ldv(in + row) - spmv_row(sl, a.aT, M.fx));
+            if (S[g].inner_active) res = (T)((double)ldv(v + row) - spmv_row(sl, a.aT, M.fx));
             M.fr[row] = res;
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int64_t c = gtid; c < M.n[1]; c += gstride) {
             double sum = 0.0;
-            for (int64_t q = __ldg(M.cptr + c); q < __ldg(M.cptr + c + 1); ++q)
-                sum += (double)ldv(M.fr + __ldg(M.crow + q));
+            const int64_t q1 = __ldg(M.cptr + c + 1);
+            for (int64_t q = __ldg(M.cptr + c); q < q1; ++q) sum += (double)ldv(M.fr + __ldg(M.crow + q));
             M.b[1][c] = (T)sum;
-            M.x[1][c] = (T)(w * (double)__ldg(M.dinv[1] + c) * sum);
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int l = 1; l < L; ++l) {
-            for (int64_t c = gtid; c < M.n[l]; c += gstride) M.y[l][c] = (T)coarse_res(l, c, M.x[l]);
-            if (!grid_sync(a.bar, nb, a.status)) return false;
-            const int64_t nc = M.n[l + 1];
-            for (int64_t C = gtid; C < nc; C += gstride) {
-                double sum = 0.0;
-                for (int k = 0; k < 4; ++k) {
-                    int64_t ch = __ldg(M.child[l + 1] + (int64_t)k * nc + C);
-                    if (ch >= 0) sum += (double)ldv(M.y[l] + ch);
+            const T* bl = M.b[l];
+            const double* dl = M.dinv[l];
+            for (int64_t t = blockIdx.x; t < M.ntiles[l]; t += nb) {
+                const MgTile tile = M.tiles[l][t];
+                const MgLevGeom q = M.lg[l][tile.g];
+                __syncthreads();  // the previous tile's reads of s_tile are done
+                stage(q, tile.x0, tile.y0, [&](int64_t j, int, int) {
+                    return mw * __ldg(dl + j) * (double)ldv(bl + j);
+                });
+                __syncthreads();
+                const int x = tile.x0 + lane, y = tile.y0 + warp;
+                double r = 0.0;
+                if (x < q.nx && y < q.ny) {
+                    const int64_t c = q.off + (int64_t)y * q.sx + x;
+                    r = (double)ldv(bl + c) - stencil(l, c);
                 }
-                M.b[l + 1][C] = (T)sum;
-                M.x[l + 1][C] = (T)(w * (double)__ldg(M.dinv[l + 1] + C) * sum);
+                __syncthreads();
+                (&s_tile[0][0])[warp * 32 + lane] = r;
+                __syncthreads();
+                if (threadIdx.x < 256) {  // 16 x 16 cells of level l+1
+                    const int px = threadIdx.x & 15, py = threadIdx.x >> 4;
+                    const MgLevGeom qp = M.lg[l + 1][tile.g];
+                    const int X = (tile.x0 >> 1) + px, Y = (tile.y0 >> 1) + py;
+                    if (X < qp.nx && Y < qp.ny) {
+                        const double* rs = &s_tile[0][0];
+                        const int k0 = (2 * py) * 32 + 2 * px;
+                        M.b[l + 1][qp.off + (int64_t)Y * qp.sx + X] =
+                            (T)((rs[k0] + rs[k0 + 1]) + (rs[k0 + 32] + rs[k0 + 33]));
+                    }
+                }
             }
             if (!grid_sync(a.bar, nb, a.status)) return false;
         }
-        // coarsest level: exact solve x_L = A_L^{-1} b_L with each geometry's dense FP64
-        // inverse (one row per thread of the grid)
+        // coarsest level: x_L = A_L^{-1} b_L with each geometry's dense FP64 inverse
+        // (one row per thread of the grid; cells numbered densely on this level)
         for (int gg = 0; gg < M.ngeom; ++gg) {
-            const int64_t c0 = __ldg(M.coff + gg);
-            const int64_t m = ((gg + 1 < M.ngeom) ? __ldg(M.coff + gg + 1) : M.n[L]) - c0;
+            const MgLevGeom q = M.lg[L][gg];
+            const int64_t m = (int64_t)q.nx * q.ny;
             const double* Ai = M.cinv + __ldg(M.cinv_off + gg);
             for (int64_t i = gtid; i < m; i += gstride) {
                 double sum = 0.0;
-                for (int64_t j = 0; j < m; ++j) sum += __ldg(Ai + i * m + j) * (double)ldv(M.b[L] + c0 + j);
-                M.x[L][c0 + i] = (T)sum;
+                for (int64_t j = 0; j < m; ++j) sum += __ldg(Ai + i * m + j) * (double)ldv(M.b[L] + q.off + j);
+                M.x[L][q.off + i] = (T)sum;
             }
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
-        // the corrected solution of level l is x_L on the coarsest level, y_l above it
         for (int l = L - 1; l >= 1; --l) {
-            const T* sol = (l + 1 == L) ? M.x[l + 1] : M.y[l + 1];
-            for (int64_t c = gtid; c < M.n[l]; c += gstride)
-                M.x[l][c] = (T)((double)ldv(M.x[l] + c) +
-                                (double)M.corr * (double)ldv(sol + __ldg(M.parent[l] + c)));
-            if (!grid_sync(a.bar, nb, a.status)) return false;
-            for (int64_t c = gtid; c < M.n[l]; c += gstride)
-                M.y[l][c] = (T)((double)ldv(M.x[l] + c) +
-                                w * (double)__ldg(M.dinv[l] + c) * coarse_res(l, c, M.x[l]));
+            const T* sol = (l + 1 == L) ? M.x[L] : M.y[l + 1];
+            const T* bl = M.b[l];
+            const double* dl = M.dinv[l];
+            for (int64_t t = blockIdx.x; t < M.ntiles[l]; t += nb) {
+                const MgTile tile = M.tiles[l][t];
+                const MgLevGeom q = M.lg[l][tile.g];
+                const MgLevGeom qp = M.lg[l + 1][tile.g];
+                __syncthreads();
+                stage(q, tile.x0, tile.y0, [&](int64_t j, int xx, int yy) {
+                    return mw * __ldg(dl + j) * (double)ldv(bl + j) +
+                           mcorr * (double)ldv(sol + qp.off + (int64_t)(yy >> 1) * qp.sx + (xx >> 1));
+                });
+                __syncthreads();
+                const int x = tile.x0 + lane, y = tile.y0 + warp;
+                if (x < q.nx && y < q.ny) {
+                    const int64_t c = q.off + (int64_t)y * q.sx + x;
+                    const double r = (double)ldv(bl + c) - stencil(l, c);
+                    M.y[l][c] = (T)(s_tile[warp + 2][lane + 2] + mw * __ldg(dl + c) * r);
+                }
+            }
             if (!grid_sync(a.bar, nb, a.status)) return false;
         }
-        const T* sol1 = (L == 1) ? M.x[1] : M.y[1];
-        for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
-            int g = a.slice_sys[sl];
-            if (!S[g].inner_active) continue;
-            int64_t row = (int64_t)sl * 32 + lane;
-            int32_t c = __ldg(M.agg + row);
-            if (c >= 0) M.fx[row] = (T)((double)ldv(M.fx + row) + (double)M.corr * (double)ldv(sol1 + c));
+        // fine prolongation f += corr s_1(agg) (four slices of the warp at a time)
+        {
+            const T* sol1 = (L == 1) ? M.x[1] : M.y[1];
+            for (int sl0 = s0 + warp; sl0 < s1; sl0 += 4 * KWARPS) {
+                int32_t cc[4];
+                int64_t rw[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int sl = sl0 + u * KWARPS;
+                    cc[u] = -1;
+                    rw[u] = (int64_t)sl * 32 + lane;
+                    if (sl < s1 && S[a.slice_sys[sl]].inner_active) cc[u] = __ldg(M.agg + rw[u]);
+                }
+                double sv[4], fv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    sv[u] = cc[u] >= 0 ? (double)ldv(sol1 + cc[u]) : 0.0;
+                    fv[u] = cc[u] >= 0 ? (double)ldv(M.fx + rw[u]) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (cc[u] >= 0) M.fx[rw[u]] = (T)(fv[u] + mcorr * sv[u]);
+            }
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
-            int g = a.slice_sys[sl];
+            const int g = a.slice_sys[sl];
             if (!S[g].inner_active) continue;
-            int64_t row = (int64_t)sl * 32 + lane;
-            double r = (double)ldv(in + row) - spmv_row(sl, a.aT, M.fx);
-            out[row] = (T)((double)ldv(M.fx + row) + w * (double)__ldg(M.fdinv + row) * r);
+            const int64_t row = (int64_t)sl * 32 + lane;
+            const double r = (double)ldv(v + row) - spmv_row(sl, a.aT, M.fx);
+            z[row] = (T)((double)ldv(M.fx + row) + mw * __ldg(M.fdinv + row) * r);
         }
         return grid_sync(a.bar, nb, a.status);
     };
@@ -428,6 +556,7 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 double pn = (double)ldv(a.r + row) +
                             S[g].beta * ((double)ldv(a.p + row) - S[g].omega * (double)ldv(a.v + row));
                 a.p[row] = (T)pn;
+                if (a.use_mg) a.mg.fx[row] = (T)(mw * (double)__ldg(a.mg.fdinv + row) * (double)(T)pn);
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
             if (a.use_mg && !vcycle(a.p, a.phat)) { alive = false; break; }
@@ -463,7 +592,9 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
-                a.s[row] = (T)((double)ldv(a.r + row) - S[g].alpha * (double)ldv(a.v + row));
+                const T si = (T)((double)ldv(a.r + row) - S[g].alpha * (double)ldv(a.v + row));
+                a.s[row] = si;
+                if (a.use_mg) a.mg.fx[row] = (T)(mw * (double)__ldg(a.mg.fdinv + row) * (double)si);
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
             if (a.use_mg && !vcycle(a.s, a.shat)) { alive = false; break; }
@@ -596,8 +727,8 @@ vip_status krylov_plan(vip_ctx* c, KrylovPlan& P, const Sell& A, const std::vect
     VIP_CUDA(dalloc(c, &P.blk_s0, nb)); VIP_CUDA(dalloc(c, &P.blk_s1, nb));
     VIP_CUDA(dalloc(c, &P.blk_g0, nb)); VIP_CUDA(dalloc(c, &P.blk_ng, nb));
     VIP_CUDA(dalloc(c, &P.sys_b0, nsys)); VIP_CUDA(dalloc(c, &P.sys_b1, nsys));
-    VIP_CUDA(dalloc(c, &P.partial, (size_t)nb * nsys * NQ));
-    VIP_CUDA(cudaMemsetAsync(P.partial, 0, (size_t)nb * nsys * NQ * sizeof(double), c->stream));
+    VIP_CUDA(dalloc(c, &P.partial, (size_t)2 * nb * nsys * NQ));
+    VIP_CUDA(cudaMemsetAsync(P.partial, 0, (size_t)2 * nb * nsys * NQ * sizeof(double), c->stream));
     VIP_CUDA(dalloc(c, &P.flags, nb));
     VIP_CUDA(dalloc(c, &P.bar, 2));
     VIP_CUDA(dalloc(c, &P.out_iters, nsys)); VIP_CUDA(dalloc(c, &P.out_outer, nsys));
@@ -618,24 +749,25 @@ template <class T>
 static MgDev<T> mg_view(const Multigrid& M) {
     MgDev<T> d;
     memset(&d, 0, sizeof(d));
-    const bool f32 = sizeof(T) == 4;
     d.nlev = M.nlev;
+    d.ngeom = M.ngeom;
     d.agg = M.agg; d.cptr = M.cptr; d.crow = M.crow;
-    d.fdinv = f32 ? (const T*)M.fdinv32 : (const T*)M.fdinv;
+    d.fdinv = M.fdinv;
     d.fr = (T*)M.fr; d.fx = (T*)M.fx;
     for (int l = 1; l <= M.nlev; ++l) {
         const MgLevel& v = M.lev[l];
-        d.n[l] = v.n; d.nbr[l] = v.nbr; d.parent[l] = v.parent; d.child[l] = v.child;
-        d.coef[l] = f32 ? (const T*)v.coef32 : (const T*)v.coef;
-        d.dinv[l] = f32 ? (const T*)v.dinv32 : (const T*)v.dinv;
+        d.n[l] = v.n;
+        d.ntiles[l] = v.ntiles;
+        d.lg[l] = v.lg;
+        d.tiles[l] = v.tiles;
+        d.coefs[l] = v.coefs;
+        d.dinv[l] = v.dinv;
         d.x[l] = (T*)v.x; d.b[l] = (T*)v.b; d.y[l] = (T*)v.y;
     }
     d.omega = 0.8f;
     d.corr = 1.5f;
     d.cinv = M.cinv;
     d.cinv_off = M.cinv_off;
-    d.coff = M.lev[M.nlev].off;
-    d.ngeom = M.ngeom;
     return d;
 }
 

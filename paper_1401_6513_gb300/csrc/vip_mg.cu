@@ -7,8 +7,11 @@
 // product P^T A P of the level above, so the coarse levels inherit the MLS
 // stencils and the boundary rows of the fine operator.  Because the aggregates are
 // lattice cells, every coarse operator is a structured 5 x 5 stencil on a cell
-// lattice (25 coefficients per cell, neighbour table precomputed).  All sums are
-// formed in a fixed order, so the hierarchy is deterministic.
+// lattice (25 coefficients per cell).  The setup works through neighbour, parent
+// and child tables; the V-cycle addresses cells by lattice position instead, with
+// rows padded to a multiple of 32 cells and the stencils stored in slices of 32
+// cells ([slice][offset][lane]) so that a warp reads one contiguous block per
+// slice.  All sums are formed in a fixed order, so the hierarchy is deterministic.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -33,7 +36,7 @@ __global__ void k_mg_agg(int64_t R, const int8_t* __restrict__ rt, const int32_t
     const int nx = G.nx[1], ny = G.ny[1];
     if (G.periodic_x) { cx %= nx; if (cx < 0) cx += nx; } else cx = min(max(cx, 0), nx - 1);
     if (G.periodic_y) { cy %= ny; if (cy < 0) cy += ny; } else cy = min(max(cy, 0), ny - 1);
-    agg[r] = (int32_t)(off1[rg[r]] + (int64_t)cy * nx + cx);
+    agg[r] = (int32_t)(off1[rg[r]] + (int64_t)cy * G.sx[1] + cx);
 }
 
 // neighbour table, parent and children of the cells of one level
@@ -46,8 +49,13 @@ __global__ void k_mg_topology(int64_t ncells, const int32_t* __restrict__ cgeom,
     if (c >= ncells) return;
     int g = cgeom[c];
     const MgGeom& G = mg[g];
-    int nx = G.nx[level], ny = G.ny[level];
+    int nx = G.nx[level], ny = G.ny[level], sx = G.sx[level];
     int x = cx_[c], y = cy_[c];
+    if (x < 0) {  // padding cell
+        for (int o = 0; o < 25; ++o) nbr[(int64_t)o * ncells + c] = -1;
+        if (has_parent) parent[c] = -1;
+        return;
+    }
     for (int dy = -2; dy <= 2; ++dy)
         for (int dx = -2; dx <= 2; ++dx) {
             int xx = x + dx, yy = y + dy;
@@ -55,11 +63,11 @@ __global__ void k_mg_topology(int64_t ncells, const int32_t* __restrict__ cgeom,
             if (G.periodic_x) { xx %= nx; if (xx < 0) xx += nx; } else ok &= xx >= 0 && xx < nx;
             if (G.periodic_y) { yy %= ny; if (yy < 0) yy += ny; } else ok &= yy >= 0 && yy < ny;
             int o = (dy + 2) * 5 + (dx + 2);
-            nbr[(int64_t)o * ncells + c] = ok ? (int32_t)(offl[g] + (int64_t)yy * nx + xx) : -1;
+            nbr[(int64_t)o * ncells + c] = ok ? (int32_t)(offl[g] + (int64_t)yy * sx + xx) : -1;
         }
     if (has_parent) {
         int px = x >> 1, py = y >> 1;
-        parent[c] = (int32_t)(offp[g] + (int64_t)py * G.nx[level + 1] + px);
+        parent[c] = (int32_t)(offp[g] + (int64_t)py * G.sx[level + 1] + px);
     }
 }
 
@@ -122,19 +130,18 @@ __global__ void k_mg_galerkin(int64_t nc, const int64_t* __restrict__ child,  //
     for (int o = 0; o < 25; ++o) ccoef[(int64_t)o * nc + C] = acc[o];
 }
 
-__global__ void k_mg_finish(int64_t n, const double* __restrict__ coef, float* __restrict__ coef32,
-                            double* __restrict__ dinv, float* __restrict__ dinv32) {
+// sliced copy of the stencils ([n/32][25][32]) and the inverse diagonal
+__global__ void k_mg_finish(int64_t n, const double* __restrict__ coef, double* __restrict__ coefs,
+                            double* __restrict__ dinv) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
-    for (int o = 0; o < 25; ++o) coef32[(int64_t)o * n + c] = (float)coef[(int64_t)o * n + c];
+    for (int o = 0; o < 25; ++o) coefs[(c >> 5) * 800 + o * 32 + (c & 31)] = coef[(int64_t)o * n + c];
     double d = coef[(int64_t)12 * n + c];
-    double di = (d != 0.0) ? 1.0 / d : 0.0;
-    dinv[c] = di;
-    dinv32[c] = (float)di;
+    dinv[c] = (d != 0.0) ? 1.0 / d : 0.0;
 }
 
 // fine-level inverse diagonal
-__global__ void k_mg_fine_diag(Sell A, double* __restrict__ dinv, float* __restrict__ dinv32) {
+__global__ void k_mg_fine_diag(Sell A, double* __restrict__ dinv) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= A.nrows) return;
     int64_t base = A.sptr[r >> 5] + (r & 31);
@@ -143,9 +150,7 @@ __global__ void k_mg_fine_diag(Sell A, double* __restrict__ dinv, float* __restr
         int64_t e = base + (int64_t)k * SLICE;
         if (A.col[e] == r) d += A.v64[e];
     }
-    double di = d != 0.0 ? 1.0 / d : 0.0;
-    dinv[r] = di;
-    dinv32[r] = (float)di;
+    dinv[r] = d != 0.0 ? 1.0 / d : 0.0;
 }
 
 // Dense inverse of each geometry's coarsest operator (Gauss-Jordan with partial
@@ -251,22 +256,35 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
                 hg[g].ny[l] = (hg[g].ny[l - 1] + 1) / 2;
             }
     M.nlev = L;  // coarse levels 1..L
+    // row strides: multiples of 32 on the tiled levels (the coarsest level keeps
+    // sx = nx, so its cells are numbered densely for the direct solve)
+    for (int g = 0; g < G; ++g)
+        for (int l = 1; l <= L; ++l) {
+            const int nx = hg[g].nx[l];
+            hg[g].sx[l] = (l == L || nx < 32) ? nx : (nx + 31) / 32 * 32;
+        }
     VIP_CUDA(dalloc(c, &M.geom, G));
     VIP_CUDA(cudaMemcpyAsync(M.geom, hg.data(), G * sizeof(MgGeom), cudaMemcpyHostToDevice, st));
-    // per level: cell offsets, coordinates
+    // per level: cell offsets (each geometry's block a multiple of 32 cells), coordinates
     std::vector<std::vector<int64_t>> offs(L + 2, std::vector<int64_t>(G));
     for (int l = 1; l <= L; ++l) {
         MgLevel& lv = M.lev[l];
         int64_t n = 0;
-        for (int g = 0; g < G; ++g) { offs[l][g] = n; n += (int64_t)hg[g].nx[l] * hg[g].ny[l]; }
+        for (int g = 0; g < G; ++g) {
+            offs[l][g] = n;
+            n += ((int64_t)hg[g].sx[l] * hg[g].ny[l] + 31) / 32 * 32;
+        }
         lv.n = n;
-        std::vector<int32_t> cg(n), cx(n), cy(n);
-        for (int g = 0; g < G; ++g)
+        std::vector<int32_t> cg(n), cx(n, -1), cy(n, -1);
+        for (int g = 0; g < G; ++g) {
+            const int64_t end = (g + 1 < G) ? offs[l][g + 1] : n;
+            for (int64_t id = offs[l][g]; id < end; ++id) cg[id] = g;
             for (int yy = 0; yy < hg[g].ny[l]; ++yy)
                 for (int xx = 0; xx < hg[g].nx[l]; ++xx) {
-                    int64_t id = offs[l][g] + (int64_t)yy * hg[g].nx[l] + xx;
-                    cg[id] = g; cx[id] = xx; cy[id] = yy;
+                    int64_t id = offs[l][g] + (int64_t)yy * hg[g].sx[l] + xx;
+                    cx[id] = xx; cy[id] = yy;
                 }
+        }
         VIP_CUDA(dalloc(c, &lv.cgeom, n)); VIP_CUDA(dalloc(c, &lv.cx, n)); VIP_CUDA(dalloc(c, &lv.cy, n));
         VIP_CUDA(dalloc(c, &lv.off, G));
         VIP_CUDA(cudaMemcpyAsync(lv.cgeom, cg.data(), n * 4, cudaMemcpyHostToDevice, st));
@@ -276,9 +294,24 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         VIP_CUDA(dalloc(c, &lv.nbr, 25 * n));
         VIP_CUDA(dalloc(c, &lv.parent, n));
         VIP_CUDA(dalloc(c, &lv.coef, 25 * n));
-        VIP_CUDA(dalloc(c, &lv.coef32, 25 * n));
+        VIP_CUDA(dalloc(c, &lv.coefs, 25 * n));
         VIP_CUDA(dalloc(c, &lv.dinv, n));
-        VIP_CUDA(dalloc(c, &lv.dinv32, n));
+        {
+            std::vector<MgLevGeom> lgh(G);
+            std::vector<MgTile> th;
+            for (int g = 0; g < G; ++g) {
+                lgh[g] = {offs[l][g], hg[g].nx[l], hg[g].ny[l], hg[g].sx[l], hg[g].periodic_x,
+                          hg[g].periodic_y, 0};
+                for (int y0 = 0; y0 < hg[g].ny[l]; y0 += 32)
+                    for (int x0 = 0; x0 < hg[g].nx[l]; x0 += 32) th.push_back({g, x0, y0, 0});
+            }
+            VIP_CUDA(dalloc(c, &lv.lg, G));
+            VIP_CUDA(cudaMemcpyAsync(lv.lg, lgh.data(), G * sizeof(MgLevGeom), cudaMemcpyHostToDevice, st));
+            lv.ntiles = (int64_t)th.size();
+            VIP_CUDA(dalloc(c, &lv.tiles, th.size()));
+            VIP_CUDA(cudaMemcpyAsync(lv.tiles, th.data(), th.size() * sizeof(MgTile), cudaMemcpyHostToDevice,
+                                     st));
+        }
         for (void** v : {&lv.x, &lv.b, &lv.y}) {
             char* m = nullptr;
             VIP_CUDA(dalloc(c, &m, n * 8));
@@ -303,6 +336,7 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         std::vector<int> cnt(lv.n, 0);
         for (int64_t f = 0; f < (int64_t)par.size(); ++f) {
             int32_t p = par[f];
+            if (p < 0) continue;  // padding cell
             ch[(int64_t)cnt[p] * lv.n + p] = f;
             cnt[p]++;
         }
@@ -349,8 +383,7 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         }
         for (int l = 1; l <= L; ++l) {
             MgLevel& lv = M.lev[l];
-            k_mg_finish<<<(unsigned)((lv.n + TB - 1) / TB), TB, 0, st>>>(lv.n, lv.coef, lv.coef32, lv.dinv,
-                                                                        lv.dinv32);
+            k_mg_finish<<<(unsigned)((lv.n + TB - 1) / TB), TB, 0, st>>>(lv.n, lv.coef, lv.coefs, lv.dinv);
             VIP_CUDA(cudaGetLastError());
         }
     }
@@ -377,8 +410,7 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         M.ngeom = G;
     }
     VIP_CUDA(dalloc(c, &M.fdinv, R));
-    VIP_CUDA(dalloc(c, &M.fdinv32, R));
-    k_mg_fine_diag<<<(unsigned)((R + TB - 1) / TB), TB, 0, st>>>(A, M.fdinv, M.fdinv32);
+    k_mg_fine_diag<<<(unsigned)((R + TB - 1) / TB), TB, 0, st>>>(A, M.fdinv);
     VIP_CUDA(cudaGetLastError());
     {
         char* m = nullptr;

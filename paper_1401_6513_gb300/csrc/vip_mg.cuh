@@ -13,19 +13,36 @@ struct MgGeom {                   // background lattice of one geometry
     double h, x0, y0;
     int32_t periodic_x, periodic_y;
     int32_t nx[MG_MAXLEV + 1], ny[MG_MAXLEV + 1];  // level 0 = lattice, l >= 1 = cells
+    int32_t sx[MG_MAXLEV + 1];    // row stride of level l (nx padded to a multiple of 32)
+};
+
+// One geometry's cell lattice on one coarse level: cell (x, y), x < nx, y < ny, is
+// number off + y * sx + x.  Cells x in [nx, sx) and the tail of the geometry's
+// block (its length is a multiple of 32) are padding: no stencil, never read.
+// px, py flag periodic directions.
+struct MgLevGeom {
+    int64_t off;
+    int32_t nx, ny, sx, px, py, pad;
+};
+
+// 32 x 32 block of one geometry's cells, processed by one CTA.
+struct MgTile {
+    int32_t g, x0, y0, pad;
 };
 
 struct MgLevel {                  // coarse level (all geometries concatenated)
-    int64_t n = 0;
-    int32_t *cgeom = nullptr, *cx = nullptr, *cy = nullptr;
+    int64_t n = 0;                // cells incl. padding (a multiple of 32)
+    int32_t *cgeom = nullptr, *cx = nullptr, *cy = nullptr;  // cx = -1: padding
     int64_t* off = nullptr;       // [G] first cell of each geometry
     int32_t* nbr = nullptr;       // [25][n] neighbour cell of each 5x5 offset (-1: none)
-    int32_t* parent = nullptr;    // [n] cell of the next level
+    int32_t* parent = nullptr;    // [n] cell of the next level (-1: padding)
     int64_t* child = nullptr;     // [4][n] cells of the level above (-1: none)
-    double* coef = nullptr;       // [25][n] Galerkin stencil
-    float* coef32 = nullptr;
-    double* dinv = nullptr;       // [n] inverse diagonal (0 for empty cells)
-    float* dinv32 = nullptr;
+    double* coef = nullptr;       // [25][n] Galerkin stencil (setup layout)
+    double* coefs = nullptr;      // the same, sliced: [n/32][25][32] (V-cycle layout)
+    double* dinv = nullptr;       // [n] inverse diagonal (0 for empty and padding cells)
+    MgLevGeom* lg = nullptr;      // [G] lattice of each geometry on this level
+    MgTile* tiles = nullptr;      // 32 x 32 tiles covering every geometry's lattice
+    int64_t ntiles = 0;
     void *x = nullptr, *b = nullptr, *y = nullptr;  // vectors (FP64 or FP32 view)
 };
 
@@ -38,7 +55,6 @@ struct Multigrid {
     int64_t* cptr = nullptr;      // [n1+1] fine rows of each level-1 cell
     int32_t* crow = nullptr;
     double* fdinv = nullptr;      // [R] inverse diagonal of the fine operator
-    float* fdinv32 = nullptr;
     void* fr = nullptr;           // [R] fine residual scratch
     void* fx = nullptr;           // [R] fine smoothing scratch
     double* cinv = nullptr;       // dense inverse of each geometry's coarsest operator
@@ -46,22 +62,23 @@ struct Multigrid {
     int ngeom = 0;
 };
 
-// Device view of the hierarchy in precision T.
+// Device view of the hierarchy, vectors in precision T (operators in FP64).
 template <class T>
 struct MgDev {
     int nlev;
+    int ngeom;
     const int32_t* agg;
     const int64_t* cptr;
     const int32_t* crow;
-    const T* fdinv;
+    const double* fdinv;
     T* fr;
     T* fx;
     int64_t n[MG_MAXLEV + 1];
-    const int32_t* nbr[MG_MAXLEV + 1];
-    const int32_t* parent[MG_MAXLEV + 1];
-    const int64_t* child[MG_MAXLEV + 1];
-    const T* coef[MG_MAXLEV + 1];
-    const T* dinv[MG_MAXLEV + 1];
+    int64_t ntiles[MG_MAXLEV + 1];
+    const MgLevGeom* lg[MG_MAXLEV + 1];
+    const MgTile* tiles[MG_MAXLEV + 1];
+    const double* coefs[MG_MAXLEV + 1];       // sliced stencils
+    const double* dinv[MG_MAXLEV + 1];
     T* x[MG_MAXLEV + 1];
     T* b[MG_MAXLEV + 1];
     T* y[MG_MAXLEV + 1];
@@ -69,8 +86,6 @@ struct MgDev {
     float corr;        // scaling of the coarse-grid correction (piecewise-constant prolongation)
     const double* cinv;
     const int64_t* cinv_off;
-    const int64_t* coff;  // [G] first cell of each geometry on the coarsest level
-    int ngeom;
 };
 
 }  // namespace vip
