@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="bumpy_h64")
+    ap.add_argument("--workload", default="bumpy_h64",
+                    choices=["bumpy_h64", "cylinder_h32", "cavity_256", "triangles64"])
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -69,6 +70,12 @@ def make_workload(name):
         ns = w.cavity(256, Re=1000.0)
         return ns, {"workload": "lid-driven cavity 256x256, Re=1000", "nodes": ns.n,
                     "Re": 1000.0, "dt": ns.dt}
+    if name == "triangles64":
+        nss = w.triangle_batch(64, seed=20140126)
+        return nss, {"workload": "64 equilateral lid-driven cavities, n_edge ~ U{64..512}, "
+                                 "Re ~ U[100,1000], seed 20140126, one context",
+                     "nodes": int(sum(ns.n for ns in nss)), "geometries": len(nss),
+                     "dt": "0.25 h per geometry"}
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -80,6 +87,9 @@ def cpu_sample(name):
         ns = w.channel_body(h, ("sines", 1.0, [(0.05, 12), (0.02, 31)]), Re=200.0, dt=0.1 * h,
                             xlim=(-2.0, 3.0), ylim=(-1.5, 1.5))
         return ns, "same body, h, Re and dt on the channel cropped to [-2,3]x[-1.5,1.5]"
+    if name == "triangles64":
+        ns = min(w.triangle_batch(64, seed=20140126), key=lambda g: g.n)
+        return ns, f"the batch's smallest geometry ({ns.name})"
     ns, _ = make_workload(name)
     return ns, "full workload"
 
@@ -206,6 +216,26 @@ def run_reference(args, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def poisson_bytes_per_iter(nnz, rows, tb):
+    """Algorithmic DRAM bytes of one inner iteration of the multigrid-preconditioned
+    BiCGSTAB (vectors of tb bytes, int32 columns):
+      * six passes over the operator entries (value + column): two Krylov SpMVs and
+        the two fine-level residuals of each of the two V-cycles;
+      * 48 row-sized vector accesses: p update 6, each V-cycle's fine level 11.5
+        (residual 3, restriction 1.5, prolongation 3, smoothing 4), v 3, s 5, t 3,
+        x/r update 8;
+      * the coarse levels, 442 B per level-1 cell per V-cycle (25 FP64 coefficients,
+        inverse diagonal and vectors, down and up), a quarter of a cell per row and
+        4/3 of it over all levels: 147 B per row per V-cycle."""
+    return 6 * nnz * (tb + 4) + 48 * tb * rows + 2 * 147 * rows
+
+
+def poisson_bytes_per_pass(nnz, rows, tb):
+    """One FP64 refinement pass: the FP64 residual SpMV, b, x and the five vectors it
+    initialises, and the correction x += d."""
+    return nnz * 12 + rows * (8 + 8 + 5 * tb) + rows * (8 + 8 + tb)
+
+
 def main():
     args = parse()
     rank, ws, local = dist_init()
@@ -222,12 +252,13 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     ns, cfg = make_workload(args.workload)
+    nss = ns if isinstance(ns, list) else [ns]
     prec = vip.VIP_PREC_MIXED if args.precision == "mixed" else vip.VIP_PREC_FP64
     t0 = time.perf_counter()
-    ctx = vip.solver_for(ns, precision=prec, rtol=1e-8, max_iters=50000, device=dev,
+    ctx = vip.solver_for(nss, precision=prec, rtol=1e-8, max_iters=50000, device=dev,
                          stream=stream.cuda_stream)
     setup_s = time.perf_counter() - t0
-    N = ns.n
+    N = int(sum(g.n for g in nss))
     ctx.vip_step(args.warmup)
     torch.cuda.synchronize()
     s0 = ctx.vip_get_stats()
@@ -263,25 +294,27 @@ def main():
     nnz_p = int(ptr[-1])
     rows_p = int(ptr.size - 1)
     tb = 4 if prec == vip.VIP_PREC_MIXED else 8
-    # per inner iteration: 2 SpMVs over the stored entries (value + int32 column) and
-    # 20 vector accesses per row; per refinement pass: one FP64 SpMV and 14 FP64-sized
-    # row accesses (x gather, b, five inits, correction read/write)
-    bytes_p = it_p * (2 * nnz_p * (tb + 4) + 20 * tb * rows_p) + \
-        out_p * (nnz_p * 12 + rows_p * (8 + 8 + 5 * tb + 8 + 8 + tb))
+    bytes_p = it_p * poisson_bytes_per_iter(nnz_p, rows_p, tb) + \
+        out_p * poisson_bytes_per_pass(nnz_p, rows_p, tb)
     t_pois = prof["poisson"] / 1e3
     pk, pk_src = peaks()
     hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     achieved = bytes_p / t_pois / 1e9 if t_pois > 0 else 0.0
-    # ---- end to end through the C ABI with pinned host buffers
-    k2 = args.e2e_steps or max(1, min(args.steps, 5))
+    # ---- end to end through the C ABI with pinned host buffers: every step loads the
+    # state from host memory, steps, and reads the new state back into host memory,
+    # from which the next step starts (the integration continues; same work per step)
+    k2 = args.e2e_steps or args.steps
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     u, v, p, phi = ctx.vip_get_state()
-    hu, hv, hp = pin(u), pin(v), pin(p)
-    ou, ov, op, oph = (torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(4))
+    bufs = [(pin(u), pin(v), pin(p)), tuple(torch.empty(N, dtype=torch.float64).pin_memory()
+                                            for _ in range(3))]
+    oph = torch.empty(N, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     barrier(ws)
     t0 = time.perf_counter()
-    for _ in range(k2):
+    for k in range(k2):
+        hu, hv, hp = bufs[k % 2]
+        ou, ov, op = bufs[(k + 1) % 2]
         ctx.vip_load_state(hu, hv, hp)
         ctx.vip_step(1)
         ctx.vip_get_state(ou, ov, op, oph)
@@ -296,7 +329,7 @@ def main():
     if ws == 1 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
         cpu = time_oracle(args.workload, 1, 0)
-    cfg.update({"global_batch": 1, "parallelism": f"replicas x{ws}", "precision": args.precision,
+    cfg.update({"global_batch": len(nss), "parallelism": f"replicas x{ws}", "precision": args.precision,
                 "l2": "working set > L2 (no flush needed)", "setup_s": round(setup_s, 2),
                 "poisson_iters_per_step": it_p / max(args.steps, 1),
                 "poisson_outer_per_step": out_p / max(args.steps, 1),

@@ -266,8 +266,10 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
     };
 
     // One V-cycle z = M^{-1} v of the aggregation multigrid: a V(1,1)-cycle with
-    // damped Jacobi smoothing from zero, summed restriction, piecewise-constant
-    // prolongation and a scaled coarse correction:
+    // l1-Jacobi smoothing from zero (D = sign(a_ii) sum_j |a_ij|, which stays a
+    // convergent smoother on boundary rows that are not diagonally dominant),
+    // summed restriction, piecewise-constant prolongation and a scaled coarse
+    // correction:
     //   fine, down:   f = w Df^{-1} v (written by the Krylov update that produces v),
     //                 fr = v - A f,  b_1 = sum of fr over the rows of each cell
     //   level l+1:    b_{l+1}(C) = sum over the children c of C of (b_l - A_l x_l)(c),
@@ -764,7 +766,7 @@ static MgDev<T> mg_view(const Multigrid& M) {
         d.dinv[l] = v.dinv;
         d.x[l] = (T*)v.x; d.b[l] = (T*)v.b; d.y[l] = (T*)v.y;
     }
-    d.omega = 0.8f;
+    d.omega = 1.0f;
     d.corr = 1.5f;
     d.cinv = M.cinv;
     d.cinv_off = M.cinv_off;

@@ -130,27 +130,33 @@ __global__ void k_mg_galerkin(int64_t nc, const int64_t* __restrict__ child,  //
     for (int o = 0; o < 25; ++o) ccoef[(int64_t)o * nc + C] = acc[o];
 }
 
-// sliced copy of the stencils ([n/32][25][32]) and the inverse diagonal
+// sliced copy of the stencils ([n/32][25][32]) and the l1-Jacobi scaling
+// sign(a_cc) / sum_o |a_co| of the smoother (0 for empty and padding cells)
 __global__ void k_mg_finish(int64_t n, const double* __restrict__ coef, double* __restrict__ coefs,
                             double* __restrict__ dinv) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
-    for (int o = 0; o < 25; ++o) coefs[(c >> 5) * 800 + o * 32 + (c & 31)] = coef[(int64_t)o * n + c];
+    double s = 0.0;
+    for (int o = 0; o < 25; ++o) {
+        coefs[(c >> 5) * 800 + o * 32 + (c & 31)] = coef[(int64_t)o * n + c];
+        s += fabs(coef[(int64_t)o * n + c]);
+    }
     double d = coef[(int64_t)12 * n + c];
-    dinv[c] = (d != 0.0) ? 1.0 / d : 0.0;
+    dinv[c] = (s != 0.0) ? (d < 0.0 ? -1.0 : 1.0) / s : 0.0;
 }
 
-// fine-level inverse diagonal
+// fine-level l1-Jacobi scaling sign(a_rr) / sum_k |a_rk|
 __global__ void k_mg_fine_diag(Sell A, double* __restrict__ dinv) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= A.nrows) return;
     int64_t base = A.sptr[r >> 5] + (r & 31);
-    double d = 0.0;
+    double d = 0.0, s = 0.0;
     for (int k = 0; k < A.rowlen[r]; ++k) {
         int64_t e = base + (int64_t)k * SLICE;
         if (A.col[e] == r) d += A.v64[e];
+        s += fabs(A.v64[e]);
     }
-    dinv[r] = d != 0.0 ? 1.0 / d : 0.0;
+    dinv[r] = s != 0.0 ? (d < 0.0 ? -1.0 : 1.0) / s : 0.0;
 }
 
 // Dense inverse of each geometry's coarsest operator (Gauss-Jordan with partial

@@ -39,7 +39,7 @@ struct MgLevel {                  // coarse level (all geometries concatenated)
     int64_t* child = nullptr;     // [4][n] cells of the level above (-1: none)
     double* coef = nullptr;       // [25][n] Galerkin stencil (setup layout)
     double* coefs = nullptr;      // the same, sliced: [n/32][25][32] (V-cycle layout)
-    double* dinv = nullptr;       // [n] inverse diagonal (0 for empty and padding cells)
+    double* dinv = nullptr;       // [n] l1-Jacobi scaling (0 for empty and padding cells)
     MgLevGeom* lg = nullptr;      // [G] lattice of each geometry on this level
     MgTile* tiles = nullptr;      // 32 x 32 tiles covering every geometry's lattice
     int64_t ntiles = 0;
@@ -54,7 +54,7 @@ struct Multigrid {
     int32_t* agg = nullptr;       // [R] level-1 cell of a fine row (-1: none)
     int64_t* cptr = nullptr;      // [n1+1] fine rows of each level-1 cell
     int32_t* crow = nullptr;
-    double* fdinv = nullptr;      // [R] inverse diagonal of the fine operator
+    double* fdinv = nullptr;      // [R] l1-Jacobi scaling of the fine operator
     void* fr = nullptr;           // [R] fine residual scratch
     void* fx = nullptr;           // [R] fine smoothing scratch
     double* cinv = nullptr;       // dense inverse of each geometry's coarsest operator
@@ -82,7 +82,7 @@ struct MgDev {
     T* x[MG_MAXLEV + 1];
     T* b[MG_MAXLEV + 1];
     T* y[MG_MAXLEV + 1];
-    float omega;       // Jacobi damping
+    float omega;       // smoother damping
     float corr;        // scaling of the coarse-grid correction (piecewise-constant prolongation)
     const double* cinv;
     const int64_t* cinv_off;
