@@ -49,6 +49,11 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--warm-start", choices=["previous", "learned"], default="previous",
+                    help="initial guess of the pressure-increment solve: the previous "
+                         "increment, or the network trained on this run's own solves")
+    ap.add_argument("--ws-samples", type=int, default=24)
+    ap.add_argument("--ws-epochs", type=int, default=20)
     return ap.parse_args()
 
 
@@ -260,6 +265,25 @@ def main():
     setup_s = time.perf_counter() - t0
     N = int(sum(g.n for g in nss))
     ctx.vip_step(args.warmup)
+    ws_info = None
+    twin = None
+    if args.warm_start == "learned":
+        # a twin context takes the same steps with the previous-increment guess, so the
+        # iteration counts compare step for step at the same residual
+        twin = vip.solver_for(nss, precision=prec, rtol=1e-8, max_iters=50000, device=dev,
+                              stream=stream.cuda_stream)
+        twin.vip_step(args.warmup + args.ws_samples + 2)
+        # collect solved increments, train, then use the network's guess (untimed)
+        t1 = time.perf_counter()
+        ctx.vip_ws_collect(True, args.ws_samples)
+        ctx.vip_step(args.ws_samples)
+        ctx.vip_ws_collect(False)
+        tc = ctx.vip_ws_train(epochs=args.ws_epochs, lr=1e-3, seed=7)
+        ctx.vip_ws_enable(True)
+        ctx.vip_step(2)
+        ws_info = {"guess": "learned", "samples": args.ws_samples, "epochs": args.ws_epochs,
+                   "first_loss": tc.first_loss, "final_loss": tc.final_loss,
+                   "collect_train_s": round(time.perf_counter() - t1, 2)}
     torch.cuda.synchronize()
     s0 = ctx.vip_get_stats()
     # ---- timed region: K steps, device time by CUDA events on the library's stream
@@ -284,6 +308,13 @@ def main():
     ctx.vip_set_profiling(False)
     prof, nprof = ctx.vip_get_profile()
     s1 = ctx.vip_get_stats()
+    if twin is not None:
+        t0s = twin.vip_get_stats()
+        twin.vip_step(args.steps)
+        t1s = twin.vip_get_stats()
+        twin.close()
+        ws_info["poisson_iters_per_step_previous_guess_same_steps"] = \
+            (t1s.total_poisson_iters - t0s.total_poisson_iters) / max(args.steps, 1)
     ms_max = max_over_ranks(ms, ws)
     value = N * args.steps * ws / (ms_max / 1e3)
     # ---- roofline of the Poisson BiCGSTAB launch (one per step)
@@ -335,7 +366,8 @@ def main():
                 "poisson_outer_per_step": out_p / max(args.steps, 1),
                 "helmholtz_iters_per_step": it_h / max(args.steps, 1),
                 "phase_ms_per_step": {k: round(v / max(nprof, 1), 3) for k, v in prof.items()},
-                "last_poisson_relres": st.poisson_relres, "status": st.status})
+                "last_poisson_relres": st.poisson_relres, "status": st.status,
+                "warm_start": ws_info or {"guess": "previous increment"}})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -348,7 +380,9 @@ def main():
                          "bytes_per_step": bytes_p / max(args.steps, 1)},
             "e2e": {"value": N * k2 * ws / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 4 * 8 * N},
-            "gpu_launches": 6 * args.steps,
+            # per step: rhs, Helmholtz, divergence, Poisson, stats, projection; the learned
+            # guess adds scales, scatter, six convolutions and gather
+            "gpu_launches": (6 + (9 if ws_info else 0)) * args.steps,
             "clocks": clk}
     if cpu is not None:
         line["cpu_baseline"] = cpu

@@ -371,17 +371,24 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
             }
             if (!grid_sync(a.bar, nb, a.status)) return false;
         }
-        // coarsest level: x_L = A_L^{-1} b_L with each geometry's dense FP64 inverse
-        // (one row per thread of the grid; cells numbered densely on this level)
-        for (int gg = 0; gg < M.ngeom; ++gg) {
-            const MgLevGeom q = M.lg[L][gg];
-            const int64_t m = (int64_t)q.nx * q.ny;
-            const double* Ai = M.cinv + __ldg(M.cinv_off + gg);
-            for (int64_t i = gtid; i < m; i += gstride) {
-                double sum = 0.0;
-                for (int64_t j = 0; j < m; ++j) sum += __ldg(Ai + i * m + j) * (double)ldv(M.b[L] + q.off + j);
-                M.x[L][q.off + i] = (T)sum;
+        // coarsest level: x_L = A_L^{-1} b_L with each geometry's dense FP64 inverse;
+        // one thread per coarsest cell of any geometry (cells numbered densely per
+        // geometry on this level, geometry found by bisection on the offsets)
+        for (int64_t c = gtid; c < M.n[L]; c += gstride) {
+            int lo = 0, hi = M.ngeom - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (M.lg[L][mid].off <= c) lo = mid;
+                else hi = mid - 1;
             }
+            const MgLevGeom q = M.lg[L][lo];
+            const int64_t m = (int64_t)q.nx * q.ny;
+            const int64_t i = c - q.off;
+            if (i >= m) continue;  // padding at the end of the geometry's block
+            const double* Ai = M.cinv + __ldg(M.cinv_off + lo) + i * m;
+            double sum = 0.0;
+            for (int64_t j = 0; j < m; ++j) sum += __ldg(Ai + j) * (double)ldv(M.b[L] + q.off + j);
+            M.x[L][c] = (T)sum;
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int l = L - 1; l >= 1; --l) {
