@@ -212,12 +212,28 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
             (&sacc[0][0][0])[i] = 0.0;
         __syncthreads();
     };
-    // accumulate a row's contributions q[0..nq) (warp-collective)
+    // Dot-product contributions are summed per lane in registers over all the
+    // warp's rows of one system and reduced across the warp once per phase (the
+    // FP64 butterfly is costly on this GPU's FP64 pipe); a warp whose slices change
+    // system flushes at the change.  The order is fixed, so sums are deterministic.
+    double qacc[NQ];
+    int qj = -1;
+    auto flush_acc = [&](int nq) {  // warp-uniform
+        if (qj >= 0)
+            for (int k = 0; k < nq; ++k) {
+                const double w = wsum(qacc[k]);
+                if (lane == 0) sacc[warp][qj][k] += w;
+            }
+        qj = -1;
+    };
+    // accumulate a row's contributions q[0..nq) for system j (warp-uniform j)
     auto acc = [&](int j, int nq, const double* q) {
-        for (int k = 0; k < nq; ++k) {
-            double w = wsum(q[k]);
-            if (lane == 0) sacc[warp][j][k] += w;
+        if (j != qj) {
+            flush_acc(nq);
+            qj = j;
+            for (int k = 0; k < nq; ++k) qacc[k] = 0.0;
         }
+        for (int k = 0; k < nq; ++k) qacc[k] += q[k];
     };
     // block partials -> global, barrier, totals of every system -> stot.
     // Layout partial[(g * NQ + k) * nb + block]: the blocks of one system are a
@@ -229,6 +245,7 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
     const int ng_blk = a.blk_ng[bid];
     int pset = 0;
     auto reduce = [&](int nq) -> bool {
+        flush_acc(nq);
         __syncthreads();
         double* part = a.partial + (int64_t)pset * nsys * NQ * nb;
         pset ^= 1;
