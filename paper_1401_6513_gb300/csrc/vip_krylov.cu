@@ -48,40 +48,31 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
     asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
 }
-__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // Grid barrier for a cooperative launch; returns false after a timeout.
-// bar[0] counts arrivals, bar[1] is the generation.  Thread 0 of each block
-// arrives with an acquire-release add (publishing the block's writes, which the
-// CTA barrier has ordered before it); the last arrival resets the count and
-// releases the next generation; the others poll it with acquire loads.  So every
-// write before the barrier happens before every read after it, for weak loads too.
-// The wait gives up after 2 s (VIP_ERR_TIMEOUT).
+// bar[0] is an arrival counter whose top bit flips once per barrier: thread 0 of
+// CTA 0 adds 2^31 - (nblocks - 1), every other CTA adds 1, so the counter moves by
+// exactly 2^31 per barrier and its top bit changes precisely when the last CTA has
+// arrived (partial sums stay below the next multiple of 2^31).  Each CTA polls the
+// same word until its top bit differs from the value it saw when arriving, so no
+// separate release store has to travel after the last arrival.  The arrival is an
+// acquire-release add and the poll an acquire load: every write before the barrier
+// happens before every read after it, for weak loads too.  The counter must start
+// at 0.  A wait gives up after 2 s (VIP_ERR_TIMEOUT), or early when another CTA has
+// already reported a timeout.
 __device__ bool grid_sync(uint32_t* bar, unsigned nblocks, int32_t* status) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = ld_volatile_i(status) != VIP_ERR_TIMEOUT;
-        if (ok) {
-            const unsigned gen = ld_acquire(bar + 1);
-            const unsigned arrived = atom_add_acq_rel(bar, 1u);
-            if (arrived == nblocks - 1) {
-                st_relaxed(bar, 0u);
-                st_release(bar + 1, gen + 1u);
-            } else {
-                const uint64_t t0 = gtimer();
-                while (ld_acquire(bar + 1) == gen) {
-                    if (gtimer() - t0 > 2000000000ull) {
-                        set_status(status, VIP_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
-                }
+        int ok = 1;
+        const unsigned add = blockIdx.x == 0 ? 0x80000000u - (nblocks - 1u) : 1u;
+        const unsigned old = atom_add_acq_rel(bar, add);
+        const uint64_t t0 = gtimer();
+        for (unsigned k = 1; ((ld_acquire(bar) ^ old) & 0x80000000u) == 0; ++k) {
+            if ((k & 63u) == 0 && (ld_volatile_i(status) == VIP_ERR_TIMEOUT || gtimer() - t0 > 2000000000ull)) {
+                set_status(status, VIP_ERR_TIMEOUT);
+                ok = 0;
+                break;
             }
         }
         s_ok = ok;
