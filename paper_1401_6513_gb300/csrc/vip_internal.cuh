@@ -62,7 +62,7 @@ struct GeomDev {
 };
 
 // Work split of a persistent Krylov launch over a batch of systems.
-constexpr int MAXSYS_PB = 8;    // systems a block may touch
+constexpr int MAXSYS_PB = 16;   // systems a block may touch
 constexpr int NQ = 4;           // reduced quantities per phase
 struct KrylovPlan {
     int nblocks = 0, nthreads = 0, nsys = 0;
@@ -75,6 +75,8 @@ struct KrylovPlan {
     int32_t* blk_ng = nullptr;      // [nblocks] number of systems of the block
     int32_t* sys_b0 = nullptr;      // [nsys] block range of a system
     int32_t* sys_b1 = nullptr;
+    int32_t* sys_s0 = nullptr;      // [nsys] slice range of a system
+    int32_t* sys_s1 = nullptr;
     double* partial = nullptr;      // [2][nsys][NQ][nblocks]: two sets, alternate reductions
     int32_t* flags = nullptr;       // [nblocks]
     uint32_t* bar = nullptr;        // [2] barrier count / generation
@@ -177,6 +179,9 @@ vip_status build_all(vip_ctx* c);
 // Krylov (vip_krylov.cu)
 vip_status krylov_plan(vip_ctx* c, KrylovPlan& plan, const Sell& A,
                        const std::vector<int64_t>& sys_row0, const std::vector<int64_t>& sys_rows);
+// Re-partition the plan's slices over its blocks in proportion to rows x the
+// iterations each system needed in its last solve (device side, stream-ordered).
+vip_status krylov_replan(vip_ctx* c, const KrylovPlan& plan, cudaStream_t s);
 vip_status krylov_solve(vip_ctx* c, const KrylovPlan& plan, const Sell& A, const double* b,
                         double* x, int precision, double rtol, int32_t max_iters,
                         double inner_rtol, const Multigrid* mg = nullptr);
