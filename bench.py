@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--warm-start", choices=["previous", "learned"], default="previous",
                     help="initial guess of the pressure-increment solve: the previous "
                          "increment, or the network trained on this run's own solves")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default multigrid parameters (omega 1.0, corr 1.5)")
     ap.add_argument("--ws-samples", type=int, default=24)
     ap.add_argument("--ws-epochs", type=int, default=20)
     return ap.parse_args()
@@ -264,6 +266,9 @@ def main():
                          stream=stream.cuda_stream)
     setup_s = time.perf_counter() - t0
     N = int(sum(g.n for g in nss))
+    # multigrid parameters tuned on this workload (one step, then back to the initial
+    # fields; untimed)
+    tune = vip.autotune(ctx, nss) if not args.no_autotune else None
     ctx.vip_step(args.warmup)
     ws_info = None
     twin = None
@@ -272,6 +277,8 @@ def main():
         # iteration counts compare step for step at the same residual
         twin = vip.solver_for(nss, precision=prec, rtol=1e-8, max_iters=50000, device=dev,
                               stream=stream.cuda_stream)
+        if tune:
+            twin.vip_set_multigrid(tune["omega"], tune["corr"])
         twin.vip_step(args.warmup + args.ws_samples + 2)
         # collect solved increments, train, then use the network's guess (untimed)
         t1 = time.perf_counter()
@@ -367,7 +374,8 @@ def main():
                 "helmholtz_iters_per_step": it_h / max(args.steps, 1),
                 "phase_ms_per_step": {k: round(v / max(nprof, 1), 3) for k, v in prof.items()},
                 "last_poisson_relres": st.poisson_relres, "status": st.status,
-                "warm_start": ws_info or {"guess": "previous increment"}})
+                "warm_start": ws_info or {"guess": "previous increment"},
+                "multigrid": tune or {"omega": 1.0, "corr": 1.5, "autotuned": False}})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,

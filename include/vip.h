@@ -221,6 +221,33 @@ vip_status vip_convection(vip_ctx* ctx, const double* u, const double* v, double
 vip_status vip_solve(vip_ctx* ctx, int which, const double* b, double* x, int precision,
                      double rtol, int32_t max_iters, int32_t* iters, double* relres);
 
+/* ---- multigrid parameters and their autotuner --------------------------------
+ * Not part of the paper's method: the Poisson solve of Eq. (13) is preconditioned
+ * by an aggregation multigrid V-cycle (l1-Jacobi smoothing with damping omega,
+ * coarse-grid correction scaled by corr; defaults 1.0 and 1.5).  Both change the
+ * iteration count only, never the residual the solve stops at. */
+vip_status vip_set_multigrid(vip_ctx* ctx, float omega, float corr);
+
+#define VIP_TUNE_MAX 16
+typedef struct {
+    int32_t ncand;                 /* candidates tried (nomega x ncorr) */
+    int32_t best;                  /* index of the chosen candidate */
+    float omega[VIP_TUNE_MAX];     /* candidate k: omega[k], corr[k] */
+    float corr[VIP_TUNE_MAX];
+    int32_t iters[VIP_TUNE_MAX];   /* Poisson BiCGSTAB iterations (max over geometries) */
+    double ms[VIP_TUNE_MAX];       /* device time of the solve, -1 if it failed */
+} vip_tune_result;
+
+/* Time the pressure-increment solve of the last step (its right-hand side, from a
+ * zero initial guess, to the context's tolerance) for every pair of omegas[0..nomega)
+ * and corrs[0..ncorr) (at most VIP_TUNE_MAX pairs; omega in (0, 1.5], corr in (0, 3]),
+ * apply the fastest pair that converged (as vip_set_multigrid) and report all of them.
+ * Needs vip_build, the multigrid and at least one vip_step since vip_set_state; the
+ * state is not changed.  Allocates one R-double scratch vector per call, owned by
+ * the context (freed by vip_destroy).  Synchronous. */
+vip_status vip_autotune(vip_ctx* ctx, const float* omegas, int32_t nomega, const float* corrs,
+                        int32_t ncorr, vip_tune_result* out);
+
 /* ---- learned warm start of the pressure-increment solve ------------------
  * Not part of the paper's method: a 6-layer 3x3 convolutional network (BF16
  * tensor-core kernels, FP32 accumulation) on each geometry's regular background

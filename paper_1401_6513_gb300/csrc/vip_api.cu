@@ -206,6 +206,81 @@ vip_status vip_set_flow(vip_ctx* c, int32_t geom, double Re, double dt) {
     return VIP_OK;
 }
 
+vip_status vip_set_multigrid(vip_ctx* c, float omega, float corr) {
+    if (!c) return VIP_ERR_ARG;
+    if (!(omega > 0.0f && omega <= 1.5f)) return fail(c, VIP_ERR_ARG, "omega must be in (0, 1.5]");
+    if (!(corr > 0.0f && corr <= 3.0f)) return fail(c, VIP_ERR_ARG, "corr must be in (0, 3]");
+    if ((omega != c->mg.omega || corr != c->mg.corr) && c->graph) {
+        cudaGraphExecDestroy(c->graph);  // the captured launch holds the old values
+        c->graph = nullptr;
+    }
+    c->mg.omega = omega;
+    c->mg.corr = corr;
+    return VIP_OK;
+}
+
+vip_status vip_autotune(vip_ctx* c, const float* omegas, int32_t nomega, const float* corrs, int32_t ncorr,
+                        vip_tune_result* out) {
+    if (!c || !omegas || !corrs || !out) return VIP_ERR_ARG;
+    if (!c->built) return fail(c, VIP_ERR_ARG, "vip_autotune before vip_build");
+    if (!c->use_mg || !c->mg.built) return fail(c, VIP_ERR_ARG, "vip_autotune: no multigrid");
+    if (c->host_steps < 1) return fail(c, VIP_ERR_ARG, "vip_autotune: take a step first");
+    if (nomega < 1 || ncorr < 1 || nomega * ncorr > VIP_TUNE_MAX)
+        return fail(c, VIP_ERR_ARG, "vip_autotune: 1 to VIP_TUNE_MAX candidate pairs");
+    for (int i = 0; i < nomega; ++i)
+        if (!(omegas[i] > 0.0f && omegas[i] <= 1.5f)) return fail(c, VIP_ERR_ARG, "omega must be in (0, 1.5]");
+    for (int i = 0; i < ncorr; ++i)
+        if (!(corrs[i] > 0.0f && corrs[i] <= 3.0f)) return fail(c, VIP_ERR_ARG, "corr must be in (0, 3]");
+    cudaStream_t st = c->stream;
+    double* x = nullptr;
+    VIP_CUDA(dalloc(c, &x, (size_t)c->R));
+    cudaEvent_t e0, e1;
+    VIP_CUDA(cudaEventCreate(&e0));
+    VIP_CUDA(cudaEventCreate(&e1));
+    memset(out, 0, sizeof(*out));
+    const float keep_w = c->mg.omega, keep_c = c->mg.corr;
+    int best = -1;
+    vip_status s = VIP_OK;
+    for (int i = 0; i < nomega && s == VIP_OK; ++i)
+        for (int j = 0; j < ncorr && s == VIP_OK; ++j) {
+            const int k = i * ncorr + j;
+            c->mg.omega = omegas[i];
+            c->mg.corr = corrs[j];
+            out->omega[k] = omegas[i];
+            out->corr[k] = corrs[j];
+            if (cudaMemsetAsync(x, 0, c->R * sizeof(double), st) != cudaSuccess ||
+                cudaMemsetAsync(c->d_status, 0, 4, st) != cudaSuccess ||
+                cudaEventRecord(e0, st) != cudaSuccess) { s = VIP_ERR_CUDA; break; }
+            s = krylov_solve(c, c->plan_pois, c->T.pois, c->prhs, x, c->precision, c->rtol, c->max_iters,
+                             c->inner_rtol, &c->mg);
+            if (s != VIP_OK) break;
+            std::vector<int32_t> it(c->plan_pois.nsys);
+            int32_t hs = 0;
+            float ms = 0.0f;
+            if (cudaEventRecord(e1, st) != cudaSuccess ||
+                cudaMemcpyAsync(it.data(), c->plan_pois.out_iters, it.size() * 4, cudaMemcpyDeviceToHost, st) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(&hs, c->d_status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                s = VIP_ERR_CUDA;
+                break;
+            }
+            out->iters[k] = *std::max_element(it.begin(), it.end());
+            out->ms[k] = hs ? -1.0 : (double)ms;  // a candidate that did not converge is out
+            if (!hs && (best < 0 || out->ms[k] < out->ms[best])) best = k;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaMemsetAsync(c->d_status, 0, 4, st);
+    out->ncand = nomega * ncorr;
+    c->mg.omega = keep_w;
+    c->mg.corr = keep_c;
+    if (s != VIP_OK) return s;
+    if (best < 0) return fail(c, VIP_ERR_NOT_CONVERGED, "vip_autotune: no candidate converged");
+    out->best = best;
+    return vip_set_multigrid(c, out->omega[best], out->corr[best]);
+}
+
 vip_status vip_set_solver(vip_ctx* c, int precision, double rtol, int32_t max_iters, int identity) {
     if (!c) return VIP_ERR_ARG;
     if (precision != VIP_PREC_FP64 && precision != VIP_PREC_MIXED) return fail(c, VIP_ERR_ARG, "bad precision");

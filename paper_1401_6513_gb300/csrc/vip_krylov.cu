@@ -861,8 +861,8 @@ static MgDev<T> mg_view(const Multigrid& M) {
         d.dinv[l] = v.dinv;
         d.x[l] = (T*)v.x; d.b[l] = (T*)v.b; d.y[l] = (T*)v.y;
     }
-    d.omega = 1.0f;
-    d.corr = 1.5f;
+    d.omega = M.omega;
+    d.corr = M.corr;
     d.cinv = M.cinv;
     d.cinv_off = M.cinv_off;
     return d;

@@ -60,6 +60,8 @@ struct Multigrid {
     double* cinv = nullptr;       // dense inverse of each geometry's coarsest operator
     int64_t* cinv_off = nullptr;  // [G] offset of geometry g's block in cinv
     int ngeom = 0;
+    float omega = 1.0f;           // smoother damping (vip_set_multigrid / vip_autotune)
+    float corr = 1.5f;            // scaling of the coarse-grid correction
 };
 
 // Device view of the hierarchy, vectors in precision T (operators in FP64).

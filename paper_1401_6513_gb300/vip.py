@@ -33,7 +33,9 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_get_state", "vip_get_stats", "vip_get_sizes", "vip_stencil_info",
            "vip_get_stencil", "vip_apply", "vip_convection", "vip_solve", "vip_load_state",
            "vip_set_profiling", "vip_get_profile", "vip_ws_collect", "vip_ws_train",
-           "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static"]
+           "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static",
+           "vip_set_multigrid", "vip_autotune"]
+VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
 
@@ -48,6 +50,18 @@ class StepStats(C.Structure):
 class TrainCfg(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64),
                 ("first_loss", C.c_double), ("final_loss", C.c_double)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("ncand", C.c_int32), ("best", C.c_int32), ("omega", C.c_float * VIP_TUNE_MAX),
+                ("corr", C.c_float * VIP_TUNE_MAX), ("iters", C.c_int32 * VIP_TUNE_MAX),
+                ("ms", C.c_double * VIP_TUNE_MAX)]
+
+    def as_dict(self):
+        n = self.ncand
+        return {"omega": self.omega[self.best], "corr": self.corr[self.best],
+                "candidates": [{"omega": round(self.omega[k], 4), "corr": round(self.corr[k], 4),
+                                "iters": self.iters[k], "ms": round(self.ms[k], 3)} for k in range(n)]}
 
 
 class VipError(RuntimeError):
@@ -99,6 +113,9 @@ def lib(path: str | Path | None = None):
         "vip_ws_eval": ([vp, i32, i32, vp, vp, vp, vp, vp, C.POINTER(dbl)], C.c_int),
         "vip_bicgstab_static": ([C.c_int, vp, i64, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(i32),
                                  C.POINTER(dbl)], C.c_int),
+        "vip_set_multigrid": ([vp, C.c_float, C.c_float], C.c_int),
+        "vip_autotune": ([vp, C.POINTER(C.c_float), i32, C.POINTER(C.c_float), i32,
+                          C.POINTER(TuneResult)], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -203,6 +220,18 @@ class Context:
         return dict(zip(PHASES, list(ms))), n.value
 
     # -- learned warm start ------------------------------------------------------
+    def vip_set_multigrid(self, omega=1.0, corr=1.5):
+        self._check(self.L.vip_set_multigrid(self.h, float(omega), float(corr)))
+
+    def vip_autotune(self, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.7, 1.9, 2.1)) -> TuneResult:
+        """Time the last step's pressure-increment solve for every (omega, corr) pair
+        and apply the fastest; returns the report."""
+        om = (C.c_float * len(omegas))(*omegas)
+        co = (C.c_float * len(corrs))(*corrs)
+        res = TuneResult()
+        self._check(self.L.vip_autotune(self.h, om, len(omegas), co, len(corrs), C.byref(res)))
+        return res
+
     def vip_ws_collect(self, enable=True, max_samples=0):
         self._check(self.L.vip_ws_collect(self.h, 1 if enable else 0, int(max_samples)))
 
@@ -296,6 +325,46 @@ def vip_bicgstab_static(device, stream, n, row_ptr, col, val, b, x, rtol=1e-10, 
                                    _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(b), _ptr(x),
                                    float(rtol), int(max_iters), C.byref(it), C.byref(rr))
     return st, it.value, rr.value
+
+
+def geometry_signature(nodesets) -> str:
+    """Key of a set of node sets for the autotuning cache: names, node counts and a
+    hash of the coordinates and kinds."""
+    import hashlib
+    hsh = hashlib.sha1()
+    parts = []
+    for ns in nodesets:
+        parts.append(f"{ns.name}:{ns.n}")
+        hsh.update(np.ascontiguousarray(ns.x, dtype=np.float64).tobytes())
+        hsh.update(np.ascontiguousarray(ns.y, dtype=np.float64).tobytes())
+        hsh.update(np.ascontiguousarray(ns.kind, dtype=np.uint8).tobytes())
+    return "|".join(parts) + "|" + hsh.hexdigest()[:16]
+
+
+def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.7, 1.9, 2.1)):
+    """Pick the multigrid parameters of a context built from `nodesets`: from the JSON
+    file `cache` when it has this geometry signature, else by vip_autotune after one
+    step (the state is then reset to the node sets' initial fields) and stored there.
+    Returns the chosen {"omega", "corr", ...} entry."""
+    import json
+    key = geometry_signature(nodesets)
+    table = {}
+    if cache is not None and Path(cache).exists():
+        table = json.loads(Path(cache).read_text())
+    if key in table:
+        entry = table[key]
+        ctx.vip_set_multigrid(entry["omega"], entry["corr"])
+        return dict(entry, cached=True)
+    ctx.vip_step(1)
+    entry = ctx.vip_autotune(omegas, corrs).as_dict()
+    ctx.vip_set_state(np.concatenate([ns.u0 for ns in nodesets]),
+                      np.concatenate([ns.v0 for ns in nodesets]),
+                      np.concatenate([ns.p0 for ns in nodesets]))
+    if cache is not None:
+        table[key] = entry
+        Path(cache).parent.mkdir(parents=True, exist_ok=True)
+        Path(cache).write_text(json.dumps(table, indent=1))
+    return dict(entry, cached=False)
 
 
 def solver_for(nodesets, precision=VIP_PREC_MIXED, rtol=1e-8, max_iters=20000,

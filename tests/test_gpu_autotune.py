@@ -1,0 +1,59 @@
+"""Autotuning of the multigrid parameters (vip_autotune / vip_set_multigrid) and
+its JSON cache, through the C ABI.  The parameters change iteration counts only:
+the tuned context steps to the same state as an untuned one, within the solver
+tolerance (both solve to relative residual 1e-10, so states agree to ~1e-8)."""
+import numpy as np
+import pytest
+
+import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_chooses_fastest_converged_candidate(vip, tmp_path):
+    ns = w.cavity(32, Re=400.0)
+    ctx = vip.solver_for(ns, precision=vip.VIP_PREC_FP64, rtol=1e-10)
+    cache = tmp_path / "tune.json"
+    entry = vip.autotune(ctx, [ns], cache=cache, omegas=(0.9, 1.0), corrs=(1.3, 1.5))
+    assert not entry["cached"]
+    cands = entry["candidates"]
+    assert len(cands) == 4
+    good = [c for c in cands if c["ms"] >= 0]
+    assert good
+    chosen = [c for c in cands if c["omega"] == round(entry["omega"], 4) and c["corr"] == round(entry["corr"], 4)]
+    assert chosen and chosen[0]["ms"] == min(c["ms"] for c in good)
+    assert all(c["iters"] > 0 for c in good)
+
+    ref = vip.solver_for(ns, precision=vip.VIP_PREC_FP64, rtol=1e-10)
+    ctx.vip_step(5)
+    ref.vip_step(5)
+    u1, v1, p1, _ = ctx.vip_get_state()
+    u0, v0, p0, _ = ref.vip_get_state()
+    assert ctx.vip_get_stats().status == 0
+    assert np.linalg.norm(u1 - u0) <= 1e-7 * np.linalg.norm(u0)
+    assert np.linalg.norm(p1 - p0) <= 1e-6 * np.linalg.norm(p0)
+    ref.close()
+
+    other = vip.solver_for(ns, precision=vip.VIP_PREC_FP64, rtol=1e-10)
+    again = vip.autotune(other, [ns], cache=cache)
+    assert again["cached"] and again["omega"] == entry["omega"] and again["corr"] == entry["corr"]
+    other.close()
+    ctx.close()
+
+
+def test_autotune_arguments(vip):
+    ns = w.cavity(16, Re=100.0)
+    ctx = vip.solver_for(ns, precision=vip.VIP_PREC_FP64)
+    with pytest.raises(vip.VipError):      # no step taken yet
+        ctx.vip_autotune((1.0,), (1.5,))
+    ctx.vip_step(1)
+    with pytest.raises(vip.VipError):      # omega out of range
+        ctx.vip_autotune((2.0,), (1.5,))
+    with pytest.raises(vip.VipError):      # too many pairs
+        ctx.vip_autotune(tuple(0.5 + 0.05 * i for i in range(5)), (1.0, 1.2, 1.4, 1.6))
+    with pytest.raises(vip.VipError):
+        ctx.vip_set_multigrid(1.0, 0.0)
+    ctx.vip_set_multigrid(0.9, 1.4)
+    ctx.vip_step(2)
+    assert ctx.vip_get_stats().status == 0
+    ctx.close()
