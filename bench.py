@@ -293,6 +293,7 @@ def main():
                    "collect_train_s": round(time.perf_counter() - t1, 2)}
     torch.cuda.synchronize()
     s0 = ctx.vip_get_stats()
+    g0_iters = ctx.vip_get_geometry_iters()
     # ---- timed region: K steps, device time by CUDA events on the library's stream
     uuid = None
     try:
@@ -332,8 +333,20 @@ def main():
     nnz_p = int(ptr[-1])
     rows_p = int(ptr.size - 1)
     tb = 4 if prec == vip.VIP_PREC_MIXED else 8
-    bytes_p = it_p * poisson_bytes_per_iter(nnz_p, rows_p, tb) + \
-        out_p * poisson_bytes_per_pass(nnz_p, rows_p, tb)
+    # per geometry: a converged system stops iterating inside the shared launch, so the
+    # algorithmic bytes are summed over geometries with their own iteration counts
+    g_iters = ctx.vip_get_geometry_iters() - g0_iters
+    bytes_p, off, kb = 0, 0, 0
+    for gi, g in enumerate(nss):
+        nnz_g = int(ptr[off + g.n] - ptr[off])
+        rows_g = g.n
+        if g.n + off <= N and not np.any(g.kind == vip.VIP_NODE_OUTLET):  # closed: bordered row
+            nnz_g += int(ptr[N + kb + 1] - ptr[N + kb])
+            rows_g += 1
+            kb += 1
+        bytes_p += int(g_iters[gi]) * poisson_bytes_per_iter(nnz_g, rows_g, tb)
+        off += g.n
+    bytes_p += out_p * poisson_bytes_per_pass(nnz_p, rows_p, tb)
     t_pois = prof["poisson"] / 1e3
     pk, pk_src = peaks()
     hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))

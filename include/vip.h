@@ -192,6 +192,13 @@ vip_status vip_get_profile(vip_ctx* ctx, double* phase_ms, int64_t* nsteps);
 /* Statistics of the last step (synchronises).  Returns the device status. */
 vip_status vip_get_stats(vip_ctx* ctx, vip_step_stats* out);
 
+/* Poisson BiCGSTAB iterations of each geometry (int64 per geometry, in the order
+ * the geometries were added), summed over the steps since vip_set_state.  In a
+ * context with several geometries all systems are solved by one launch and a
+ * system that has converged stops iterating, so these are the per-geometry work
+ * counts (vip_get_stats reports the maximum).  Synchronises. */
+vip_status vip_get_geometry_iters(vip_ctx* ctx, int64_t* poisson_iters);
+
 /* Total node count N and the number of geometries. */
 vip_status vip_get_sizes(vip_ctx* ctx, int64_t* n_nodes, int32_t* n_geoms);
 

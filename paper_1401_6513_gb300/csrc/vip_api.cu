@@ -26,10 +26,11 @@ __global__ void k_check_finite(const double* __restrict__ a, const int8_t* __res
 }
 
 __global__ void k_stats(const int32_t* __restrict__ it, const int32_t* __restrict__ outer, int nsys,
-                        const int32_t* __restrict__ hit, int nhsys, int64_t* __restrict__ tot) {
+                        const int32_t* __restrict__ hit, int nhsys, int64_t* __restrict__ tot,
+                        int64_t* __restrict__ git) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         int m = 0, o = 0, hm = 0;
-        for (int g = 0; g < nsys; ++g) { m = max(m, it[g]); o = max(o, outer[g]); }
+        for (int g = 0; g < nsys; ++g) { m = max(m, it[g]); o = max(o, outer[g]); git[g] += it[g]; }
         for (int g = 0; g < nhsys; ++g) hm = max(hm, hit[g]);
         tot[0] += m;
         tot[1] += 1;
@@ -82,7 +83,7 @@ vip_status do_step(vip_ctx* c, cudaStream_t s) {
     if ((st = cnn_after_solve(c, s)) != VIP_OK) return st;
     VIP_CUDA(cudaEventRecord(c->ev[4], s));
     k_stats<<<1, 32, 0, s>>>(c->plan_pois.out_iters, c->plan_pois.out_outer, c->plan_pois.nsys,
-                             c->plan_helm.out_iters, c->plan_helm.nsys, c->d_stats);
+                             c->plan_helm.out_iters, c->plan_helm.nsys, c->d_stats, c->d_giters);
     // several geometries: give the next step's Poisson solve a block partition
     // weighted by this step's iteration counts
     if ((st = krylov_replan(c, c->plan_pois, s)) != VIP_OK) return st;
@@ -206,6 +207,15 @@ vip_status vip_set_flow(vip_ctx* c, int32_t geom, double Re, double dt) {
     return VIP_OK;
 }
 
+vip_status vip_get_geometry_iters(vip_ctx* c, int64_t* poisson_iters) {
+    if (!c || !poisson_iters) return VIP_ERR_ARG;
+    if (!c->built) return fail(c, VIP_ERR_ARG, "vip_get_geometry_iters before vip_build");
+    VIP_CUDA(cudaMemcpyAsync(poisson_iters, c->d_giters, c->geoms.size() * 8, cudaMemcpyDeviceToHost,
+                             c->stream));
+    VIP_CUDA(cudaStreamSynchronize(c->stream));
+    return VIP_OK;
+}
+
 vip_status vip_set_multigrid(vip_ctx* c, float omega, float corr) {
     if (!c) return VIP_ERR_ARG;
     if (!(omega > 0.0f && omega <= 1.5f)) return fail(c, VIP_ERR_ARG, "omega must be in (0, 1.5]");
@@ -304,6 +314,8 @@ vip_status vip_build(vip_ctx* c) {
     if (c->geoms.empty()) return fail(c, VIP_ERR_ARG, "no nodes");
     VIP_CUDA(cudaSetDevice(c->device));
     const int G = (int)c->geoms.size();
+    VIP_CUDA(dalloc(c, &c->d_giters, (size_t)G));
+    VIP_CUDA(cudaMemsetAsync(c->d_giters, 0, G * sizeof(int64_t), c->stream));
     int64_t R = 0;
     c->nbordered = 0;
     for (Geom& g : c->geoms) {
@@ -421,6 +433,7 @@ vip_status vip_set_state(vip_ctx* c, const double* u, const double* v, const dou
     VIP_CUDA(cudaMemsetAsync(c->nv_prev, 0, c->R * 8, st));
     VIP_CUDA(cudaMemsetAsync(c->d_step, 0, 8, st));
     VIP_CUDA(cudaMemsetAsync(c->d_stats, 0, 32, st));
+    VIP_CUDA(cudaMemsetAsync(c->d_giters, 0, c->geoms.size() * 8, st));
     int32_t hs = 0;
     VIP_CUDA(cudaMemcpyAsync(&hs, c->d_status, 4, cudaMemcpyDeviceToHost, st));
     VIP_CUDA(cudaStreamSynchronize(st));

@@ -163,6 +163,7 @@ struct vip_ctx {
     void* shat = nullptr;
     // per-step statistics on the device
     int64_t* d_stats = nullptr;     // [4] poisson inner iters, steps, poisson outer, helm iters
+    int64_t* d_giters = nullptr;    // [G] Poisson inner iterations of each geometry since vip_set_state
     cudaGraphExec_t graph = nullptr;
     int64_t host_steps = 0;
     // phase events recorded inside every step (also inside the graph)

@@ -34,7 +34,7 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_get_stencil", "vip_apply", "vip_convection", "vip_solve", "vip_load_state",
            "vip_set_profiling", "vip_get_profile", "vip_ws_collect", "vip_ws_train",
            "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static",
-           "vip_set_multigrid", "vip_autotune"]
+           "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters"]
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -114,6 +114,7 @@ def lib(path: str | Path | None = None):
         "vip_bicgstab_static": ([C.c_int, vp, i64, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(i32),
                                  C.POINTER(dbl)], C.c_int),
         "vip_set_multigrid": ([vp, C.c_float, C.c_float], C.c_int),
+        "vip_get_geometry_iters": ([vp, vp], C.c_int),
         "vip_autotune": ([vp, C.POINTER(C.c_float), i32, C.POINTER(C.c_float), i32,
                           C.POINTER(TuneResult)], C.c_int),
     }
@@ -220,6 +221,13 @@ class Context:
         return dict(zip(PHASES, list(ms))), n.value
 
     # -- learned warm start ------------------------------------------------------
+    def vip_get_geometry_iters(self):
+        """Poisson iterations of each geometry since vip_set_state (numpy int64)."""
+        _, g = self.sizes()
+        out = np.zeros(g, np.int64)
+        self._check(self.L.vip_get_geometry_iters(self.h, _ptr(out)))
+        return out
+
     def vip_set_multigrid(self, omega=1.0, corr=1.5):
         self._check(self.L.vip_set_multigrid(self.h, float(omega), float(corr)))
 

@@ -42,6 +42,9 @@ def test_batch_matches_oracle_per_geometry(vip):
     ctx.vip_step(nsteps)
     st = ctx.vip_get_stats()
     assert st.status == 0
+    # per-geometry work counts: every system iterated, none more than the lock-step maximum
+    gi = ctx.vip_get_geometry_iters()
+    assert gi.shape == (len(nss),) and np.all(gi > 0) and gi.max() <= st.total_poisson_iters
     u, v, p, _ = ctx.vip_get_state()
     sizes = [ns.n for ns in nss]
     for ns, ug, vg, pg in zip(nss, split(u, sizes), split(v, sizes), split(p, sizes)):
