@@ -1,15 +1,18 @@
-// 3x3 convolution of the warm-start network as an implicit GEMM on the tensor
-// cores with warp-level mma.sync (m16n8k16, BF16 x BF16 -> FP32).
+// 3x3 convolution of the warm-start network as an implicit GEMM on the 5th-generation
+// tensor cores (tcgen05, kind::f16: BF16 x BF16 -> FP32 accumulators in TMEM).
 //
-// A CTA of four warps loops over tiles of 128 consecutive pixels of one lattice
-// row (persistent grid).  Per tile it stages the 3 x 130 halo of the input in
-// shared memory, channel-chunk planar: plane[c][row][col] holds channels
-// 8c..8c+7 (16 bytes) of one pixel, so the nine taps read the same planes at
-// shifted pixel offsets (no im2col copy).  The weights stay in shared memory for
-// the whole launch as [tap][chunk][cout][8 ci].  Warp w owns pixels 32w..32w+31 of
-// the tile (two m16 tiles) and all output channels (Cout/8 n8 tiles); the K loop
-// runs over 9 taps x Cin/16.  Fragments are read with 32-bit shared loads
-// (two consecutive channels), which are bank-conflict free in this layout.
+// A CTA owns one TMEM accumulator of 128 lanes x Cout columns and loops over tiles
+// of 128 consecutive pixels of one lattice row (persistent grid).  Per tile it
+// stages the 3 x 130 halo of the input in shared memory, channel-chunk planar:
+// plane[c][row][col] holds channels 8c..8c+7 (16 bytes) of one pixel.  In that
+// layout the 8-pixel x 8-channel core matrices of the MMA operand A are 128
+// contiguous bytes, so every one of the nine taps is the same operand seen from a
+// shifted start address -- no im2col copy.  The weights sit in shared memory for the
+// whole launch in the same core-matrix layout ([tap][chunk][cout][8 ci]).  One
+// thread issues 9 * Cin/16 MMAs (K = 16 each) and commits them to an mbarrier; the
+// four warps then read their 32 TMEM lanes with tcgen05.ld and run the epilogue.
+// Four CTAs share an SM, so one CTA's staging overlaps another's MMAs and epilogue.
+// Every mbarrier wait is bounded (2 s, then VIP_ERR_TIMEOUT); TMEM is always freed.
 #include <algorithm>
 #include <cstdio>
 
@@ -18,45 +21,171 @@
 namespace vip {
 
 constexpr int PLANE_COLS = CNN_TILE + 2;               // 130
-constexpr int PLANE_ELEMS = 3 * PLANE_COLS * 8;        // bf16 per chunk plane
+constexpr int PLANE_BYTES = 3 * PLANE_COLS * 16;       // 6240
 constexpr int MAX_CHUNKS = CNN_CH / 8;                 // 4
+constexpr int SMEM_IN = MAX_CHUNKS * PLANE_BYTES;      // 24960
+constexpr int SMEM_W = 9 * MAX_CHUNKS * CNN_CH * 16;   // 18432
+// Operands, the mbarrier, the TMEM address word and the failure flag: small enough
+// for four CTAs (4 x 32 TMEM columns) per SM, so one CTA's staging overlaps another's
+// MMAs and epilogue.
+constexpr int SMEM_CONV = SMEM_IN + SMEM_W + 32;
 
-__device__ __forceinline__ uint32_t ld_s32(const __nv_bfloat16* p) {
-    return *reinterpret_cast<const uint32_t*>(p);
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                               uint32_t b1) {
+// Shared-memory matrix descriptor, no swizzle, K-major operand: start address,
+// leading-dimension (K direction) and stride-dimension (M/N direction) byte
+// offsets between 8x16-byte core matrices, all >> 4, and the descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and
+// B (bits 7-9 = 1, 10-12 = 1), both K-major, N/8 at bit 17, M/16 at bit 24.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
     asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 
-template <int COUT>
-__global__ void __launch_bounds__(128) k_conv_mma(CnnConvArgs a) {
-    __shared__ __align__(16) __nv_bfloat16 s_in[MAX_CHUNKS * PLANE_ELEMS];
-    __shared__ __align__(16) __nv_bfloat16 s_w[9 * MAX_CHUNKS * CNN_CH * 8];
-    constexpr int NT = COUT / 8;  // n8 tiles
+// Bounded wait for the phase with the given parity; false after 2 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    uint64_t t0 = gtime();
+    while (!mbar_try_wait(bar, parity)) {
+        if (gtime() - t0 > 2000000000ull) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(128) k_conv_tc(CnnConvArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* s_in = smem;
+    uint8_t* s_w = smem + SMEM_IN;
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + SMEM_IN + SMEM_W);
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + SMEM_IN + SMEM_W + 8);
+    int* s_fail = reinterpret_cast<int*>(smem + SMEM_IN + SMEM_W + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int grp = lane >> 2, tig = lane & 3;
-    const int cin = a.cin;
+    const int cin = a.cin, cout = a.cout;
     const int nch = cin / 8;
-    // weights [tap][chunk][cout][8]
-    const int wvec = 9 * nch * COUT;  // 16-byte vectors
-    for (int i = tid; i < wvec; i += blockDim.x)
+    const int ncol = 32;  // TMEM columns (power of two >= cout)
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(s_tmem)), "r"(ncol));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(s_bar, 1);
+        *s_fail = 0;
+    }
+    // weights, already in [tap][chunk][cout][8] order: one 16-byte copy per thread step
+    const int wbytes = 9 * nch * cout * 16;
+    for (int i = tid; i < wbytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(s_w)[i] = reinterpret_cast<const uint4*>(a.wpack)[i];
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+    const uint32_t idesc = umma_idesc(CNN_TILE, cout);
+    const uint32_t in_base = smem_u32(s_in);
+    const uint32_t w_base = smem_u32(s_w);
+    uint32_t phase = 0;
 
     for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         int im = 0;
         while (im + 1 < a.nimg && a.img[im + 1].tile0 <= tile) ++im;
         const CnnImage I = a.img[im];
         const int64_t tloc = tile - I.tile0;
-        const int tpr = (I.W + CNN_TILE - 1) / CNN_TILE;
+        const int tpr = (I.W + CNN_TILE - 1) / CNN_TILE;  // tiles per row
         const int y = (int)(tloc / tpr);
         const int x0 = (int)(tloc % tpr) * CNN_TILE;
-        __syncthreads();  // previous tile's reads of s_in are done
+        // stage the halo: planes [chunk][3][130] x 16 bytes, zero outside the image
         const int nitem = nch * 3 * PLANE_COLS;
         for (int i = tid; i < nitem; i += blockDim.x) {
             int c = i / (3 * PLANE_COLS);
@@ -69,74 +198,81 @@ __global__ void __launch_bounds__(128) k_conv_mma(CnnConvArgs a) {
                 const int64_t cell = I.off + (int64_t)yy * I.W + xx;
                 v = *reinterpret_cast<const uint4*>(a.x + cell * cin + c * 8);
             }
-            *reinterpret_cast<uint4*>(s_in + c * PLANE_ELEMS + (r * PLANE_COLS + col) * 8) = v;
+            *reinterpret_cast<uint4*>(s_in + c * PLANE_BYTES + (r * PLANE_COLS + col) * 16) = v;
         }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
         __syncthreads();
-        float acc[2][NT][4];
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-#pragma unroll
-            for (int n = 0; n < NT; ++n)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) acc[m][n][q] = 0.0f;
-        for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap % 3;
-            for (int kc = 0; kc < nch / 2; ++kc) {
-                const __nv_bfloat16* p0 = s_in + (2 * kc) * PLANE_ELEMS + (dy * PLANE_COLS + dx) * 8;
-                const __nv_bfloat16* p1 = p0 + PLANE_ELEMS;
-                uint32_t af[2][4];
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    const int px = warp * 32 + m * 16 + grp;
-                    af[m][0] = ld_s32(p0 + px * 8 + tig * 2);
-                    af[m][1] = ld_s32(p0 + (px + 8) * 8 + tig * 2);
-                    af[m][2] = ld_s32(p1 + px * 8 + tig * 2);
-                    af[m][3] = ld_s32(p1 + (px + 8) * 8 + tig * 2);
+        if (tid == 0) {
+            tc_fence_after();
+            uint32_t acc = 0;
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap % 3;  // 0..2 = offset + 1
+                for (int kc = 0; kc < nch / 2; ++kc) {
+                    uint32_t aaddr = in_base + (2 * kc) * PLANE_BYTES + (dy * PLANE_COLS + dx) * 16;
+                    uint32_t baddr = w_base + (tap * nch + 2 * kc) * cout * 16;
+                    uint64_t ad = umma_desc(aaddr, PLANE_BYTES, 128);
+                    uint64_t bd = umma_desc(baddr, cout * 16, 128);
+                    umma_bf16(tmem, ad, bd, idesc, acc);
+                    acc = 1;
                 }
-                const __nv_bfloat16* w0 = s_w + ((tap * nch + 2 * kc) * COUT) * 8;
-                const __nv_bfloat16* w1 = w0 + COUT * 8;
-#pragma unroll
-                for (int n = 0; n < NT; ++n) {
-                    const int co = n * 8 + grp;
-                    uint32_t b0 = ld_s32(w0 + co * 8 + tig * 2);
-                    uint32_t b1 = ld_s32(w1 + co * 8 + tig * 2);
-#pragma unroll
-                    for (int m = 0; m < 2; ++m) mma_bf16_16816(acc[m][n], af[m], b0, b1);
+            }
+            umma_commit(s_bar);
+        }
+        bool ok = mbar_wait_bounded(s_bar, phase);
+        phase ^= 1u;
+        if (!ok) {
+            set_status(a.status, VIP_ERR_TIMEOUT);
+            *s_fail = 1;
+        }
+        tc_fence_after();
+        __syncthreads();
+        if (*s_fail) break;
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 = pixels x0 + 32w + lane
+        float v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        if (cout == 32) tmem_ld_x32(taddr, v);
+        else tmem_ld_x16(taddr, v);
+        const int x = x0 + warp * 32 + lane;
+        if (x < I.W) {
+            const int64_t cell = I.off + (int64_t)y * I.W + x;
+            if (a.epi == EPI_F32_CH0) {
+                a.y32[cell] = v[0] + (a.bias ? a.bias[0] : 0.0f);
+            } else {
+                uint32_t packed[16];
+                for (int c2 = 0; c2 < cout / 2; ++c2) {
+                    float p0 = v[2 * c2], p1 = v[2 * c2 + 1];
+                    if (a.epi == EPI_RELU_BF16) {
+                        p0 = fmaxf(p0 + a.bias[2 * c2], 0.0f);
+                        p1 = fmaxf(p1 + a.bias[2 * c2 + 1], 0.0f);
+                    } else {  // gradient through the ReLU of the layer below
+                        const __nv_bfloat16* m = a.mask + cell * cout;
+                        p0 = __bfloat162float(m[2 * c2]) > 0.0f ? p0 : 0.0f;
+                        p1 = __bfloat162float(m[2 * c2 + 1]) > 0.0f ? p1 : 0.0f;
+                    }
+                    packed[c2] = pack_bf16(p0, p1);
                 }
+                uint4* dst = reinterpret_cast<uint4*>(a.y + cell * cout);
+                for (int q = 0; q < cout / 8; ++q)
+                    dst[q] = make_uint4(packed[4 * q], packed[4 * q + 1], packed[4 * q + 2],
+                                        packed[4 * q + 3]);
             }
         }
-        // epilogue: the thread holds rows grp, grp + 8 and columns 2 tig, 2 tig + 1 of each tile
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-#pragma unroll
-            for (int hrow = 0; hrow < 2; ++hrow) {
-                const int x = x0 + warp * 32 + m * 16 + grp + hrow * 8;
-                if (x >= I.W) continue;
-                const int64_t cell = I.off + (int64_t)y * I.W + x;
-#pragma unroll
-                for (int n = 0; n < NT; ++n) {
-                    const int co = n * 8 + tig * 2;
-                    float v0 = acc[m][n][2 * hrow], v1 = acc[m][n][2 * hrow + 1];
-                    if (a.epi == EPI_F32_CH0) {
-                        if (co == 0) a.y32[cell] = v0 + (a.bias ? a.bias[0] : 0.0f);
-                        continue;
-                    }
-                    if (a.epi == EPI_RELU_BF16) {
-                        v0 = fmaxf(v0 + a.bias[co], 0.0f);
-                        v1 = fmaxf(v1 + a.bias[co + 1], 0.0f);
-                    } else {  // gradient through the ReLU of the layer below
-                        const __nv_bfloat16* mk = a.mask + cell * COUT + co;
-                        v0 = __bfloat162float(mk[0]) > 0.0f ? v0 : 0.0f;
-                        v1 = __bfloat162float(mk[1]) > 0.0f ? v1 : 0.0f;
-                    }
-                    *reinterpret_cast<__nv_bfloat162*>(a.y + cell * COUT + co) =
-                        __floats2bfloat162_rn(v0, v1);
-                }
-            }
+        tc_fence_before();
+        __syncthreads();
     }
+    // a failed wait may leave MMAs in flight: wait once more (bounded) before freeing TMEM
+    if (*s_fail && tid == 0) mbar_wait_bounded(s_bar, phase ^ 1u);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncol));
 }
 
-cudaError_t cnn_conv_init() { return cudaSuccess; }
+cudaError_t cnn_conv_init() {
+    return cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CONV);
+}
 
 cudaError_t cnn_conv_fwd(const CnnConvArgs& a, int nsm, cudaStream_t s, const char** why) {
     *why = "";
@@ -150,9 +286,8 @@ cudaError_t cnn_conv_fwd(const CnnConvArgs& a, int nsm, cudaStream_t s, const ch
         *why = "unsupported channel counts";
         return cudaErrorInvalidValue;
     }
-    int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)std::max(nsm, 1) * 4);
-    if (a.cout == 32) k_conv_mma<32><<<grid, 128, 0, s>>>(a);
-    else k_conv_mma<16><<<grid, 128, 0, s>>>(a);
+    const int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)std::max(nsm, 1) * 4);
+    k_conv_tc<<<grid, 128, SMEM_CONV, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) *why = "kernel launch";
     return e;
