@@ -223,6 +223,14 @@ def run_reference(args, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes per inner iteration of the Poisson launch, from one ncu capture of the
+# same workload and kernel (dram__bytes_read.sum + dram__bytes_write.sum of a launch of
+# 97 iterations, profiles/k_bicgstab_poisson_bumpy_h64.md); every iteration streams
+# the same operator and vectors, so a launch's traffic scales with its iterations.
+# Measured on the current k_bicgstab; to be re-measured whenever the kernel changes.
+TRAFFIC_PER_ITER = {("bumpy_h64", "fp64"): 296.63e9 / 97.0}
+
+
 def poisson_bytes_per_iter(nnz, rows, tb):
     """Algorithmic DRAM bytes of one inner iteration of the multigrid-preconditioned
     BiCGSTAB (vectors of tb bytes, int32 columns):
@@ -348,6 +356,8 @@ def main():
         off += g.n
     bytes_p += out_p * poisson_bytes_per_pass(nnz_p, rows_p, tb)
     t_pois = prof["poisson"] / 1e3
+    tpi = TRAFFIC_PER_ITER.get((args.workload, args.precision))
+    traffic = tpi * it_p / max(args.steps, 1) if tpi else None  # per launch (one per step)
     pk, pk_src = peaks()
     hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     achieved = bytes_p / t_pois / 1e9 if t_pois > 0 else 0.0
@@ -395,7 +405,7 @@ def main():
             "dtype": "f32-inner/f64" if args.precision == "mixed" else "f64",
             "data": "synthetic", "config": cfg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
+                         "frac": achieved / hbm, "traffic": traffic,
                          "kernel": "k_bicgstab (Poisson)",
                          "peak_source": f"hbm_gbs {pk_src}",
                          "bytes_per_step": bytes_p / max(args.steps, 1)},
