@@ -169,6 +169,12 @@ def dist_init():
     return rank, ws, local
 
 
+def throughput(n_nodes, steps, ws, ms_max):
+    """Whole-job node-updates/s: every rank steps its own replica of n_nodes nodes, so
+    the job processes n_nodes x steps x ws node updates in the slowest rank's time."""
+    return n_nodes * steps * ws / (ms_max / 1e3)
+
+
 def barrier(ws):
     if ws > 1:
         import torch.distributed as dist
@@ -332,7 +338,7 @@ def main():
         ws_info["poisson_iters_per_step_previous_guess_same_steps"] = \
             (t1s.total_poisson_iters - t0s.total_poisson_iters) / max(args.steps, 1)
     ms_max = max_over_ranks(ms, ws)
-    value = N * args.steps * ws / (ms_max / 1e3)
+    value = throughput(N, args.steps, ws, ms_max)
     # ---- roofline of the Poisson BiCGSTAB launch (one per step)
     it_p = s1.total_poisson_iters - s0.total_poisson_iters
     out_p = s1.total_poisson_outer - s0.total_poisson_outer
