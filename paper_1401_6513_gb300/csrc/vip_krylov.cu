@@ -381,9 +381,10 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
             if (!grid_sync(a.bar, nb, a.status)) return false;
         }
         // coarsest level: x_L = A_L^{-1} b_L with each geometry's dense FP64 inverse;
-        // one thread per coarsest cell of any geometry (cells numbered densely per
-        // geometry on this level, geometry found by bisection on the offsets)
-        for (int64_t c = gtid; c < M.n[L]; c += gstride) {
+        // one warp per coarsest cell of any geometry (cells numbered densely per
+        // geometry on this level, geometry found by bisection on the offsets), lanes
+        // over the row, then a fixed-order warp sum
+        for (int64_t c = gtid >> 5; c < M.n[L]; c += gstride >> 5) {
             int lo = 0, hi = M.ngeom - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
@@ -393,11 +394,13 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
             const MgLevGeom q = M.lg[L][lo];
             const int64_t m = (int64_t)q.nx * q.ny;
             const int64_t i = c - q.off;
-            if (i >= m || !S[lo].inner_active) continue;  // padding, or a finished geometry
+            if (i >= m || !S[lo].inner_active) continue;  // padding, or a finished geometry (warp-uniform)
             const double* Ai = M.cinv + __ldg(M.cinv_off + lo) + i * m;
+            const T* bL = M.b[L] + q.off;
             double sum = 0.0;
-            for (int64_t j = 0; j < m; ++j) sum += __ldg(Ai + j) * (double)ldv(M.b[L] + q.off + j);
-            M.x[L][c] = (T)sum;
+            for (int64_t j = lane; j < m; j += 32) sum += __ldg(Ai + j) * (double)ldv(bL + j);
+            sum = wsum(sum);
+            if (lane == 0) M.x[L][c] = (T)sum;
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int l = L - 1; l >= 1; --l) {

@@ -159,63 +159,42 @@ __global__ void k_mg_fine_diag(Sell A, double* __restrict__ dinv) {
     dinv[r] = s != 0.0 ? (d < 0.0 ? -1.0 : 1.0) / s : 0.0;
 }
 
-// Dense inverse of each geometry's coarsest operator (Gauss-Jordan with partial
-// pivoting in shared memory, one block per geometry).  Cells without a row
-// (empty cells) are decoupled: their unknown stays 0.
-__global__ void k_mg_coarse_inv(const double* __restrict__ coef, const int32_t* __restrict__ nbr, int64_t n,
-                                const int64_t* __restrict__ off, const MgGeom* __restrict__ mg, int L,
-                                const int64_t* __restrict__ ioff, double* __restrict__ inv) {
-    extern __shared__ double sm[];
-    const int g = blockIdx.x;
-    const int m = mg[g].nx[L] * mg[g].ny[L];
-    const int64_t c0 = off[g];
-    double* A = sm;              // [m][2m]
+// Dense inverse of one geometry's coarsest operator, A (m x m, row-major), by
+// Gauss-Jordan elimination with partial pivoting in FP64 on the host (setup only).
+// Cells without a row (empty cells) are decoupled: their unknown stays 0.  The
+// result is stored row-major, inv[i * m + j] = (A^{-1})_{ij}.
+static void coarse_inverse(std::vector<double>& A, int m, double* inv) {
     const int w = 2 * m;
-    for (int i = threadIdx.x; i < m * w; i += blockDim.x) A[i] = 0.0;
-    __syncthreads();
-    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    std::vector<double> T((size_t)m * w, 0.0);
+    for (int r = 0; r < m; ++r) {
         bool empty = true;
-        for (int o = 0; o < 25; ++o) {
-            int32_t j = nbr[(int64_t)o * n + c0 + r];
-            double a = coef[(int64_t)o * n + c0 + r];
-            if (j >= 0 && a != 0.0) {
-                A[r * w + (int)(j - c0)] += a;
-                empty = false;
-            }
+        for (int j = 0; j < m; ++j) {
+            T[(size_t)r * w + j] = A[(size_t)r * m + j];
+            if (A[(size_t)r * m + j] != 0.0) empty = false;
         }
-        if (empty) A[r * w + r] = 1.0;
-        A[r * w + m + r] = 1.0;
+        if (empty) T[(size_t)r * w + r] = 1.0;
+        T[(size_t)r * w + m + r] = 1.0;
     }
-    __syncthreads();
-    __shared__ int piv;
     for (int k = 0; k < m; ++k) {
-        if (threadIdx.x == 0) {
-            int best = k;
-            for (int i = k + 1; i < m; ++i)
-                if (fabs(A[i * w + k]) > fabs(A[best * w + k])) best = i;
-            piv = best;
-        }
-        __syncthreads();
+        int piv = k;
+        for (int i = k + 1; i < m; ++i)
+            if (std::fabs(T[(size_t)i * w + k]) > std::fabs(T[(size_t)piv * w + k])) piv = i;
         if (piv != k)
-            for (int j = threadIdx.x; j < w; j += blockDim.x) {
-                double t = A[k * w + j]; A[k * w + j] = A[piv * w + j]; A[piv * w + j] = t;
-            }
-        __syncthreads();
-        double d = A[k * w + k];
-        double di = fabs(d) > 1e-300 ? 1.0 / d : 0.0;
-        __syncthreads();
-        for (int j = threadIdx.x; j < w; j += blockDim.x) A[k * w + j] *= di;
-        __syncthreads();
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            for (int j = 0; j < w; ++j) std::swap(T[(size_t)k * w + j], T[(size_t)piv * w + j]);
+        const double d = T[(size_t)k * w + k];
+        const double di = std::fabs(d) > 1e-300 ? 1.0 / d : 0.0;
+        double* rk = &T[(size_t)k * w];
+        for (int j = 0; j < w; ++j) rk[j] *= di;
+        for (int i = 0; i < m; ++i) {
             if (i == k) continue;
-            double f = A[i * w + k];
-            if (f != 0.0)
-                for (int j = 0; j < w; ++j) A[i * w + j] -= f * A[k * w + j];
+            double* ri = &T[(size_t)i * w];
+            const double f = ri[k];
+            if (f == 0.0) continue;
+            for (int j = k; j < w; ++j) ri[j] -= f * rk[j];
         }
-        __syncthreads();
     }
-    for (int i = threadIdx.x; i < m * m; i += blockDim.x)
-        inv[ioff[g] + i] = A[(i / m) * w + m + (i % m)];
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) inv[(size_t)i * m + j] = T[(size_t)i * w + m + j];
 }
 
 vip_status mg_build(vip_ctx* c, Multigrid& M) {
@@ -225,6 +204,9 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
     // lattice of each geometry
     std::vector<MgGeom> hg(G);
     int L = 1;
+    bool any_closed = false;
+    for (const Geom& gg : c->geoms) any_closed |= gg.bordered;
+    const int coarsest = any_closed ? MG_COARSEST_CLOSED : MG_COARSEST_OPEN;
     for (int g = 0; g < G; ++g) {
         const Geom& gg = c->geoms[g];
         double hmin = 1e300, x0 = 1e300, y0 = 1e300, x1 = -1e300, y1 = -1e300;
@@ -250,7 +232,7 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
             m.nx[l + 1] = nx;
             m.ny[l + 1] = ny;
             ++l;
-            if ((int64_t)nx * ny <= MG_COARSEST) break;
+            if ((int64_t)nx * ny <= coarsest) break;
         }
         L = std::max(L, l);
     }
@@ -393,26 +375,37 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
             VIP_CUDA(cudaGetLastError());
         }
     }
-    {   // exact solve on the coarsest level: dense inverses, one per geometry
+    {   // exact solve on the coarsest level: dense inverses, one per geometry (host)
         MgLevel& lc = M.lev[L];
         std::vector<int64_t> ioff(G);
         int64_t tot = 0;
-        int mmax = 1;
         for (int g = 0; g < G; ++g) {
-            int m = hg[g].nx[L] * hg[g].ny[L];
+            const int m = hg[g].nx[L] * hg[g].ny[L];
             ioff[g] = tot;
             tot += (int64_t)m * m;
-            mmax = std::max(mmax, m);
+        }
+        std::vector<double> hcoef((size_t)25 * lc.n);
+        std::vector<int32_t> hnbr((size_t)25 * lc.n);
+        VIP_CUDA(cudaMemcpyAsync(hcoef.data(), lc.coef, hcoef.size() * 8, cudaMemcpyDeviceToHost, st));
+        VIP_CUDA(cudaMemcpyAsync(hnbr.data(), lc.nbr, hnbr.size() * 4, cudaMemcpyDeviceToHost, st));
+        VIP_CUDA(cudaStreamSynchronize(st));
+        std::vector<double> hinv((size_t)tot);
+        for (int g = 0; g < G; ++g) {
+            const int m = hg[g].nx[L] * hg[g].ny[L];
+            const int64_t c0 = offs[L][g];  // cells numbered densely on the coarsest level
+            std::vector<double> Ad((size_t)m * m, 0.0);
+            for (int r = 0; r < m; ++r)
+                for (int o = 0; o < 25; ++o) {
+                    const int32_t j = hnbr[(size_t)o * lc.n + c0 + r];
+                    if (j >= 0) Ad[(size_t)r * m + (j - c0)] += hcoef[(size_t)o * lc.n + c0 + r];
+                }
+            coarse_inverse(Ad, m, hinv.data() + ioff[g]);
         }
         VIP_CUDA(dalloc(c, &M.cinv, tot));
         VIP_CUDA(dalloc(c, &M.cinv_off, G));
+        VIP_CUDA(cudaMemcpyAsync(M.cinv, hinv.data(), tot * 8, cudaMemcpyHostToDevice, st));
         VIP_CUDA(cudaMemcpyAsync(M.cinv_off, ioff.data(), G * 8, cudaMemcpyHostToDevice, st));
-        size_t smem = (size_t)mmax * 2 * mmax * sizeof(double);
-        VIP_CUDA(cudaFuncSetAttribute(k_mg_coarse_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)std::max<size_t>(smem, 1024)));
-        k_mg_coarse_inv<<<G, 256, smem, st>>>(lc.coef, lc.nbr, lc.n, lc.off, M.geom, L, M.cinv_off,
-                                               M.cinv);
-        VIP_CUDA(cudaGetLastError());
+        VIP_CUDA(cudaStreamSynchronize(st));
         M.ngeom = G;
     }
     VIP_CUDA(dalloc(c, &M.fdinv, R));

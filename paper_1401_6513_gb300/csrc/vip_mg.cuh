@@ -7,7 +7,12 @@
 namespace vip {
 
 constexpr int MG_MAXLEV = 16;
-constexpr int MG_COARSEST = 64;   // cells of the largest geometry on the coarsest level
+// Cells of the largest geometry on the coarsest level (solved exactly by its dense
+// inverse).  Open domains take a larger exact coarse solve (fewer iterations); a
+// closed domain's pinned constant mode makes large coarse operators nearly singular,
+// so contexts with a closed geometry keep it small.
+constexpr int MG_COARSEST_OPEN = 576;
+constexpr int MG_COARSEST_CLOSED = 64;
 
 struct MgGeom {                   // background lattice of one geometry
     double h, x0, y0;
@@ -57,7 +62,7 @@ struct Multigrid {
     double* fdinv = nullptr;      // [R] l1-Jacobi scaling of the fine operator
     void* fr = nullptr;           // [R] fine residual scratch
     void* fx = nullptr;           // [R] fine smoothing scratch
-    double* cinv = nullptr;       // dense inverse of each geometry's coarsest operator
+    double* cinv = nullptr;       // dense inverse of each geometry's coarsest operator (row-major)
     int64_t* cinv_off = nullptr;  // [G] offset of geometry g's block in cinv
     int ngeom = 0;
     float omega = 1.0f;           // smoother damping (vip_set_multigrid / vip_autotune)
