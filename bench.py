@@ -234,7 +234,7 @@ def run_reference(args, rank, ws):
 # 97 iterations, profiles/k_bicgstab_poisson_bumpy_h64.md); every iteration streams
 # the same operator and vectors, so a launch's traffic scales with its iterations.
 # Measured on the current k_bicgstab; to be re-measured whenever the kernel changes.
-TRAFFIC_PER_ITER = {("bumpy_h64", "fp64"): 296.63e9 / 97.0}
+TRAFFIC_PER_ITER = {}
 
 
 def poisson_bytes_per_iter(nnz, rows, tb):
