@@ -231,10 +231,10 @@ def run_reference(args, rank, ws):
 
 # DRAM bytes per inner iteration of the Poisson launch, from one ncu capture of the
 # same workload and kernel (dram__bytes_read.sum + dram__bytes_write.sum of a launch of
-# 97 iterations, profiles/k_bicgstab_poisson_bumpy_h64.md); every iteration streams
+# 72 iterations, profiles/k_bicgstab_poisson_bumpy_h64.md); every iteration streams
 # the same operator and vectors, so a launch's traffic scales with its iterations.
 # Measured on the current k_bicgstab; to be re-measured whenever the kernel changes.
-TRAFFIC_PER_ITER = {}
+TRAFFIC_PER_ITER = {("bumpy_h64", "fp64"): 221.29e9 / 72.0}
 
 
 def poisson_bytes_per_iter(nnz, rows, tb):
