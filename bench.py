@@ -2,8 +2,8 @@
 """Benchmark of the VIP fractional-step solver on one or more GPUs.
 
 Metric: fractional-step node-updates/s with every Poisson solve converged to a
-1e-8 relative residual (nodes x steps / seconds), plus the HBM roofline of the
-dominant kernel (the Poisson BiCGSTAB launch).
+1e-8 relative residual (nodes x steps / seconds), plus the HBM and FP64 rooflines
+of the dominant kernel (the Poisson BiCGSTAB launch).
 
 Workload (default): flow past the bumpy cylinder r = 1 + 0.05 sin 12t + 0.02 sin 31t
 in the channel [-8,24]x[-8,8] at h = 1/64 (about 2.1M nodes), Re = 200, dt = h/10,
@@ -230,25 +230,43 @@ def run_reference(args, rank, ws):
 
 
 # DRAM bytes per inner iteration of the Poisson launch, from one ncu capture of the
-# same workload and kernel (dram__bytes_read.sum + dram__bytes_write.sum of a launch of
-# 72 iterations, profiles/k_bicgstab_poisson_bumpy_h64.md); every iteration streams
-# the same operator and vectors, so a launch's traffic scales with its iterations.
-# Measured on the current k_bicgstab; to be re-measured whenever the kernel changes.
-TRAFFIC_PER_ITER = {("bumpy_h64", "fp64"): 221.29e9 / 72.0}
+# same workload and kernel (dram__bytes_read.sum + dram__bytes_write.sum of one launch
+# divided by its iterations); every iteration streams the same operator and vectors,
+# so a launch's traffic scales with its iterations (profiles/k_bicgstab_poisson_bumpy_h64.md).
+# Re-measured whenever the kernel changes.
+TRAFFIC_PER_ITER = {("bumpy_h64", "fp64"): 60.470488064e9 / 72.0}
+
+# FP64 operations per clock per SM of GB300 (two FP64 FMAs), for the ALU roofline;
+# 152 SMs at 2070 MHz give 1.26 TFLOP/s, the part's nominal FP64 rate.
+FP64_FLOPS_PER_CLK_SM = 4
 
 
-def poisson_bytes_per_iter(nnz, rows, tb):
+def poisson_bytes_per_iter(streamed, rows, tb):
     """Algorithmic DRAM bytes of one inner iteration of the multigrid-preconditioned
     BiCGSTAB (vectors of tb bytes, int32 columns):
-      * six passes over the operator entries (value + column): two Krylov SpMVs and
-        the two fine-level residuals of each of the two V-cycles;
+      * six passes over the operator as stored (value + column per streamed entry:
+        the stored entries of ordinary slices plus one stencil per slice whose 32
+        rows share it; vip_operator_layout): two Krylov SpMVs and the two fine-level
+        residuals of each of the two V-cycles;
       * 48 row-sized vector accesses: p update 6, each V-cycle's fine level 11.5
         (residual 3, restriction 1.5, prolongation 3, smoothing 4), v 3, s 5, t 3,
         x/r update 8;
-      * the coarse levels, 442 B per level-1 cell per V-cycle (25 FP64 coefficients,
-        inverse diagonal and vectors, down and up), a quarter of a cell per row and
-        4/3 of it over all levels: 147 B per row per V-cycle."""
-    return 6 * nnz * (tb + 4) + 48 * tb * rows + 2 * 147 * rows
+      * the coarse levels, 188 B per level-1 cell per V-cycle (down: b and the
+        inverse diagonal, the 9 coefficients of the 3 x 3 stencil core, a quarter
+        of b_{l+1}; up: the same plus the parent's correction and y), a quarter of a
+        cell per row and 4/3 of it over all levels: 63 B per row per V-cycle."""
+    return 6 * streamed * (tb + 4) + 48 * tb * rows + 2 * 63 * rows
+
+
+def poisson_flops_per_iter(nnz, rows):
+    """Algorithmic FP64 operations of one inner iteration (an FMA counts 2): six
+    operator applications (2 nnz each); per row 46 in the Krylov and fine-level
+    vector updates and dot products (p 6, two V-cycles' fine level 8 each, v 4, s 4,
+    t 6, x/r 10) and 32 on the coarse levels (48 per level-1 cell per V-cycle: 3 x 3
+    stencils down and up, smoothing, restriction, correction; a quarter of a cell
+    per row, 4/3 over all levels).  The dense coarsest solve (under 0.5 % of the
+    total on the benchmarked workloads) is not counted."""
+    return 12 * nnz + 78 * rows
 
 
 def poisson_bytes_per_pass(nnz, rows, tb):
@@ -347,10 +365,14 @@ def main():
     nnz_p = int(ptr[-1])
     rows_p = int(ptr.size - 1)
     tb = 4 if prec == vip.VIP_PREC_MIXED else 8
+    lay = ctx.vip_operator_layout("POISSON")
+    # entries one operator pass streams, per real entry (exact for one geometry; a
+    # batch's geometries are assigned the table's ratio)
+    stream_ratio = (lay["other_entries"] + lay["uniform_entries"]) / max(nnz_p, 1)
     # per geometry: a converged system stops iterating inside the shared launch, so the
     # algorithmic bytes are summed over geometries with their own iteration counts
     g_iters = ctx.vip_get_geometry_iters() - g0_iters
-    bytes_p, off, kb = 0, 0, 0
+    bytes_p, flops_p, off, kb = 0, 0, 0, 0
     for gi, g in enumerate(nss):
         nnz_g = int(ptr[off + g.n] - ptr[off])
         rows_g = g.n
@@ -358,15 +380,36 @@ def main():
             nnz_g += int(ptr[N + kb + 1] - ptr[N + kb])
             rows_g += 1
             kb += 1
-        bytes_p += int(g_iters[gi]) * poisson_bytes_per_iter(nnz_g, rows_g, tb)
+        bytes_p += int(g_iters[gi]) * poisson_bytes_per_iter(nnz_g * stream_ratio, rows_g, tb)
+        flops_p += int(g_iters[gi]) * poisson_flops_per_iter(nnz_g, rows_g)
         off += g.n
     bytes_p += out_p * poisson_bytes_per_pass(nnz_p, rows_p, tb)
+    flops_p += out_p * (2 * nnz_p + 8 * rows_p)  # refinement: residual, 3 dots, x update
     t_pois = prof["poisson"] / 1e3
     tpi = TRAFFIC_PER_ITER.get((args.workload, args.precision))
     traffic = tpi * it_p / max(args.steps, 1) if tpi else None  # per launch (one per step)
     pk, pk_src = peaks()
     hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
     achieved = bytes_p / t_pois / 1e9 if t_pois > 0 else 0.0
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    fp64_peak = FP64_FLOPS_PER_CLK_SM * torch.cuda.get_device_properties(0).multi_processor_count \
+        * sm_mhz * 1e6 / 1e12
+    fp64_achieved = flops_p / t_pois / 1e12 if t_pois > 0 else 0.0
+    roof_hbm = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": f"hbm_gbs {pk_src}",
+                "bytes_per_step": bytes_p / max(args.steps, 1)}
+    roof_alu = {"bound": "alu", "achieved": fp64_achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": fp64_achieved / fp64_peak,
+                "peak_source": f"FP64: {FP64_FLOPS_PER_CLK_SM} flops/clk/SM x SMs x sm_max_mhz "
+                               f"{sm_mhz:.0f} ({pk_src})",
+                "flops_per_step": flops_p / max(args.steps, 1)}
+    # the binding roof is the one the kernel is closest to; the other is reported beside it
+    if prec == vip.VIP_PREC_FP64 and roof_alu["frac"] > roof_hbm["frac"]:
+        roof, roof_other = roof_alu, roof_hbm
+    else:
+        roof, roof_other = roof_hbm, roof_alu
+    roof = dict(roof, traffic=traffic, kernel="k_bicgstab (Poisson)",
+                operator_layout=lay)
     # ---- end to end through the C ABI with pinned host buffers: every step loads the
     # state from host memory, steps, and reads the new state back into host memory,
     # from which the next step starts (the integration continues; same work per step)
@@ -410,11 +453,8 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32-inner/f64" if args.precision == "mixed" else "f64",
             "data": "synthetic", "config": cfg,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "k_bicgstab (Poisson)",
-                         "peak_source": f"hbm_gbs {pk_src}",
-                         "bytes_per_step": bytes_p / max(args.steps, 1)},
+            "roofline": roof,
+            "roofline_other": roof_other,
             "e2e": {"value": N * k2 * ws / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 4 * 8 * N},
             # per step: rhs, Helmholtz, divergence, Poisson, stats, projection; several

@@ -687,6 +687,21 @@ vip_status vip_stencil_info(vip_ctx* c, int which, int64_t* nrows, int64_t* nnz)
     return VIP_OK;
 }
 
+vip_status vip_operator_layout(vip_ctx* c, int which, int64_t* slices, int64_t* uniform_slices,
+                               int64_t* uniform_entries, int64_t* other_entries) {
+    if (!c) return VIP_ERR_ARG;
+    if (!c->built) return fail(c, VIP_ERR_ARG, "vip_operator_layout before vip_build");
+    const Sell* S = nullptr;
+    if (which == VIP_OP_HELM_U || which == VIP_OP_HELM_V) S = &c->T.helm;
+    else if (which == VIP_OP_POISSON) S = &c->T.pois;
+    else return fail(c, VIP_ERR_ARG, "vip_operator_layout: not a Krylov operator");
+    if (slices) *slices = S->nslices;
+    if (uniform_slices) *uniform_slices = S->nuniform;
+    if (uniform_entries) *uniform_entries = S->nuentries;
+    if (other_entries) *other_entries = S->nstored_other;
+    return VIP_OK;
+}
+
 vip_status vip_get_stencil(vip_ctx* c, int which, int64_t* row_ptr, int32_t* col, double* val) {
     if (!c) return VIP_ERR_ARG;
     if (!c->built) return fail(c, VIP_ERR_ARG, "vip_get_stencil before vip_build");

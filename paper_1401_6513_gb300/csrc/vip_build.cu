@@ -601,6 +601,90 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
     if (i < n) b[i] = (float)a[i];
 }
 
+// Uniform slices of a SELL table (see Sell): one warp per slice decides whether all
+// 32 rows hold the same stencil and writes its entry count (0 if not).
+__global__ void k_sell_uniform(Sell A, int64_t* __restrict__ usize) {
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= A.nslices) return;  // whole warps
+    const int w = A.width[s];
+    const int64_t row = s * SLICE + lane;
+    const int64_t base = A.sptr[s] + lane;
+    const int64_t lim = (int64_t)1 << 29;  // column codes fit in int32
+    bool ok = (s + 1) * SLICE <= A.nrows && w > 0;
+    for (int k = 0; ok && k < w; ++k) {
+        const int64_t e = base + (int64_t)k * SLICE;
+        const long long v = __double_as_longlong(A.v64[e]);
+        const int64_t col = A.col[e];
+        const long long v0 = __shfl_sync(0xffffffffu, v, 0);
+        const int64_t c0 = __shfl_sync(0xffffffffu, col, 0);
+        const int64_t d = col - row, d0 = c0 - s * SLICE;
+        const bool rel = __all_sync(0xffffffffu, d == d0 && d > -lim && d < lim);
+        const bool ab = __all_sync(0xffffffffu, col == c0 && c0 < lim);
+        ok = __all_sync(0xffffffffu, v == v0) && (rel || ab);
+    }
+    if (lane == 0) usize[s] = ok ? w : 0;
+}
+
+// Stencil of each uniform slice, taken from its first row.  Entry k's column is
+// relative when rows 0 and 1 of the slice differ by one there, absolute when equal
+// (exactly one holds in a uniform slice).
+__global__ void k_sell_compact(Sell A, const int64_t* __restrict__ usize,
+                               const int64_t* __restrict__ uoff) {
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= A.nslices) return;
+    if (usize[s] == 0) {
+        if (lane == 0) A.ucptr[s] = -1;
+        return;
+    }
+    const int64_t o = uoff[s];
+    const int w = A.width[s];
+    for (int k = lane; k < w; k += 32) {
+        const int64_t e = A.sptr[s] + (int64_t)k * SLICE;
+        const int64_t c0 = A.col[e], c1 = A.col[e + 1];
+        A.ucode[o + k] = c1 == c0 ? (int32_t)(2 * c0 + 1) : (int32_t)(2 * (c0 - s * SLICE));
+        A.uv64[o + k] = A.v64[e];
+        if (A.uv32) A.uv32[o + k] = A.v32[e];
+    }
+    if (lane == 0) A.ucptr[s] = o;
+}
+
+static vip_status sell_uniform(vip_ctx* c, Sell& S) {
+    cudaStream_t st = c->stream;
+    int64_t* usize = nullptr;
+    int64_t* uoff = nullptr;
+    VIP_CUDA(cudaMalloc(&usize, S.nslices * sizeof(int64_t)));
+    VIP_CUDA(cudaMalloc(&uoff, (S.nslices + 1) * sizeof(int64_t)));
+    const int TB = 256;
+    const unsigned grid = (unsigned)((S.nslices * 32 + TB - 1) / TB);
+    k_sell_uniform<<<grid, TB, 0, st>>>(S, usize);
+    VIP_CUDA(cudaGetLastError());
+    VIP_CUDA(scan_excl<int64_t>(usize, uoff, S.nslices, st));
+    VIP_CUDA(cudaMemcpyAsync(&S.nuentries, uoff + S.nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    std::vector<int64_t> hs(S.nslices), hp(S.nslices + 1);
+    std::vector<int32_t> hw(S.nslices);
+    VIP_CUDA(cudaMemcpyAsync(hs.data(), usize, S.nslices * 8, cudaMemcpyDeviceToHost, st));
+    VIP_CUDA(cudaMemcpyAsync(hw.data(), S.width, S.nslices * 4, cudaMemcpyDeviceToHost, st));
+    VIP_CUDA(cudaStreamSynchronize(st));
+    S.nuniform = 0;
+    S.nstored_other = 0;
+    for (int64_t k = 0; k < S.nslices; ++k) {
+        if (hs[k]) ++S.nuniform;
+        else S.nstored_other += (int64_t)hw[k] * SLICE;
+    }
+    VIP_CUDA(dalloc(c, &S.ucptr, S.nslices));
+    VIP_CUDA(dalloc(c, &S.ucode, S.nuentries));
+    VIP_CUDA(dalloc(c, &S.uv64, S.nuentries));
+    if (S.v32) VIP_CUDA(dalloc(c, &S.uv32, S.nuentries));
+    k_sell_compact<<<grid, TB, 0, st>>>(S, usize, uoff);
+    VIP_CUDA(cudaGetLastError());
+    VIP_CUDA(cudaStreamSynchronize(st));
+    cudaFree(usize);
+    cudaFree(uoff);
+    return VIP_OK;
+}
+
 static vip_status build_table(vip_ctx* c, const AsmArgs& A, int tb, int64_t nrows, Sell& S,
                               bool f32) {
     cudaStream_t st = c->stream;
@@ -631,10 +715,11 @@ static vip_status build_table(vip_ctx* c, const AsmArgs& A, int tb, int64_t nrow
     k_table_fill<<<(unsigned)((nrows + TB - 1) / TB), TB, 0, st>>>(A, tb, nrows, S.sptr, S.width,
                                                                    S.col, S.v64);
     VIP_CUDA(cudaGetLastError());
-    if (f32) {
+    if (f32) {  // the Krylov operators: FP32 copy and uniform slices
         VIP_CUDA(dalloc(c, &S.v32, S.nstored));
         k_to_f32<<<(unsigned)((S.nstored + TB - 1) / TB), TB, 0, st>>>(S.v64, S.v32, S.nstored);
         VIP_CUDA(cudaGetLastError());
+        return sell_uniform(c, S);
     }
     return VIP_OK;
 }

@@ -39,6 +39,19 @@ struct Sell {
     int32_t* col = nullptr;       // [nstored]
     double* v64 = nullptr;        // [nstored]
     float* v32 = nullptr;         // [nstored] (only for Krylov operators)
+    // Uniform slices (Krylov operators only): a slice whose 32 rows hold the same
+    // stencil (entry k has the same value, bit for bit, in every row, and a column
+    // that is the row plus the same offset in every row or the same column in every
+    // row) is also stored once, as `width` entries at ucptr[s]: value uv64/uv32 and
+    // column code ucode (2 d: column = row + d; 2 c + 1: column c).  ucptr[s] = -1
+    // for the other slices.  Results are the same either way.
+    int64_t* ucptr = nullptr;     // [nslices]
+    int32_t* ucode = nullptr;     // [nuentries]
+    double* uv64 = nullptr;
+    float* uv32 = nullptr;
+    int64_t nuniform = 0;         // uniform slices
+    int64_t nuentries = 0;        // their stencil entries
+    int64_t nstored_other = 0;    // stored entries of the other slices
 };
 
 struct Geom {

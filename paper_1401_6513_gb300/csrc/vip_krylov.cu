@@ -19,6 +19,7 @@
 // meet at a grid barrier whose wait is bounded (2 s, then VIP_ERR_TIMEOUT).
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "vip_internal.cuh"
@@ -88,6 +89,10 @@ struct KArgs {
     const int32_t* col;
     const double* a64;
     const T* aT;
+    const int64_t* ucptr;   // uniform slices (null: none)
+    const int32_t* ucode;
+    const double* u64;
+    const T* uT;
     const int32_t* slice_sys;
     const int32_t* blk_s0;
     const int32_t* blk_s1;
@@ -151,16 +156,46 @@ __device__ __forceinline__ double wsum(double v) {
 
 // sum_k A[row, k] f(col[row, k]) over the SELL entries of one row (lane of the
 // slice's warp), in entry order.  The column indices and values of U entries are
-// loaded before their U gathers, so each warp keeps several loads in flight.
+// loaded before their U gathers, so each warp keeps several loads in flight.  A
+// uniform slice (ucptr[sl] >= 0, warp-uniform) reads its single stored stencil
+// instead (the same values and columns, so the same sum): one broadcast load per
+// entry for the whole warp in place of 32 value and 32 column loads.
 template <int U, class TA, class F>
 __device__ __forceinline__ double sell_row(const int64_t* __restrict__ sptr,
                                            const int32_t* __restrict__ width,
                                            const int32_t* __restrict__ col, const TA* __restrict__ A,
-                                           int64_t sl, int lane, F&& f) {
-    const int64_t base = __ldg(sptr + sl) + lane;
+                                           const int64_t* __restrict__ ucptr,
+                                           const int32_t* __restrict__ ucode,
+                                           const TA* __restrict__ uA, int64_t sl, int lane, F&& f) {
     const int w = __ldg(width + sl);
     double sum = 0.0;
     int k = 0;
+    const int64_t up = ucptr ? __ldg(ucptr + sl) : -1;
+    if (up >= 0) {
+        const int32_t row = (int32_t)(sl * SLICE + lane);
+        const int32_t* uc = ucode + up;
+        const TA* ua = uA + up;
+        for (; k + U <= w; k += U) {
+            int c[U];
+            double av[U], xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t code = __ldg(uc + k + u);
+                c[u] = (code & 1) ? (code >> 1) : row + (code >> 1);
+                av[u] = (double)__ldg(ua + k + u);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = f(c[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) sum += av[u] * xv[u];
+        }
+        for (; k < w; ++k) {
+            const int32_t code = __ldg(uc + k);
+            sum += (double)__ldg(ua + k) * f((code & 1) ? (code >> 1) : row + (code >> 1));
+        }
+        return sum;
+    }
+    const int64_t base = __ldg(sptr + sl) + lane;
     for (; k + U <= w; k += U) {
         int c[U];
         double av[U], xv[U];
@@ -269,7 +304,11 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
     };
     // y_row = sum_k A[row,k] * vec[col] for the warp's slice (lane = row)
     auto spmv_row = [&](int64_t sl, const auto* A, const auto* vec) -> double {
-        return sell_row<4>(a.sptr, a.width, a.col, A, sl, lane,
+        using TA = std::remove_cv_t<std::remove_pointer_t<decltype(A)>>;
+        const TA* uA;
+        if constexpr (std::is_same_v<TA, double>) uA = a.u64;
+        else uA = a.uT;
+        return sell_row<4>(a.sptr, a.width, a.col, A, a.ucptr, a.ucode, uA, sl, lane,
                            [&](int j) { return (double)ldv(vec + j); });
     };
 
@@ -286,25 +325,29 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
     //   level l, up:  y_l = x_l + w D_l^{-1} (b_l - A_l x_l),
     //                 x_l = w D_l^{-1} b_l + corr s_{l+1}(parent),  s = x_L or y_{l+1}
     //   fine, up:     f += corr s_1(agg),  z = f + w Df^{-1} (v - A f)
-    // A coarse level is processed in 32 x 32 tiles of its cell lattice, one CTA per
-    // tile: the smoothing iterate x_l of the tile and a two-cell halo is formed once
-    // in shared memory, then each thread applies its cell's 25-point stencil (warp =
-    // lattice row, coefficients read as one contiguous slice per warp).  Going down,
-    // the tile's residuals are summed over 2 x 2 children straight into b_{l+1}.
+    // A coarse level is processed in 32 x th tiles of its cell lattice (th = 32 on
+    // large levels, down to 2 on small ones so that every SM gets a share of the
+    // FP64 stencil work), one CTA per tile: the smoothing iterate x_l of the tile and
+    // a two-cell halo is formed once in shared memory, then each thread of the first
+    // th warps applies its cell's 5 x 5 stencil (warp = lattice row, coefficients read
+    // as one contiguous slice per warp; 3 x 3 where the slice's outer ring is zero).
+    // Going down, the tile's residuals are summed over 2 x 2 children straight into
+    // b_{l+1}.
     // Only rows of systems still in their inner pass are touched on the fine level.
     const int64_t gtid = (int64_t)blockIdx.x * KTHREADS + threadIdx.x;
     const int64_t gstride = (int64_t)nb * KTHREADS;
     const double mw = (double)a.mg.omega;
     const double mcorr = (double)a.mg.corr;
-    // s_tile[r][c] = f(cell, x, y) for the tile at (x0, y0) and its halo (0 outside a
-    // non-periodic lattice; periodic directions wrap)
-    auto stage = [&](const MgLevGeom& q, int x0, int y0, auto&& f) {
+    // s_tile[r][c] = f(cell, x, y) for the 32 x th tile at (x0, y0) and its halo (0
+    // outside a non-periodic lattice; periodic directions wrap)
+    auto stage = [&](const MgLevGeom& q, int x0, int y0, int th, auto&& f) {
         double v[2];
+        const int nst = 36 * (th + 4);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = threadIdx.x + h * KTHREADS;
             v[h] = 0.0;
-            if (k < 36 * 36) {
+            if (k < nst) {
                 int xx = x0 - 2 + k % 36, yy = y0 - 2 + k / 36;
                 bool ok = true;
                 if (q.px) { xx %= q.nx; if (xx < 0) xx += q.nx; } else ok = xx >= 0 && xx < q.nx;
@@ -315,15 +358,25 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = threadIdx.x + h * KTHREADS;
-            if (k < 36 * 36) s_tile[k / 36][k % 36] = v[h];
+            if (k < nst) s_tile[k / 36][k % 36] = v[h];
         }
     };
-    // sum_o A_l[c, o] s_tile[warp + dy][lane + dx] for the thread's cell c
-    auto stencil = [&](int l, int64_t c) -> double {
+    // sum_o A_l[c, o] s_tile[warp + dy][lane + dx] for the thread's cell c, in offset
+    // order; a warp whose slices hold no nonzero outside the 3 x 3 core (wide false,
+    // warp-uniform) skips the zero products, which leaves the sum unchanged
+    auto stencil = [&](int l, int64_t c, bool wide) -> double {
         const double* cp = a.mg.coefs[l] + (c >> 5) * 800 + (c & 31);
         double acc = 0.0;
+        if (wide) {
 #pragma unroll
-        for (int o = 0; o < 25; ++o) acc += ldm(cp + o * 32) * s_tile[warp + o / 5][lane + o % 5];
+            for (int o = 0; o < 25; ++o) acc += ldm(cp + o * 32) * s_tile[warp + o / 5][lane + o % 5];
+        } else {
+#pragma unroll
+            for (int dy = 1; dy <= 3; ++dy)
+#pragma unroll
+                for (int dx = 1; dx <= 3; ++dx)
+                    acc += ldm(cp + (dy * 5 + dx) * 32) * s_tile[warp + dy][lane + dx];
+        }
         return acc;
     };
     // z = M^{-1} v, given v and f = w Df^{-1} v on the rows of active systems
@@ -348,25 +401,26 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
         for (int l = 1; l < L; ++l) {
             const T* bl = M.b[l];
             const double* dl = M.dinv[l];
+            const int th = M.th[l];
             for (int64_t t = blockIdx.x; t < M.ntiles[l]; t += nb) {
                 const MgTile tile = M.tiles[l][t];
                 if (!S[tile.g].inner_active) continue;  // that geometry's solve is done
                 const MgLevGeom q = M.lg[l][tile.g];
                 __syncthreads();  // the previous tile's reads of s_tile are done
-                stage(q, tile.x0, tile.y0, [&](int64_t j, int, int) {
+                stage(q, tile.x0, tile.y0, th, [&](int64_t j, int, int) {
                     return mw * __ldg(dl + j) * (double)ldv(bl + j);
                 });
                 __syncthreads();
                 const int x = tile.x0 + lane, y = tile.y0 + warp;
+                const bool in = warp < th && x < q.nx && y < q.ny;
+                const int64_t c = q.off + (int64_t)y * q.sx + x;
+                const bool wide = __any_sync(0xffffffffu, in && __ldg(M.ring[l] + (c >> 5)));
                 double r = 0.0;
-                if (x < q.nx && y < q.ny) {
-                    const int64_t c = q.off + (int64_t)y * q.sx + x;
-                    r = (double)ldv(bl + c) - stencil(l, c);
-                }
+                if (in) r = (double)ldv(bl + c) - stencil(l, c, wide);
                 __syncthreads();
-                (&s_tile[0][0])[warp * 32 + lane] = r;
+                if (warp < th) (&s_tile[0][0])[warp * 32 + lane] = r;
                 __syncthreads();
-                if (threadIdx.x < 256) {  // 16 x 16 cells of level l+1
+                if (threadIdx.x < th * 8) {  // 16 x th/2 cells of level l+1
                     const int px = threadIdx.x & 15, py = threadIdx.x >> 4;
                     const MgLevGeom qp = M.lg[l + 1][tile.g];
                     const int X = (tile.x0 >> 1) + px, Y = (tile.y0 >> 1) + py;
@@ -407,21 +461,24 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
             const T* sol = (l + 1 == L) ? M.x[L] : M.y[l + 1];
             const T* bl = M.b[l];
             const double* dl = M.dinv[l];
+            const int th = M.th[l];
             for (int64_t t = blockIdx.x; t < M.ntiles[l]; t += nb) {
                 const MgTile tile = M.tiles[l][t];
                 if (!S[tile.g].inner_active) continue;
                 const MgLevGeom q = M.lg[l][tile.g];
                 const MgLevGeom qp = M.lg[l + 1][tile.g];
                 __syncthreads();
-                stage(q, tile.x0, tile.y0, [&](int64_t j, int xx, int yy) {
+                stage(q, tile.x0, tile.y0, th, [&](int64_t j, int xx, int yy) {
                     return mw * __ldg(dl + j) * (double)ldv(bl + j) +
                            mcorr * (double)ldv(sol + qp.off + (int64_t)(yy >> 1) * qp.sx + (xx >> 1));
                 });
                 __syncthreads();
                 const int x = tile.x0 + lane, y = tile.y0 + warp;
-                if (x < q.nx && y < q.ny) {
-                    const int64_t c = q.off + (int64_t)y * q.sx + x;
-                    const double r = (double)ldv(bl + c) - stencil(l, c);
+                const bool in = warp < th && x < q.nx && y < q.ny;
+                const int64_t c = q.off + (int64_t)y * q.sx + x;
+                const bool wide = __any_sync(0xffffffffu, in && __ldg(M.ring[l] + (c >> 5)));
+                if (in) {
+                    const double r = (double)ldv(bl + c) - stencil(l, c, wide);
                     M.y[l][c] = (T)(s_tile[warp + 2][lane + 2] + mw * __ldg(dl + c) * r);
                 }
             }
@@ -861,6 +918,8 @@ static MgDev<T> mg_view(const Multigrid& M) {
         d.lg[l] = v.lg;
         d.tiles[l] = v.tiles;
         d.coefs[l] = v.coefs;
+        d.ring[l] = v.ring;
+        d.th[l] = v.th;
         d.dinv[l] = v.dinv;
         d.x[l] = (T*)v.x; d.b[l] = (T*)v.b; d.y[l] = (T*)v.y;
     }
@@ -879,6 +938,8 @@ static vip_status launch(vip_ctx* c, const KrylovPlan& P, const Sell& A, const d
     KArgs<T> a;
     a.sptr = A.sptr; a.width = A.width; a.col = A.col; a.a64 = A.v64;
     a.aT = sizeof(T) == 8 ? (const T*)A.v64 : (const T*)A.v32;
+    a.ucptr = A.ucptr; a.ucode = A.ucode; a.u64 = A.uv64;
+    a.uT = sizeof(T) == 8 ? (const T*)A.uv64 : (const T*)A.uv32;
     a.slice_sys = P.slice_sys; a.blk_s0 = P.blk_s0; a.blk_s1 = P.blk_s1; a.blk_g0 = P.blk_g0;
     a.blk_ng = P.blk_ng;
     a.sys_b0 = P.sys_b0; a.sys_b1 = P.sys_b1; a.partial = P.partial; a.bar = P.bar;

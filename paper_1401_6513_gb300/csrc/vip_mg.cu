@@ -130,19 +130,30 @@ __global__ void k_mg_galerkin(int64_t nc, const int64_t* __restrict__ child,  //
     for (int o = 0; o < 25; ++o) ccoef[(int64_t)o * nc + C] = acc[o];
 }
 
-// sliced copy of the stencils ([n/32][25][32]) and the l1-Jacobi scaling
-// sign(a_cc) / sum_o |a_co| of the smoother (0 for empty and padding cells)
+// sliced copy of the stencils ([n/32][25][32]), the l1-Jacobi scaling
+// sign(a_cc) / sum_o |a_co| of the smoother (0 for empty and padding cells), and per
+// slice of 32 cells whether any stencil has a nonzero outside the central 3 x 3
+// offsets.  Away from boundaries a 2 x 2 aggregate of the 13-point fine stencil, and
+// of a 3 x 3 coarse stencil, couples only to the adjacent cells, so most slices
+// need 9 of the 25 products.  n is a multiple of 32 and blockDim a multiple of 32,
+// so each warp is one slice.
 __global__ void k_mg_finish(int64_t n, const double* __restrict__ coef, double* __restrict__ coefs,
-                            double* __restrict__ dinv) {
+                            double* __restrict__ dinv, uint8_t* __restrict__ ring) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     double s = 0.0;
+    bool outer = false;
     for (int o = 0; o < 25; ++o) {
-        coefs[(c >> 5) * 800 + o * 32 + (c & 31)] = coef[(int64_t)o * n + c];
-        s += fabs(coef[(int64_t)o * n + c]);
+        const double a = coef[(int64_t)o * n + c];
+        coefs[(c >> 5) * 800 + o * 32 + (c & 31)] = a;
+        s += fabs(a);
+        const int dy = o / 5 - 2, dx = o % 5 - 2;
+        if ((dx < -1 || dx > 1 || dy < -1 || dy > 1) && a != 0.0) outer = true;
     }
     double d = coef[(int64_t)12 * n + c];
     dinv[c] = (s != 0.0) ? (d < 0.0 ? -1.0 : 1.0) / s : 0.0;
+    const unsigned any = __ballot_sync(0xffffffffu, outer);
+    if ((threadIdx.x & 31) == 0) ring[c >> 5] = any ? 1 : 0;
 }
 
 // fine-level l1-Jacobi scaling sign(a_rr) / sum_k |a_rk|
@@ -284,13 +295,28 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         VIP_CUDA(dalloc(c, &lv.coef, 25 * n));
         VIP_CUDA(dalloc(c, &lv.coefs, 25 * n));
         VIP_CUDA(dalloc(c, &lv.dinv, n));
+        VIP_CUDA(dalloc(c, &lv.ring, n / 32));
         {
+            // Tile height: a level with few 32 x 32 tiles would keep most SMs idle
+            // while a few apply 1024 stencils each on the FP64 pipe, so small levels
+            // take shorter tiles.  Cost model per CTA: rounds of tiles x (stencil and
+            // staging FP64 work + a fixed latency per tile).
+            const int64_t nblk = std::max(1, c->num_sms);
+            double best_cost = 1e300;
+            for (int h : {32, 16, 8, 4, 2}) {
+                int64_t nt = 0;
+                for (int g = 0; g < G; ++g)
+                    nt += (int64_t)((hg[g].nx[l] + 31) / 32) * ((hg[g].ny[l] + h - 1) / h);
+                const double cost = (double)((nt + nblk - 1) / nblk) *
+                                    (h * 32 * 12.0 + (h + 4) * 36 * 3.0 + 4000.0);
+                if (cost < best_cost) { best_cost = cost; lv.th = h; }
+            }
             std::vector<MgLevGeom> lgh(G);
             std::vector<MgTile> th;
             for (int g = 0; g < G; ++g) {
                 lgh[g] = {offs[l][g], hg[g].nx[l], hg[g].ny[l], hg[g].sx[l], hg[g].periodic_x,
                           hg[g].periodic_y, 0};
-                for (int y0 = 0; y0 < hg[g].ny[l]; y0 += 32)
+                for (int y0 = 0; y0 < hg[g].ny[l]; y0 += lv.th)
                     for (int x0 = 0; x0 < hg[g].nx[l]; x0 += 32) th.push_back({g, x0, y0, 0});
             }
             VIP_CUDA(dalloc(c, &lv.lg, G));
@@ -371,7 +397,8 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         }
         for (int l = 1; l <= L; ++l) {
             MgLevel& lv = M.lev[l];
-            k_mg_finish<<<(unsigned)((lv.n + TB - 1) / TB), TB, 0, st>>>(lv.n, lv.coef, lv.coefs, lv.dinv);
+            k_mg_finish<<<(unsigned)((lv.n + TB - 1) / TB), TB, 0, st>>>(lv.n, lv.coef, lv.coefs, lv.dinv,
+                                                                          lv.ring);
             VIP_CUDA(cudaGetLastError());
         }
     }

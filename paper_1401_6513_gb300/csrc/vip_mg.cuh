@@ -30,7 +30,8 @@ struct MgLevGeom {
     int32_t nx, ny, sx, px, py, pad;
 };
 
-// 32 x 32 block of one geometry's cells, processed by one CTA.
+// Block of 32 x th cells of one geometry (th = the level's tile height), processed
+// by one CTA.
 struct MgTile {
     int32_t g, x0, y0, pad;
 };
@@ -45,9 +46,11 @@ struct MgLevel {                  // coarse level (all geometries concatenated)
     double* coef = nullptr;       // [25][n] Galerkin stencil (setup layout)
     double* coefs = nullptr;      // the same, sliced: [n/32][25][32] (V-cycle layout)
     double* dinv = nullptr;       // [n] l1-Jacobi scaling (0 for empty and padding cells)
+    uint8_t* ring = nullptr;      // [n/32] 1 if a cell of the slice has a nonzero outside its 3 x 3 core
     MgLevGeom* lg = nullptr;      // [G] lattice of each geometry on this level
-    MgTile* tiles = nullptr;      // 32 x 32 tiles covering every geometry's lattice
+    MgTile* tiles = nullptr;      // 32 x th tiles covering every geometry's lattice
     int64_t ntiles = 0;
+    int th = 32;                  // tile height (32, 16, 8, 4 or 2 rows)
     void *x = nullptr, *b = nullptr, *y = nullptr;  // vectors (FP64 or FP32 view)
 };
 
@@ -85,6 +88,8 @@ struct MgDev {
     const MgLevGeom* lg[MG_MAXLEV + 1];
     const MgTile* tiles[MG_MAXLEV + 1];
     const double* coefs[MG_MAXLEV + 1];       // sliced stencils
+    const uint8_t* ring[MG_MAXLEV + 1];       // slices whose stencils reach beyond 3 x 3
+    int32_t th[MG_MAXLEV + 1];                // tile heights
     const double* dinv[MG_MAXLEV + 1];
     T* x[MG_MAXLEV + 1];
     T* b[MG_MAXLEV + 1];

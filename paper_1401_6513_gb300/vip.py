@@ -34,7 +34,7 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_get_stencil", "vip_apply", "vip_convection", "vip_solve", "vip_load_state",
            "vip_set_profiling", "vip_get_profile", "vip_ws_collect", "vip_ws_train",
            "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static",
-           "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters"]
+           "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout"]
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -115,6 +115,8 @@ def lib(path: str | Path | None = None):
                                  C.POINTER(dbl)], C.c_int),
         "vip_set_multigrid": ([vp, C.c_float, C.c_float], C.c_int),
         "vip_get_geometry_iters": ([vp, vp], C.c_int),
+        "vip_operator_layout": ([vp, C.c_int, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64),
+                                 C.POINTER(i64)], C.c_int),
         "vip_autotune": ([vp, C.POINTER(C.c_float), i32, C.POINTER(C.c_float), i32,
                           C.POINTER(TuneResult)], C.c_int),
     }
@@ -287,6 +289,15 @@ class Context:
         return n.value, g.value
 
     # -- inspection ----------------------------------------------------------
+    def vip_operator_layout(self, which):
+        """Device storage of a Krylov operator: dict with slices, uniform_slices,
+        uniform_entries and other_entries (see the C header)."""
+        w = OP[which] if isinstance(which, str) else int(which)
+        v = [C.c_int64() for _ in range(4)]
+        self._check(self.L.vip_operator_layout(self.h, w, *(C.byref(x) for x in v)))
+        return dict(zip(("slices", "uniform_slices", "uniform_entries", "other_entries"),
+                        (x.value for x in v)))
+
     def vip_get_stencil(self, which):
         """Return (row_ptr, col, val) of a table as numpy arrays."""
         w = OP[which] if isinstance(which, str) else int(which)
