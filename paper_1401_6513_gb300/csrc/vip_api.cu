@@ -224,9 +224,7 @@ vip_status vip_set_multigrid(vip_ctx* c, float omega, float corr) {
         cudaGraphExecDestroy(c->graph);  // the captured launch holds the old values
         c->graph = nullptr;
     }
-    c->mg.omega = omega;
-    c->mg.corr = corr;
-    return VIP_OK;
+    return mg_set_params(c, c->mg, omega, corr);
 }
 
 vip_status vip_autotune(vip_ctx* c, const float* omegas, int32_t nomega, const float* corrs, int32_t ncorr,
@@ -254,8 +252,7 @@ vip_status vip_autotune(vip_ctx* c, const float* omegas, int32_t nomega, const f
     for (int i = 0; i < nomega && s == VIP_OK; ++i)
         for (int j = 0; j < ncorr && s == VIP_OK; ++j) {
             const int k = i * ncorr + j;
-            c->mg.omega = omegas[i];
-            c->mg.corr = corrs[j];
+            if ((s = mg_set_params(c, c->mg, omegas[i], corrs[j])) != VIP_OK) break;
             out->omega[k] = omegas[i];
             out->corr[k] = corrs[j];
             if (cudaMemsetAsync(x, 0, c->R * sizeof(double), st) != cudaSuccess ||
@@ -283,8 +280,10 @@ vip_status vip_autotune(vip_ctx* c, const float* omegas, int32_t nomega, const f
     cudaEventDestroy(e1);
     cudaMemsetAsync(c->d_status, 0, 4, st);
     out->ncand = nomega * ncorr;
-    c->mg.omega = keep_w;
-    c->mg.corr = keep_c;
+    {
+        const vip_status s2 = mg_set_params(c, c->mg, keep_w, keep_c);
+        if (s == VIP_OK) s = s2;
+    }
     if (s != VIP_OK) return s;
     if (best < 0) return fail(c, VIP_ERR_NOT_CONVERGED, "vip_autotune: no candidate converged");
     out->best = best;

@@ -201,6 +201,9 @@ vip_status krylov_solve(vip_ctx* c, const KrylovPlan& plan, const Sell& A, const
                         double inner_rtol, const Multigrid* mg = nullptr);
 // multigrid (vip_mg.cu)
 vip_status mg_build(vip_ctx* c, Multigrid& M);
+// Sets the smoother damping and the correction scale; rescales omega * dinv on every
+// level (stream-ordered) when omega changes.
+vip_status mg_set_params(vip_ctx* c, Multigrid& M, float omega, float corr);
 // warm-start network (vip_cnn.cu)
 vip_status cnn_setup(vip_ctx* c, uint64_t seed);
 void cnn_free(vip_ctx* c);

@@ -218,7 +218,7 @@ __device__ __forceinline__ double sell_row(const int64_t* __restrict__ sptr,
 }
 
 template <class T>
-__global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
+__global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     // |r_hat . r| below this fraction of ||r_hat|| ||r|| is rounding noise in T
     // (FP32 vectors of ~1e6 rows: ~6e-8 / sqrt(n) relative noise in a dot product)
     const double bd_tol = sizeof(T) == 8 ? 1e-14 : 1e-9;
@@ -332,11 +332,11 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
     // th warps applies its cell's 5 x 5 stencil (warp = lattice row, coefficients read
     // as one contiguous slice per warp; 3 x 3 where the slice's outer ring is zero).
     // Going down, the tile's residuals are summed over 2 x 2 children straight into
-    // b_{l+1}.
+    // b_{l+1}; going up, level 1 adds corr y_1 to the fine rows of each cell directly
+    // (y_1 is not stored).  The smoothing steps w D^{-1} are precomputed per omega.
     // Only rows of systems still in their inner pass are touched on the fine level.
     const int64_t gtid = (int64_t)blockIdx.x * KTHREADS + threadIdx.x;
     const int64_t gstride = (int64_t)nb * KTHREADS;
-    const double mw = (double)a.mg.omega;
     const double mcorr = (double)a.mg.corr;
     // s_tile[r][c] = f(cell, x, y) for the 32 x th tile at (x0, y0) and its halo (0
     // outside a non-periodic lattice; periodic directions wrap)
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int l = 1; l < L; ++l) {
             const T* bl = M.b[l];
-            const double* dl = M.dinv[l];
+            const double* wdl = M.wdinv[l];
             const int th = M.th[l];
             for (int64_t t = blockIdx.x; t < M.ntiles[l]; t += nb) {
                 const MgTile tile = M.tiles[l][t];
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 const MgLevGeom q = M.lg[l][tile.g];
                 __syncthreads();  // the previous tile's reads of s_tile are done
                 stage(q, tile.x0, tile.y0, th, [&](int64_t j, int, int) {
-                    return mw * __ldg(dl + j) * (double)ldv(bl + j);
+                    return __ldg(wdl + j) * (double)ldv(bl + j);
                 });
                 __syncthreads();
                 const int x = tile.x0 + lane, y = tile.y0 + warp;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
         for (int l = L - 1; l >= 1; --l) {
             const T* sol = (l + 1 == L) ? M.x[L] : M.y[l + 1];
             const T* bl = M.b[l];
-            const double* dl = M.dinv[l];
+            const double* wdl = M.wdinv[l];
             const int th = M.th[l];
             for (int64_t t = blockIdx.x; t < M.ntiles[l]; t += nb) {
                 const MgTile tile = M.tiles[l][t];
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 const MgLevGeom qp = M.lg[l + 1][tile.g];
                 __syncthreads();
                 stage(q, tile.x0, tile.y0, th, [&](int64_t j, int xx, int yy) {
-                    return mw * __ldg(dl + j) * (double)ldv(bl + j) +
+                    return __ldg(wdl + j) * (double)ldv(bl + j) +
                            mcorr * (double)ldv(sol + qp.off + (int64_t)(yy >> 1) * qp.sx + (xx >> 1));
                 });
                 __syncthreads();
@@ -479,14 +479,24 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 const bool wide = __any_sync(0xffffffffu, in && __ldg(M.ring[l] + (c >> 5)));
                 if (in) {
                     const double r = (double)ldv(bl + c) - stencil(l, c, wide);
-                    M.y[l][c] = (T)(s_tile[warp + 2][lane + 2] + mw * __ldg(dl + c) * r);
+                    const T y = (T)(s_tile[warp + 2][lane + 2] + __ldg(wdl + c) * r);
+                    if (l > 1) {
+                        M.y[l][c] = y;
+                    } else {  // fine prolongation f += corr y_1 over the cell's rows
+                        const int64_t q1 = __ldg(M.cptr + c + 1);
+                        for (int64_t qq = __ldg(M.cptr + c); qq < q1; ++qq) {
+                            const int32_t row = __ldg(M.crow + qq);
+                            M.fx[row] = (T)((double)ldv(M.fx + row) + mcorr * (double)y);
+                        }
+                    }
                 }
             }
             if (!grid_sync(a.bar, nb, a.status)) return false;
         }
-        // fine prolongation f += corr s_1(agg) (four slices of the warp at a time)
-        {
-            const T* sol1 = (L == 1) ? M.x[1] : M.y[1];
+        // fine prolongation f += corr s_1(agg) when level 1 is the coarsest (four slices
+        // of the warp at a time); otherwise the level-1 pass above did it
+        if (L == 1) {
+            const T* sol1 = M.x[1];
             for (int sl0 = s0 + warp; sl0 < s1; sl0 += 4 * KWARPS) {
                 int32_t cc[4];
                 int64_t rw[4];
@@ -507,14 +517,14 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 for (int u = 0; u < 4; ++u)
                     if (cc[u] >= 0) M.fx[rw[u]] = (T)(fv[u] + mcorr * sv[u]);
             }
+            if (!grid_sync(a.bar, nb, a.status)) return false;
         }
-        if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
             const int g = a.slice_sys[sl];
             if (!S[g].inner_active) continue;
             const int64_t row = (int64_t)sl * 32 + lane;
             const double r = (double)ldv(v + row) - spmv_row(sl, a.aT, M.fx);
-            z[row] = (T)((double)ldv(M.fx + row) + mw * __ldg(M.fdinv + row) * r);
+            z[row] = (T)((double)ldv(M.fx + row) + __ldg(M.fwdinv + row) * r);
         }
         return grid_sync(a.bar, nb, a.status);
     };
@@ -635,7 +645,7 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 double pn = (double)ldv(a.r + row) +
                             S[g].beta * ((double)ldv(a.p + row) - S[g].omega * (double)ldv(a.v + row));
                 a.p[row] = (T)pn;
-                if (a.use_mg) a.mg.fx[row] = (T)(mw * (double)__ldg(a.mg.fdinv + row) * (double)(T)pn);
+                if (a.use_mg) a.mg.fx[row] = (T)(__ldg(a.mg.fwdinv + row) * (double)(T)pn);
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
             if (a.use_mg && !vcycle(a.p, a.phat)) { alive = false; break; }
@@ -673,7 +683,7 @@ __global__ void __launch_bounds__(KTHREADS) k_bicgstab(KArgs<T> a) {
                 int64_t row = (int64_t)sl * 32 + lane;
                 const T si = (T)((double)ldv(a.r + row) - S[g].alpha * (double)ldv(a.v + row));
                 a.s[row] = si;
-                if (a.use_mg) a.mg.fx[row] = (T)(mw * (double)__ldg(a.mg.fdinv + row) * (double)si);
+                if (a.use_mg) a.mg.fx[row] = (T)(__ldg(a.mg.fwdinv + row) * (double)si);
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
             if (a.use_mg && !vcycle(a.s, a.shat)) { alive = false; break; }
@@ -909,7 +919,7 @@ static MgDev<T> mg_view(const Multigrid& M) {
     d.nlev = M.nlev;
     d.ngeom = M.ngeom;
     d.agg = M.agg; d.cptr = M.cptr; d.crow = M.crow;
-    d.fdinv = M.fdinv;
+    d.fwdinv = M.fwdinv;
     d.fr = (T*)M.fr; d.fx = (T*)M.fx;
     for (int l = 1; l <= M.nlev; ++l) {
         const MgLevel& v = M.lev[l];
@@ -920,10 +930,9 @@ static MgDev<T> mg_view(const Multigrid& M) {
         d.coefs[l] = v.coefs;
         d.ring[l] = v.ring;
         d.th[l] = v.th;
-        d.dinv[l] = v.dinv;
+        d.wdinv[l] = v.wdinv;
         d.x[l] = (T*)v.x; d.b[l] = (T*)v.b; d.y[l] = (T*)v.y;
     }
-    d.omega = M.omega;
     d.corr = M.corr;
     d.cinv = M.cinv;
     d.cinv_off = M.cinv_off;

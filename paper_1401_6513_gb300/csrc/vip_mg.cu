@@ -170,6 +170,28 @@ __global__ void k_mg_fine_diag(Sell A, double* __restrict__ dinv) {
     dinv[r] = s != 0.0 ? (d < 0.0 ? -1.0 : 1.0) / s : 0.0;
 }
 
+// w[i] = omega * d[i]
+__global__ void k_mg_scale(int64_t n, double omega, const double* __restrict__ d, double* __restrict__ w) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] = omega * d[i];
+}
+
+vip_status mg_set_params(vip_ctx* c, Multigrid& M, float omega, float corr) {
+    M.corr = corr;
+    M.omega = omega;
+    if (!M.built || M.scaled_omega == omega) return VIP_OK;
+    const int TB = 256;
+    cudaStream_t st = c->stream;
+    k_mg_scale<<<(unsigned)((c->R + TB - 1) / TB), TB, 0, st>>>(c->R, (double)omega, M.fdinv, M.fwdinv);
+    for (int l = 1; l <= M.nlev; ++l) {
+        const MgLevel& lv = M.lev[l];
+        k_mg_scale<<<(unsigned)((lv.n + TB - 1) / TB), TB, 0, st>>>(lv.n, (double)omega, lv.dinv, lv.wdinv);
+    }
+    VIP_CUDA(cudaGetLastError());
+    M.scaled_omega = omega;
+    return VIP_OK;
+}
+
 // Dense inverse of one geometry's coarsest operator, A (m x m, row-major), by
 // Gauss-Jordan elimination with partial pivoting in FP64 on the host (setup only).
 // Cells without a row (empty cells) are decoupled: their unknown stays 0.  The
@@ -295,6 +317,7 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         VIP_CUDA(dalloc(c, &lv.coef, 25 * n));
         VIP_CUDA(dalloc(c, &lv.coefs, 25 * n));
         VIP_CUDA(dalloc(c, &lv.dinv, n));
+        VIP_CUDA(dalloc(c, &lv.wdinv, n));
         VIP_CUDA(dalloc(c, &lv.ring, n / 32));
         {
             // Tile height: a level with few 32 x 32 tiles would keep most SMs idle
@@ -436,6 +459,7 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         M.ngeom = G;
     }
     VIP_CUDA(dalloc(c, &M.fdinv, R));
+    VIP_CUDA(dalloc(c, &M.fwdinv, R));
     k_mg_fine_diag<<<(unsigned)((R + TB - 1) / TB), TB, 0, st>>>(A, M.fdinv);
     VIP_CUDA(cudaGetLastError());
     {
@@ -447,6 +471,10 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
     }
     VIP_CUDA(cudaStreamSynchronize(st));
     M.built = true;
+    M.scaled_omega = -1.0f;
+    vip_status s = mg_set_params(c, M, M.omega, M.corr);
+    if (s != VIP_OK) return s;
+    VIP_CUDA(cudaStreamSynchronize(st));
     return VIP_OK;
 }
 

@@ -46,6 +46,7 @@ struct MgLevel {                  // coarse level (all geometries concatenated)
     double* coef = nullptr;       // [25][n] Galerkin stencil (setup layout)
     double* coefs = nullptr;      // the same, sliced: [n/32][25][32] (V-cycle layout)
     double* dinv = nullptr;       // [n] l1-Jacobi scaling (0 for empty and padding cells)
+    double* wdinv = nullptr;      // [n] omega * dinv (the smoother's step)
     uint8_t* ring = nullptr;      // [n/32] 1 if a cell of the slice has a nonzero outside its 3 x 3 core
     MgLevGeom* lg = nullptr;      // [G] lattice of each geometry on this level
     MgTile* tiles = nullptr;      // 32 x th tiles covering every geometry's lattice
@@ -63,6 +64,7 @@ struct Multigrid {
     int64_t* cptr = nullptr;      // [n1+1] fine rows of each level-1 cell
     int32_t* crow = nullptr;
     double* fdinv = nullptr;      // [R] l1-Jacobi scaling of the fine operator
+    double* fwdinv = nullptr;     // [R] omega * fdinv
     void* fr = nullptr;           // [R] fine residual scratch
     void* fx = nullptr;           // [R] fine smoothing scratch
     double* cinv = nullptr;       // dense inverse of each geometry's coarsest operator (row-major)
@@ -70,6 +72,7 @@ struct Multigrid {
     int ngeom = 0;
     float omega = 1.0f;           // smoother damping (vip_set_multigrid / vip_autotune)
     float corr = 1.5f;            // scaling of the coarse-grid correction
+    float scaled_omega = -1.0f;   // the omega that fwdinv and wdinv hold
 };
 
 // Device view of the hierarchy, vectors in precision T (operators in FP64).
@@ -80,7 +83,7 @@ struct MgDev {
     const int32_t* agg;
     const int64_t* cptr;
     const int32_t* crow;
-    const double* fdinv;
+    const double* fwdinv;   // omega * fine l1-Jacobi scaling
     T* fr;
     T* fx;
     int64_t n[MG_MAXLEV + 1];
@@ -90,11 +93,10 @@ struct MgDev {
     const double* coefs[MG_MAXLEV + 1];       // sliced stencils
     const uint8_t* ring[MG_MAXLEV + 1];       // slices whose stencils reach beyond 3 x 3
     int32_t th[MG_MAXLEV + 1];                // tile heights
-    const double* dinv[MG_MAXLEV + 1];
+    const double* wdinv[MG_MAXLEV + 1];       // omega * l1-Jacobi scaling
     T* x[MG_MAXLEV + 1];
     T* b[MG_MAXLEV + 1];
     T* y[MG_MAXLEV + 1];
-    float omega;       // smoother damping
     float corr;        // scaling of the coarse-grid correction (piecewise-constant prolongation)
     const double* cinv;
     const int64_t* cinv_off;

@@ -360,11 +360,19 @@ def geometry_signature(nodesets) -> str:
     return "|".join(parts) + "|" + hsh.hexdigest()[:16]
 
 
-def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.7, 1.9, 2.1)):
+def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.7, 1.9, 2.1),
+             refine=3, refine_steps=3):
     """Pick the multigrid parameters of a context built from `nodesets`: from the JSON
-    file `cache` when it has this geometry signature, else by vip_autotune after one
-    step (the state is then reset to the node sets' initial fields) and stored there.
-    Returns the chosen {"omega", "corr", ...} entry."""
+    file `cache` when it has this geometry signature, else in two stages, then store
+    the choice there:
+      1. vip_autotune after one step: every (omega, corr) pair solves that step's
+         pressure-increment system from a zero guess, timed on the device;
+      2. the `refine` fastest pairs each run `refine_steps` steps from the node sets'
+         initial fields, scored by the Poisson iterations of the steps after the first
+         (warm-started like the steps that follow; the cost of an iteration does not
+         depend on the pair, so iterations rank them without timing noise).
+    The state is reset to the initial fields afterwards.  Returns the chosen
+    {"omega", "corr", ...} entry."""
     import json
     key = geometry_signature(nodesets)
     table = {}
@@ -374,11 +382,30 @@ def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.7,
         entry = table[key]
         ctx.vip_set_multigrid(entry["omega"], entry["corr"])
         return dict(entry, cached=True)
+
+    def reset():
+        ctx.vip_set_state(np.concatenate([ns.u0 for ns in nodesets]),
+                          np.concatenate([ns.v0 for ns in nodesets]),
+                          np.concatenate([ns.p0 for ns in nodesets]))
+
     ctx.vip_step(1)
     entry = ctx.vip_autotune(omegas, corrs).as_dict()
-    ctx.vip_set_state(np.concatenate([ns.u0 for ns in nodesets]),
-                      np.concatenate([ns.v0 for ns in nodesets]),
-                      np.concatenate([ns.p0 for ns in nodesets]))
+    cands = sorted((c for c in entry["candidates"] if c["ms"] >= 0), key=lambda c: c["ms"])[:refine]
+    if refine_steps > 1 and len(cands) > 1:
+        scored = []
+        for c in cands:
+            ctx.vip_set_multigrid(c["omega"], c["corr"])
+            reset()
+            ctx.vip_step(1)
+            i0 = ctx.vip_get_stats().total_poisson_iters
+            ctx.vip_step(refine_steps - 1)
+            c["step_iters"] = ctx.vip_get_stats().total_poisson_iters - i0
+            scored.append(c)
+        best = min(scored, key=lambda c: (c["step_iters"], c["ms"]))
+        entry["omega"], entry["corr"] = best["omega"], best["corr"]
+        entry["refined_on_steps"] = refine_steps - 1
+    ctx.vip_set_multigrid(entry["omega"], entry["corr"])
+    reset()
     if cache is not None:
         table[key] = entry
         Path(cache).parent.mkdir(parents=True, exist_ok=True)
