@@ -12,8 +12,9 @@
 // the mixed form (FP32 operator copy and FP32 vectors inside, tol_in =
 // max(inner_rtol ||r||, rtol ||b|| / 2)).
 //
-// Every system keeps its own scalars; all systems advance in lock step and a
-// finished system idles.  Dot products are reduced deterministically: warp
+// Every system keeps its own scalars; all systems advance in lock step, and the
+// slices of the systems still iterating are re-spread over all blocks whenever a
+// system finishes.  Dot products are reduced deterministically: warp
 // shuffles, per-warp partials summed in warp order, per-block partials summed in
 // block order by every block, so all blocks hold identical scalars.  Blocks
 // meet at a grid barrier whose wait is bounded (2 s, then VIP_ERR_TIMEOUT).
@@ -29,6 +30,7 @@ namespace vip {
 constexpr int KTHREADS = 1024;
 constexpr int KWARPS = KTHREADS / 32;
 constexpr int MAXSYS = 128;
+constexpr int KSMEM_DYN = 36 * 36 * (int)sizeof(double);  // a coarse tile and its halo
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -100,6 +102,8 @@ struct KArgs {
     const int32_t* blk_ng;
     const int32_t* sys_b0;
     const int32_t* sys_b1;
+    const int32_t* sys_s0;   // [nsys] first slice of each system
+    const int32_t* sys_s1;   // [nsys] one past its last slice
     double* partial;     // [2][nsys][NQ][nblocks], zero where a block has no rows of a system
     uint32_t* bar;
     int nsys;
@@ -225,13 +229,134 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     __shared__ double sacc[KWARPS][MAXSYS_PB][NQ];
     __shared__ double stot[MAXSYS][NQ];
     __shared__ SysState S[MAXSYS];
-    __shared__ double s_tile[36][36];  // multigrid: a coarse tile and its halo
+    extern __shared__ double s_tile[];  // multigrid: a coarse tile and its halo, 36 x 36
     __shared__ int s_any;
+    // work partition: this block's slices are p_nv "virtual" slices in p_nseg
+    // segments, segment k being the slices p_segs[k] + [0, p_segv[k+1] - p_segv[k]);
+    // its dot-product slots j < p_ng belong to systems p_sys[j] (p_j[g] = slot of
+    // system g, -1 if none); the partials of system g come from blocks
+    // [p_b0[g], p_b1[g])
+    __shared__ int p_nv, p_nseg, p_ng, p_valid;
+    __shared__ int p_segv[MAXSYS_PB + 1], p_segs[MAXSYS_PB];
+    __shared__ int p_b0[MAXSYS], p_b1[MAXSYS], p_j[MAXSYS], p_sys[MAXSYS_PB];
+    __shared__ int p_ss0[MAXSYS], p_ss1[MAXSYS];
+    __shared__ uint32_t p_mask[MAXSYS / 32];
     const int bid = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s0 = a.blk_s0[bid], s1 = a.blk_s1[bid], g0 = a.blk_g0[bid];
     const unsigned nb = gridDim.x;
     const int nsys = a.nsys;
+    for (int g = threadIdx.x; g < nsys; g += KTHREADS) {
+        p_ss0[g] = a.sys_s0[g];
+        p_ss1[g] = a.sys_s1[g];
+    }
+    if (threadIdx.x == 0) p_valid = 0;
+    int nv = 0, ng_blk = 0, seg0 = 0;
+    bool one_seg = true, p_valid_r = false;
+    // slice of virtual index v; sg (the segment of the previous call) only advances,
+    // as each warp's v increases; a block of one segment needs no lookup
+    auto vslice = [&](int v, int& sg) {
+        if (one_seg) return seg0 + v;
+        while (v >= p_segv[sg + 1]) ++sg;
+        return p_segs[sg] + (v - p_segv[sg]);
+    };
+    // The slices of the systems still being solved (outer set: solving or to be
+    // zeroed; inner set: inside a BiCGSTAB pass) are spread evenly over all blocks,
+    // recomputed whenever that set changes, so that blocks whose systems have
+    // finished take over the work of the others.  Every block computes the whole
+    // partition from the same system states, so all blocks agree without
+    // communicating.  A block holds one segment of slices per active system in its
+    // range (finished systems in between are passed over) and reduces only for
+    // those systems.  A partition in which some block would hold more than
+    // MAXSYS_PB active systems is replaced by the launch's static one (one segment
+    // of all slices, finished systems' rows skipped).
+    auto repartition = [&](int inner) {
+        if (nsys == 1 && p_valid_r) return;  // one system: the partition never changes
+        p_valid_r = true;
+        if (threadIdx.x == 0) {
+            uint32_t m[MAXSYS / 32];
+            for (int w = 0; w < MAXSYS / 32; ++w) m[w] = 0;
+            for (int g = 0; g < nsys; ++g) {
+                const bool on = inner ? S[g].inner_active : (S[g].outer_active || S[g].zero_x);
+                if (on) m[g >> 5] |= 1u << (g & 31);
+            }
+            bool same = p_valid != 0;
+            for (int w = 0; w < MAXSYS / 32; ++w) same = same && m[w] == p_mask[w];
+            if (!same) {
+                auto on = [&](int g) { return ((m[g >> 5] >> (g & 31)) & 1u) != 0; };
+                auto len = [&](int g) -> int64_t { return on(g) ? (int64_t)(p_ss1[g] - p_ss0[g]) : 0; };
+                int64_t W = 0;
+                for (int g = 0; g < nsys; ++g) W += len(g);
+                for (int g = 0; g < nsys; ++g) { p_b0[g] = 0; p_b1[g] = 0; p_j[g] = -1; }
+                p_nv = p_nseg = p_ng = 0;
+                p_segv[0] = 0;
+                bool ok = true;
+                int gl = 0, gh = 0;
+                int64_t cl = 0, ch = 0;  // active slices of the systems before gl, gh
+                // block b takes the active slices [W b / nb, W (b + 1) / nb); a block
+                // with none (fewer active slices than blocks) holds an empty range
+                // of the active system at its position, for which it reduces a zero,
+                // so that the blocks listed for a system are exactly those that
+                // write its partials
+                for (int b = 0; b < (int)nb && ok && W > 0; ++b) {
+                    const int64_t lo = W * b / nb, hi = W * (b + 1) / nb;
+                    while (lo >= cl + len(gl)) { cl += len(gl); ++gl; }
+                    int last = gl;
+                    if (hi > lo) {
+                        while (hi - 1 >= ch + len(gh)) { ch += len(gh); ++gh; }
+                        last = gh;
+                    }
+                    int cnt = 0;
+                    for (int g = gl; g <= last; ++g) cnt += on(g) ? 1 : 0;
+                    if (cnt > MAXSYS_PB) { ok = false; break; }
+                    if (b == (int)bid) {
+                        int64_t cg = cl;  // active slices before system g
+                        for (int g = gl; g <= last; ++g) {
+                            if (!on(g)) continue;
+                            p_j[g] = p_ng;
+                            p_sys[p_ng] = g;
+                            ++p_ng;
+                            const int64_t v0 = lo > cg ? lo : cg;
+                            const int64_t v1 = hi < cg + len(g) ? hi : cg + len(g);
+                            if (v1 > v0) {
+                                p_segs[p_nseg] = p_ss0[g] + (int)(v0 - cg);
+                                p_segv[p_nseg + 1] = p_segv[p_nseg] + (int)(v1 - v0);
+                                ++p_nseg;
+                            }
+                            cg += len(g);
+                        }
+                        p_nv = p_segv[p_nseg];
+                    }
+                    for (int g = gl; g <= last; ++g) {
+                        if (!on(g)) continue;
+                        if (p_b1[g] == 0) p_b0[g] = b;
+                        p_b1[g] = b + 1;
+                    }
+                }
+                if (!ok) {  // the static partition: every system of the block's range
+                    const int g0 = a.blk_g0[bid];
+                    p_nseg = 1;
+                    p_segs[0] = a.blk_s0[bid];
+                    p_segv[0] = 0;
+                    p_segv[1] = a.blk_s1[bid] - a.blk_s0[bid];
+                    p_nv = p_segv[1];
+                    p_ng = a.blk_ng[bid];
+                    for (int g = 0; g < nsys; ++g) {
+                        p_b0[g] = a.sys_b0[g];
+                        p_b1[g] = a.sys_b1[g];
+                        p_j[g] = (g >= g0 && g < g0 + p_ng) ? g - g0 : -1;
+                    }
+                    for (int j = 0; j < p_ng; ++j) p_sys[j] = g0 + j;
+                }
+                for (int w = 0; w < MAXSYS / 32; ++w) p_mask[w] = m[w];
+                p_valid = 1;
+            }
+        }
+        __syncthreads();
+        nv = p_nv;
+        ng_blk = p_ng;
+        one_seg = p_nseg <= 1;
+        seg0 = p_nseg >= 1 ? p_segs[0] : 0;
+    };
 
     auto clear_acc = [&]() {
         for (int i = threadIdx.x; i < KWARPS * MAXSYS_PB * NQ; i += KTHREADS)
@@ -243,7 +368,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     // FP64 butterfly is costly on this GPU's FP64 pipe); a warp whose slices change
     // system flushes at the change.  The order is fixed, so sums are deterministic.
     double qacc[NQ];
-    int qj = -1;
+    int qj = -1, qg = -1;
     auto flush_acc = [&](int nq) {  // warp-uniform
         if (qj >= 0)
             for (int k = 0; k < nq; ++k) {
@@ -251,12 +376,14 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 if (lane == 0) sacc[warp][qj][k] += w;
             }
         qj = -1;
+        qg = -1;
     };
-    // accumulate a row's contributions q[0..nq) for system j (warp-uniform j)
-    auto acc = [&](int j, int nq, const double* q) {
-        if (j != qj) {
+    // accumulate a row's contributions q[0..nq) for system g (warp-uniform g)
+    auto acc = [&](int g, int nq, const double* q) {
+        if (g != qg) {
             flush_acc(nq);
-            qj = j;
+            qg = g;
+            qj = p_j[g];
             for (int k = 0; k < nq; ++k) qacc[k] = 0.0;
         }
         for (int k = 0; k < nq; ++k) qacc[k] += q[k];
@@ -268,7 +395,6 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     // Two partial sets used by alternate reductions: a block that has read one
     // reduction's totals and runs ahead into the next one writes the other set, so
     // it never overwrites a partial that a slower block is still reading.
-    const int ng_blk = a.blk_ng[bid];
     int pset = 0;
     auto reduce = [&](int nq) -> bool {
         flush_acc(nq);
@@ -279,14 +405,14 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             int j = i / nq, k = i % nq;
             double sum = 0.0;
             for (int w = 0; w < KWARPS; ++w) sum += sacc[w][j][k];
-            __stcg(&part[((int64_t)(g0 + j) * NQ + k) * nb + bid], sum);
+            __stcg(&part[((int64_t)p_sys[j] * NQ + k) * nb + bid], sum);
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int i = warp; i < nsys * nq; i += KWARPS) {
             int g = i / nq, k = i % nq;
             const double* src = part + ((int64_t)g * NQ + k) * nb;
             double sum = 0.0;
-            for (int bb = a.sys_b0[g] + lane; bb < a.sys_b1[g]; bb += 32) sum += __ldcg(src + bb);
+            for (int bb = p_b0[g] + lane; bb < p_b1[g]; bb += 32) sum += __ldcg(src + bb);
             sum = wsum(sum);
             if (lane == 0) stot[g][k] = sum;
         }
@@ -338,7 +464,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     const int64_t gtid = (int64_t)blockIdx.x * KTHREADS + threadIdx.x;
     const int64_t gstride = (int64_t)nb * KTHREADS;
     const double mcorr = (double)a.mg.corr;
-    // s_tile[r][c] = f(cell, x, y) for the 32 x th tile at (x0, y0) and its halo (0
+    // s_tile[36 r + c] = f(cell, x, y) for the 32 x th tile at (x0, y0) and its halo (0
     // outside a non-periodic lattice; periodic directions wrap)
     auto stage = [&](const MgLevGeom& q, int x0, int y0, int th, auto&& f) {
         double v[2];
@@ -358,10 +484,10 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = threadIdx.x + h * KTHREADS;
-            if (k < nst) s_tile[k / 36][k % 36] = v[h];
+            if (k < nst) s_tile[k] = v[h];
         }
     };
-    // sum_o A_l[c, o] s_tile[warp + dy][lane + dx] for the thread's cell c, in offset
+    // sum_o A_l[c, o] s_tile[36 (warp + dy) + lane + dx] for the thread's cell c, in offset
     // order; a warp whose slices hold no nonzero outside the 3 x 3 core (wide false,
     // warp-uniform) skips the zero products, which leaves the sum unchanged
     auto stencil = [&](int l, int64_t c, bool wide) -> double {
@@ -369,13 +495,13 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
         double acc = 0.0;
         if (wide) {
 #pragma unroll
-            for (int o = 0; o < 25; ++o) acc += ldm(cp + o * 32) * s_tile[warp + o / 5][lane + o % 5];
+            for (int o = 0; o < 25; ++o) acc += ldm(cp + o * 32) * s_tile[(warp + o / 5) * 36 + lane + o % 5];
         } else {
 #pragma unroll
             for (int dy = 1; dy <= 3; ++dy)
 #pragma unroll
                 for (int dx = 1; dx <= 3; ++dx)
-                    acc += ldm(cp + (dy * 5 + dx) * 32) * s_tile[warp + dy][lane + dx];
+                    acc += ldm(cp + (dy * 5 + dx) * 32) * s_tile[(warp + dy) * 36 + lane + dx];
         }
         return acc;
     };
@@ -383,7 +509,8 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     auto vcycle = [&](const T* v, T* z) -> bool {
         const MgDev<T>& M = a.mg;
         const int L = M.nlev;
-        for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+        for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+            const int sl = vslice(iv, sg);
             const int g = a.slice_sys[sl];
             const int64_t row = (int64_t)sl * 32 + lane;
             T res = (T)0;
@@ -418,14 +545,14 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 double r = 0.0;
                 if (in) r = (double)ldv(bl + c) - stencil(l, c, wide);
                 __syncthreads();
-                if (warp < th) (&s_tile[0][0])[warp * 32 + lane] = r;
+                if (warp < th) s_tile[warp * 32 + lane] = r;
                 __syncthreads();
                 if (threadIdx.x < th * 8) {  // 16 x th/2 cells of level l+1
                     const int px = threadIdx.x & 15, py = threadIdx.x >> 4;
                     const MgLevGeom qp = M.lg[l + 1][tile.g];
                     const int X = (tile.x0 >> 1) + px, Y = (tile.y0 >> 1) + py;
                     if (X < qp.nx && Y < qp.ny) {
-                        const double* rs = &s_tile[0][0];
+                        const double* rs = s_tile;
                         const int k0 = (2 * py) * 32 + 2 * px;
                         M.b[l + 1][qp.off + (int64_t)Y * qp.sx + X] =
                             (T)((rs[k0] + rs[k0 + 1]) + (rs[k0 + 32] + rs[k0 + 33]));
@@ -479,7 +606,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 const bool wide = __any_sync(0xffffffffu, in && __ldg(M.ring[l] + (c >> 5)));
                 if (in) {
                     const double r = (double)ldv(bl + c) - stencil(l, c, wide);
-                    const T y = (T)(s_tile[warp + 2][lane + 2] + __ldg(wdl + c) * r);
+                    const T y = (T)(s_tile[(warp + 2) * 36 + lane + 2] + __ldg(wdl + c) * r);
                     if (l > 1) {
                         M.y[l][c] = y;
                     } else {  // fine prolongation f += corr y_1 over the cell's rows
@@ -493,33 +620,21 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             }
             if (!grid_sync(a.bar, nb, a.status)) return false;
         }
-        // fine prolongation f += corr s_1(agg) when level 1 is the coarsest (four slices
-        // of the warp at a time); otherwise the level-1 pass above did it
+        // fine prolongation f += corr s_1(agg) when level 1 is the coarsest; otherwise
+        // the level-1 pass above did it
         if (L == 1) {
             const T* sol1 = M.x[1];
-            for (int sl0 = s0 + warp; sl0 < s1; sl0 += 4 * KWARPS) {
-                int32_t cc[4];
-                int64_t rw[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int sl = sl0 + u * KWARPS;
-                    cc[u] = -1;
-                    rw[u] = (int64_t)sl * 32 + lane;
-                    if (sl < s1 && S[a.slice_sys[sl]].inner_active) cc[u] = __ldg(M.agg + rw[u]);
-                }
-                double sv[4], fv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    sv[u] = cc[u] >= 0 ? (double)ldv(sol1 + cc[u]) : 0.0;
-                    fv[u] = cc[u] >= 0 ? (double)ldv(M.fx + rw[u]) : 0.0;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (cc[u] >= 0) M.fx[rw[u]] = (T)(fv[u] + mcorr * sv[u]);
+            for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+                const int sl = vslice(iv, sg);
+                if (!S[a.slice_sys[sl]].inner_active) continue;
+                const int64_t rw = (int64_t)sl * 32 + lane;
+                const int32_t cc = __ldg(M.agg + rw);
+                if (cc >= 0) M.fx[rw] = (T)((double)ldv(M.fx + rw) + mcorr * (double)ldv(sol1 + cc));
             }
             if (!grid_sync(a.bar, nb, a.status)) return false;
         }
-        for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+        for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+            const int sl = vslice(iv, sg);
             const int g = a.slice_sys[sl];
             if (!S[g].inner_active) continue;
             const int64_t row = (int64_t)sl * 32 + lane;
@@ -541,9 +656,11 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
 
     bool alive = true;
     for (int outer = 0; alive; ++outer) {
+        repartition(0);
         // ---- X: apply the correction of the previous pass
         if (outer > 0) {
-            for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+            for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+                const int sl = vslice(iv, sg);
                 int g = a.slice_sys[sl];
                 int64_t row = (int64_t)sl * 32 + lane;
                 if (S[g].zero_x) a.x[row] = 0.0;
@@ -554,7 +671,8 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
         }
         // ---- R: FP64 residual, inner initialisation
         clear_acc();
-        for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+        for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+            const int sl = vslice(iv, sg);
             int g = a.slice_sys[sl];
             if (!S[g].outer_active) continue;
             int64_t row = (int64_t)sl * 32 + lane;
@@ -567,7 +685,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             a.v[row] = (T)0;
             a.dx[row] = (T)0;
             double q[3] = {ri * ri, bi * bi, (double)rt * (double)rt};
-            acc(g - g0, 3, q);
+            acc(g, 3, q);
         }
         if (!reduce(3)) { alive = false; break; }
         if (threadIdx.x < nsys) {
@@ -622,7 +740,8 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
         any_zero = s_any != 0;
         if (!any_of(0)) {
             if (any_zero) {  // final zeroing pass
-                for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+                for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+                    const int sl = vslice(iv, sg);
                     int g = a.slice_sys[sl];
                     if (S[g].zero_x) a.x[(int64_t)sl * 32 + lane] = 0.0;
                 }
@@ -632,13 +751,15 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
 
         // ---- inner BiCGSTAB pass
         while (any_of(1)) {
+            repartition(1);
             // A: beta, p = r + beta (p - omega v)
             if (threadIdx.x < nsys) {
                 SysState& st = S[threadIdx.x];
                 if (st.inner_active) st.beta = (st.rho / st.rho_old) * (st.alpha / st.omega);
             }
             __syncthreads();
-            for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+            for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+                const int sl = vslice(iv, sg);
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
@@ -651,14 +772,15 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             if (a.use_mg && !vcycle(a.p, a.phat)) { alive = false; break; }
             // B: v = A phat, rhat . v
             clear_acc();
-            for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+            for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+                const int sl = vslice(iv, sg);
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
                 double vi = spmv_row(sl, a.aT, a.phat);
                 a.v[row] = (T)vi;
                 double q[2] = {(double)ldv(a.rhat + row) * (double)(T)vi, (double)(T)vi * (double)(T)vi};
-                acc(g - g0, 2, q);
+                acc(g, 2, q);
             }
             if (!reduce(2)) { alive = false; break; }
             if (threadIdx.x < nsys) {
@@ -677,7 +799,8 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             }
             __syncthreads();
             // C: s = r - alpha v
-            for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+            for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+                const int sl = vslice(iv, sg);
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
@@ -689,7 +812,8 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             if (a.use_mg && !vcycle(a.s, a.shat)) { alive = false; break; }
             // D: t = A shat; t.s, t.t, s.s
             clear_acc();
-            for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+            for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+                const int sl = vslice(iv, sg);
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
@@ -697,7 +821,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 a.t[row] = ti;
                 double si = (double)ldv(a.s + row);
                 double q[3] = {(double)ti * si, (double)ti * (double)ti, si * si};
-                acc(g - g0, 3, q);
+                acc(g, 3, q);
             }
             if (!reduce(3)) { alive = false; break; }
             if (threadIdx.x < nsys) {
@@ -722,7 +846,8 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             __syncthreads();
             // E: d += alpha p + omega s; r = s - omega t; rhat.r, r.r
             clear_acc();
-            for (int sl = s0 + warp; sl < s1; sl += KWARPS) {
+            for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+                const int sl = vslice(iv, sg);
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
@@ -734,7 +859,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 T rn = (T)(si - om * (double)ldv(a.t + row));
                 a.r[row] = rn;
                 double q[2] = {(double)ldv(a.rhat + row) * (double)rn, (double)rn * (double)rn};
-                acc(g - g0, 2, q);
+                acc(g, 2, q);
             }
             if (!reduce(2)) { alive = false; break; }
             if (threadIdx.x < nsys) {
@@ -779,9 +904,19 @@ vip_status krylov_plan(vip_ctx* c, KrylovPlan& P, const Sell& A, const std::vect
         c->err = "too many systems in one Krylov batch (limit 128)";
         return VIP_ERR_ARG;
     }
+    // the coarse tile lives in dynamic shared memory (above the static 48 KB limit
+    // together with the rest; set here, outside any graph capture)
+    VIP_CUDA(cudaFuncSetAttribute(k_bicgstab<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSMEM_DYN));
+    VIP_CUDA(cudaFuncSetAttribute(k_bicgstab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSMEM_DYN));
+    // as much L1 as possible for the vector gathers: the smallest shared-memory
+    // configuration that holds the block's ~51 KB
+    VIP_CUDA(cudaFuncSetAttribute(k_bicgstab<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxL1));
+    VIP_CUDA(cudaFuncSetAttribute(k_bicgstab<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxL1));
     int occ64 = 0, occ32 = 0;
-    VIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_bicgstab<double>, KTHREADS, 0));
-    VIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_bicgstab<float>, KTHREADS, 0));
+    VIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_bicgstab<double>, KTHREADS, KSMEM_DYN));
+    VIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_bicgstab<float>, KTHREADS, KSMEM_DYN));
     int occ = std::max(1, std::min(std::min(occ64, occ32), 1));
     const int64_t nsl = A.nslices;
     std::vector<int32_t> slice_sys(nsl, -1);
@@ -952,6 +1087,7 @@ static vip_status launch(vip_ctx* c, const KrylovPlan& P, const Sell& A, const d
     a.slice_sys = P.slice_sys; a.blk_s0 = P.blk_s0; a.blk_s1 = P.blk_s1; a.blk_g0 = P.blk_g0;
     a.blk_ng = P.blk_ng;
     a.sys_b0 = P.sys_b0; a.sys_b1 = P.sys_b1; a.partial = P.partial; a.bar = P.bar;
+    a.sys_s0 = P.sys_s0; a.sys_s1 = P.sys_s1;
     a.nsys = P.nsys; a.b = b; a.x = x;
     a.r = (T*)W.r; a.rhat = (T*)W.rhat; a.p = (T*)W.p; a.v = (T*)W.v; a.s = (T*)W.s;
     a.t = (T*)W.t; a.dx = (T*)W.dx;
@@ -975,7 +1111,7 @@ static vip_status launch(vip_ctx* c, const KrylovPlan& P, const Sell& A, const d
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(P.nblocks);
     cfg.blockDim = dim3(P.nthreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = a.use_mg ? KSMEM_DYN : 0;
     cfg.stream = c->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
