@@ -221,6 +221,112 @@ __device__ __forceinline__ double sell_row(const int64_t* __restrict__ sptr,
     return sum;
 }
 
+// Work partition of one block of the Krylov launch (see k_bicgstab): this block's
+// slices are nv "virtual" slices in nseg segments, segment k being the slices
+// segs[k] + [0, segv[k+1] - segv[k]); its dot-product slots j < ng belong to systems
+// sys[j] (j[g] = slot of system g, -1 if none); the partials of system g come from
+// blocks [b0[g], b1[g]).
+struct Partition {
+    int nv, nseg, ng, valid;
+    int segv[MAXSYS_PB + 1], segs[MAXSYS_PB];
+    int b0[MAXSYS], b1[MAXSYS], j[MAXSYS], sys[MAXSYS_PB];
+    int ss0[MAXSYS], ss1[MAXSYS];  // slices [ss0[g], ss1[g]) of system g
+    uint32_t mask[MAXSYS / 32];    // the set the partition was made for
+};
+
+// Recomputes block bid's partition for the systems flagged in S (inner: inside a
+// BiCGSTAB pass; else solving or to be zeroed) if that set changed.  The slices of
+// those systems are spread evenly over all nb blocks; every block computes the
+// whole partition from the same states, so all blocks agree without communicating.
+// A block holds one segment per active system in its range (finished systems in
+// between are passed over) and reduces only for those systems.  A partition in
+// which some block would hold more than MAXSYS_PB active systems is replaced by
+// the launch's static one (one segment of all the block's slices).  Run by one
+// thread; kept out of line, as it runs only when a system finishes.
+__device__ __noinline__ void partition_update(Partition& P, const SysState* S, int nsys, int inner,
+                                              int nb, int bid, const int32_t* blk_s0,
+                                              const int32_t* blk_s1, const int32_t* blk_g0,
+                                              const int32_t* blk_ng, const int32_t* sys_b0,
+                                              const int32_t* sys_b1) {
+    uint32_t m[MAXSYS / 32];
+    for (int w = 0; w < MAXSYS / 32; ++w) m[w] = 0;
+    for (int g = 0; g < nsys; ++g) {
+        const bool on = inner ? S[g].inner_active : (S[g].outer_active || S[g].zero_x);
+        if (on) m[g >> 5] |= 1u << (g & 31);
+    }
+    bool same = P.valid != 0;
+    for (int w = 0; w < MAXSYS / 32; ++w) same = same && m[w] == P.mask[w];
+    if (!same) {
+        auto on = [&](int g) { return ((m[g >> 5] >> (g & 31)) & 1u) != 0; };
+        auto len = [&](int g) -> int64_t { return on(g) ? (int64_t)(P.ss1[g] - P.ss0[g]) : 0; };
+        int64_t W = 0;
+        for (int g = 0; g < nsys; ++g) W += len(g);
+        for (int g = 0; g < nsys; ++g) { P.b0[g] = 0; P.b1[g] = 0; P.j[g] = -1; }
+        P.nv = P.nseg = P.ng = 0;
+        P.segv[0] = 0;
+        bool ok = true;
+        int gl = 0, gh = 0;
+        int64_t cl = 0, ch = 0;  // active slices of the systems before gl, gh
+        // block b takes the active slices [W b / nb, W (b + 1) / nb); a block
+        // with none (fewer active slices than blocks) holds an empty range
+        // of the active system at its position, for which it reduces a zero,
+        // so that the blocks listed for a system are exactly those that
+        // write its partials
+        for (int b = 0; b < nb && ok && W > 0; ++b) {
+            const int64_t lo = W * b / nb, hi = W * (b + 1) / nb;
+            while (lo >= cl + len(gl)) { cl += len(gl); ++gl; }
+            int last = gl;
+            if (hi > lo) {
+                while (hi - 1 >= ch + len(gh)) { ch += len(gh); ++gh; }
+                last = gh;
+            }
+            int cnt = 0;
+            for (int g = gl; g <= last; ++g) cnt += on(g) ? 1 : 0;
+            if (cnt > MAXSYS_PB) { ok = false; break; }
+            if (b == bid) {
+                int64_t cg = cl;  // active slices before system g
+                for (int g = gl; g <= last; ++g) {
+                    if (!on(g)) continue;
+                    P.j[g] = P.ng;
+                    P.sys[P.ng] = g;
+                    ++P.ng;
+                    const int64_t v0 = lo > cg ? lo : cg;
+                    const int64_t v1 = hi < cg + len(g) ? hi : cg + len(g);
+                    if (v1 > v0) {
+                        P.segs[P.nseg] = P.ss0[g] + (int)(v0 - cg);
+                        P.segv[P.nseg + 1] = P.segv[P.nseg] + (int)(v1 - v0);
+                        ++P.nseg;
+                    }
+                    cg += len(g);
+                }
+                P.nv = P.segv[P.nseg];
+            }
+            for (int g = gl; g <= last; ++g) {
+                if (!on(g)) continue;
+                if (P.b1[g] == 0) P.b0[g] = b;
+                P.b1[g] = b + 1;
+            }
+        }
+        if (!ok) {  // the static partition: every system of the block's range
+            const int g0 = blk_g0[bid];
+            P.nseg = 1;
+            P.segs[0] = blk_s0[bid];
+            P.segv[0] = 0;
+            P.segv[1] = blk_s1[bid] - blk_s0[bid];
+            P.nv = P.segv[1];
+            P.ng = blk_ng[bid];
+            for (int g = 0; g < nsys; ++g) {
+                P.b0[g] = sys_b0[g];
+                P.b1[g] = sys_b1[g];
+                P.j[g] = (g >= g0 && g < g0 + P.ng) ? g - g0 : -1;
+            }
+            for (int j = 0; j < P.ng; ++j) P.sys[j] = g0 + j;
+        }
+        for (int w = 0; w < MAXSYS / 32; ++w) P.mask[w] = m[w];
+        P.valid = 1;
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     // |r_hat . r| below this fraction of ||r_hat|| ||r|| is rounding noise in T
@@ -231,33 +337,24 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     __shared__ SysState S[MAXSYS];
     extern __shared__ double s_tile[];  // multigrid: a coarse tile and its halo, 36 x 36
     __shared__ int s_any;
-    // work partition: this block's slices are p_nv "virtual" slices in p_nseg
-    // segments, segment k being the slices p_segs[k] + [0, p_segv[k+1] - p_segv[k]);
-    // its dot-product slots j < p_ng belong to systems p_sys[j] (p_j[g] = slot of
-    // system g, -1 if none); the partials of system g come from blocks
-    // [p_b0[g], p_b1[g])
-    __shared__ int p_nv, p_nseg, p_ng, p_valid;
-    __shared__ int p_segv[MAXSYS_PB + 1], p_segs[MAXSYS_PB];
-    __shared__ int p_b0[MAXSYS], p_b1[MAXSYS], p_j[MAXSYS], p_sys[MAXSYS_PB];
-    __shared__ int p_ss0[MAXSYS], p_ss1[MAXSYS];
-    __shared__ uint32_t p_mask[MAXSYS / 32];
+    __shared__ Partition P;  // this block's share of the work
     const int bid = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned nb = gridDim.x;
     const int nsys = a.nsys;
     for (int g = threadIdx.x; g < nsys; g += KTHREADS) {
-        p_ss0[g] = a.sys_s0[g];
-        p_ss1[g] = a.sys_s1[g];
+        P.ss0[g] = a.sys_s0[g];
+        P.ss1[g] = a.sys_s1[g];
     }
-    if (threadIdx.x == 0) p_valid = 0;
+    if (threadIdx.x == 0) P.valid = 0;
     int nv = 0, ng_blk = 0, seg0 = 0;
     bool one_seg = true, p_valid_r = false;
     // slice of virtual index v; sg (the segment of the previous call) only advances,
     // as each warp's v increases; a block of one segment needs no lookup
     auto vslice = [&](int v, int& sg) {
         if (one_seg) return seg0 + v;
-        while (v >= p_segv[sg + 1]) ++sg;
-        return p_segs[sg] + (v - p_segv[sg]);
+        while (v >= P.segv[sg + 1]) ++sg;
+        return P.segs[sg] + (v - P.segv[sg]);
     };
     // The slices of the systems still being solved (outer set: solving or to be
     // zeroed; inner set: inside a BiCGSTAB pass) are spread evenly over all blocks,
@@ -272,90 +369,14 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     auto repartition = [&](int inner) {
         if (nsys == 1 && p_valid_r) return;  // one system: the partition never changes
         p_valid_r = true;
-        if (threadIdx.x == 0) {
-            uint32_t m[MAXSYS / 32];
-            for (int w = 0; w < MAXSYS / 32; ++w) m[w] = 0;
-            for (int g = 0; g < nsys; ++g) {
-                const bool on = inner ? S[g].inner_active : (S[g].outer_active || S[g].zero_x);
-                if (on) m[g >> 5] |= 1u << (g & 31);
-            }
-            bool same = p_valid != 0;
-            for (int w = 0; w < MAXSYS / 32; ++w) same = same && m[w] == p_mask[w];
-            if (!same) {
-                auto on = [&](int g) { return ((m[g >> 5] >> (g & 31)) & 1u) != 0; };
-                auto len = [&](int g) -> int64_t { return on(g) ? (int64_t)(p_ss1[g] - p_ss0[g]) : 0; };
-                int64_t W = 0;
-                for (int g = 0; g < nsys; ++g) W += len(g);
-                for (int g = 0; g < nsys; ++g) { p_b0[g] = 0; p_b1[g] = 0; p_j[g] = -1; }
-                p_nv = p_nseg = p_ng = 0;
-                p_segv[0] = 0;
-                bool ok = true;
-                int gl = 0, gh = 0;
-                int64_t cl = 0, ch = 0;  // active slices of the systems before gl, gh
-                // block b takes the active slices [W b / nb, W (b + 1) / nb); a block
-                // with none (fewer active slices than blocks) holds an empty range
-                // of the active system at its position, for which it reduces a zero,
-                // so that the blocks listed for a system are exactly those that
-                // write its partials
-                for (int b = 0; b < (int)nb && ok && W > 0; ++b) {
-                    const int64_t lo = W * b / nb, hi = W * (b + 1) / nb;
-                    while (lo >= cl + len(gl)) { cl += len(gl); ++gl; }
-                    int last = gl;
-                    if (hi > lo) {
-                        while (hi - 1 >= ch + len(gh)) { ch += len(gh); ++gh; }
-                        last = gh;
-                    }
-                    int cnt = 0;
-                    for (int g = gl; g <= last; ++g) cnt += on(g) ? 1 : 0;
-                    if (cnt > MAXSYS_PB) { ok = false; break; }
-                    if (b == (int)bid) {
-                        int64_t cg = cl;  // active slices before system g
-                        for (int g = gl; g <= last; ++g) {
-                            if (!on(g)) continue;
-                            p_j[g] = p_ng;
-                            p_sys[p_ng] = g;
-                            ++p_ng;
-                            const int64_t v0 = lo > cg ? lo : cg;
-                            const int64_t v1 = hi < cg + len(g) ? hi : cg + len(g);
-                            if (v1 > v0) {
-                                p_segs[p_nseg] = p_ss0[g] + (int)(v0 - cg);
-                                p_segv[p_nseg + 1] = p_segv[p_nseg] + (int)(v1 - v0);
-                                ++p_nseg;
-                            }
-                            cg += len(g);
-                        }
-                        p_nv = p_segv[p_nseg];
-                    }
-                    for (int g = gl; g <= last; ++g) {
-                        if (!on(g)) continue;
-                        if (p_b1[g] == 0) p_b0[g] = b;
-                        p_b1[g] = b + 1;
-                    }
-                }
-                if (!ok) {  // the static partition: every system of the block's range
-                    const int g0 = a.blk_g0[bid];
-                    p_nseg = 1;
-                    p_segs[0] = a.blk_s0[bid];
-                    p_segv[0] = 0;
-                    p_segv[1] = a.blk_s1[bid] - a.blk_s0[bid];
-                    p_nv = p_segv[1];
-                    p_ng = a.blk_ng[bid];
-                    for (int g = 0; g < nsys; ++g) {
-                        p_b0[g] = a.sys_b0[g];
-                        p_b1[g] = a.sys_b1[g];
-                        p_j[g] = (g >= g0 && g < g0 + p_ng) ? g - g0 : -1;
-                    }
-                    for (int j = 0; j < p_ng; ++j) p_sys[j] = g0 + j;
-                }
-                for (int w = 0; w < MAXSYS / 32; ++w) p_mask[w] = m[w];
-                p_valid = 1;
-            }
-        }
+        if (threadIdx.x == 0)
+            partition_update(P, S, nsys, inner, (int)nb, bid, a.blk_s0, a.blk_s1, a.blk_g0, a.blk_ng,
+                             a.sys_b0, a.sys_b1);
         __syncthreads();
-        nv = p_nv;
-        ng_blk = p_ng;
-        one_seg = p_nseg <= 1;
-        seg0 = p_nseg >= 1 ? p_segs[0] : 0;
+        nv = P.nv;
+        ng_blk = P.ng;
+        one_seg = P.nseg <= 1;
+        seg0 = P.nseg >= 1 ? P.segs[0] : 0;
     };
 
     auto clear_acc = [&]() {
@@ -383,7 +404,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
         if (g != qg) {
             flush_acc(nq);
             qg = g;
-            qj = p_j[g];
+            qj = P.j[g];
             for (int k = 0; k < nq; ++k) qacc[k] = 0.0;
         }
         for (int k = 0; k < nq; ++k) qacc[k] += q[k];
@@ -405,14 +426,14 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             int j = i / nq, k = i % nq;
             double sum = 0.0;
             for (int w = 0; w < KWARPS; ++w) sum += sacc[w][j][k];
-            __stcg(&part[((int64_t)p_sys[j] * NQ + k) * nb + bid], sum);
+            __stcg(&part[((int64_t)P.sys[j] * NQ + k) * nb + bid], sum);
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int i = warp; i < nsys * nq; i += KWARPS) {
             int g = i / nq, k = i % nq;
             const double* src = part + ((int64_t)g * NQ + k) * nb;
             double sum = 0.0;
-            for (int bb = p_b0[g] + lane; bb < p_b1[g]; bb += 32) sum += __ldcg(src + bb);
+            for (int bb = P.b0[g] + lane; bb < P.b1[g]; bb += 32) sum += __ldcg(src + bb);
             sum = wsum(sum);
             if (lane == 0) stot[g][k] = sum;
         }
