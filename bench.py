@@ -457,10 +457,9 @@ def main():
             "roofline_other": roof_other,
             "e2e": {"value": N * k2 * ws / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 4 * 8 * N},
-            # per step: rhs, Helmholtz, divergence, Poisson, stats, projection; several
-            # geometries add the Poisson re-partition; the learned guess adds scales,
-            # scatter, six convolutions and gather
-            "gpu_launches": (6 + (1 if len(nss) > 1 else 0) + (9 if ws_info else 0)) * args.steps,
+            # per step: rhs, Helmholtz, divergence, Poisson, stats, projection; the
+            # learned guess adds scales, scatter, six convolutions and gather
+            "gpu_launches": (6 + (9 if ws_info else 0)) * args.steps,
             "clocks": clk}
     if cpu is not None:
         line["cpu_baseline"] = cpu

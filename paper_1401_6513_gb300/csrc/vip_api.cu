@@ -84,9 +84,6 @@ vip_status do_step(vip_ctx* c, cudaStream_t s) {
     VIP_CUDA(cudaEventRecord(c->ev[4], s));
     k_stats<<<1, 32, 0, s>>>(c->plan_pois.out_iters, c->plan_pois.out_outer, c->plan_pois.nsys,
                              c->plan_helm.out_iters, c->plan_helm.nsys, c->d_stats, c->d_giters);
-    // several geometries: give the next step's Poisson solve a block partition
-    // weighted by this step's iteration counts
-    if ((st = krylov_replan(c, c->plan_pois, s)) != VIP_OK) return st;
     launch_project(c, s);
     VIP_CUDA(cudaGetLastError());
     VIP_CUDA(cudaEventRecord(c->ev[5], s));

@@ -195,7 +195,6 @@ vip_status krylov_plan(vip_ctx* c, KrylovPlan& plan, const Sell& A,
                        const std::vector<int64_t>& sys_row0, const std::vector<int64_t>& sys_rows);
 // Re-partition the plan's slices over its blocks in proportion to rows x the
 // iterations each system needed in its last solve (device side, stream-ordered).
-vip_status krylov_replan(vip_ctx* c, const KrylovPlan& plan, cudaStream_t s);
 vip_status krylov_solve(vip_ctx* c, const KrylovPlan& plan, const Sell& A, const double* b,
                         double* x, int precision, double rtol, int32_t max_iters,
                         double inner_rtol, const Multigrid* mg = nullptr);

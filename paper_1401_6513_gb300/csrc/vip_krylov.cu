@@ -1001,73 +1001,6 @@ vip_status krylov_plan(vip_ctx* c, KrylovPlan& P, const Sell& A, const std::vect
     return VIP_OK;
 }
 
-// One thread re-partitions the slices (systems are contiguous runs of slices, in
-// order) into nb contiguous block ranges of nearly equal weight, a slice of system g
-// weighing max(iters[g], 1): a system that needs many iterations gets more blocks.
-// Every block keeps at least one slice and at most MAXSYS_PB systems; a partition
-// that would break the cap is not written (the previous one stays).
-__global__ void k_replan(int nsys, int nb, const int32_t* __restrict__ sys_s0,
-                         const int32_t* __restrict__ sys_s1, const int32_t* __restrict__ iters,
-                         int32_t* __restrict__ blk_s0, int32_t* __restrict__ blk_s1,
-                         int32_t* __restrict__ blk_g0, int32_t* __restrict__ blk_ng,
-                         int32_t* __restrict__ sys_b0, int32_t* __restrict__ sys_b1) {
-    __shared__ int32_t bnd[1025];
-    __shared__ int32_t g0[1024], ng[1024];
-    if (threadIdx.x != 0 || nb > 1024) return;
-    const int32_t total = sys_s1[nsys - 1];
-    double W = 0.0;
-    for (int g = 0; g < nsys; ++g) W += (double)(sys_s1[g] - sys_s0[g]) * (double)max(iters[g], 1);
-    // boundaries: first slice whose preceding weight reaches b W / nb
-    bnd[0] = 0;
-    bnd[nb] = total;
-    int g = 0;
-    double before = 0.0;  // weight of the slices of systems < g
-    for (int b = 1; b < nb; ++b) {
-        const double T = W * (double)b / (double)nb;
-        while (g < nsys - 1 && before + (double)(sys_s1[g] - sys_s0[g]) * max(iters[g], 1) < T) {
-            before += (double)(sys_s1[g] - sys_s0[g]) * max(iters[g], 1);
-            ++g;
-        }
-        const double w = (double)max(iters[g], 1);
-        int32_t s = sys_s0[g] + (int32_t)ceil((T - before) / w);
-        s = max(s, bnd[b - 1] + 1);
-        s = min(s, total - (nb - b));
-        bnd[b] = s;
-    }
-    // system ranges of the blocks; check the cap
-    int gs = 0;
-    for (int b = 0; b < nb; ++b) {
-        while (sys_s1[gs] <= bnd[b]) ++gs;
-        int ge = gs;
-        while (sys_s1[ge] < bnd[b + 1]) ++ge;
-        if (ge - gs + 1 > MAXSYS_PB) return;
-        g0[b] = gs;
-        ng[b] = ge - gs + 1;
-    }
-    for (int q = 0; q < nsys; ++q) {
-        sys_b0[q] = 1 << 30;
-        sys_b1[q] = -1;
-    }
-    for (int b = 0; b < nb; ++b) {
-        blk_s0[b] = bnd[b];
-        blk_s1[b] = bnd[b + 1];
-        blk_g0[b] = g0[b];
-        blk_ng[b] = ng[b];
-        for (int q = g0[b]; q < g0[b] + ng[b]; ++q) {
-            sys_b0[q] = min(sys_b0[q], b);
-            sys_b1[q] = max(sys_b1[q], b + 1);
-        }
-    }
-}
-
-vip_status krylov_replan(vip_ctx* c, const KrylovPlan& P, cudaStream_t s) {
-    if (P.nsys < 2) return VIP_OK;
-    k_replan<<<1, 32, 0, s>>>(P.nsys, P.nblocks, P.sys_s0, P.sys_s1, P.out_iters, P.blk_s0, P.blk_s1,
-                              P.blk_g0, P.blk_ng, P.sys_b0, P.sys_b1);
-    VIP_CUDA(cudaGetLastError());
-    return VIP_OK;
-}
-
 template <class T>
 static MgDev<T> mg_view(const Multigrid& M) {
     MgDev<T> d;
