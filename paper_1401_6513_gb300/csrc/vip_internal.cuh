@@ -82,6 +82,8 @@ struct KrylovPlan {
     int64_t nslices = 0;
     // device arrays
     int32_t* slice_sys = nullptr;   // [nslices] system of each slice
+    // static partition (equal slice counts), used by the launch only when its own
+    // partition of the active systems would give a block too many systems
     int32_t* blk_s0 = nullptr;      // [nblocks] slice range of a block
     int32_t* blk_s1 = nullptr;
     int32_t* blk_g0 = nullptr;      // [nblocks] first system of the block
