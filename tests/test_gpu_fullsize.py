@@ -35,16 +35,21 @@ def full(vip):
 
 
 def sample_nodes(ns, per_kind=40, seed=2014):
+    # the node set is ordered by lattice row, so the body's surface nodes are found
+    # by kind and position: wall nodes near the origin (the channel's walls are at
+    # |x| = 8, 24 and |y| = 8)
     rng = np.random.default_rng(seed)
     r = np.hypot(ns.x, ns.y)
-    nsurf = ns.meta["surface_nodes"]
-    lattice = np.arange(ns.n - nsurf)
+    idx = np.arange(ns.n)
+    interior = ns.kind == vo.KIND_INTERIOR
+    surface = (ns.kind == vo.KIND_WALL) & (r < 2.0)
     groups = {
-        "interior": lattice[(ns.kind[lattice] == vo.KIND_INTERIOR) & (r[lattice] > 2.0)],
-        "near body": lattice[(ns.kind[lattice] == vo.KIND_INTERIOR) & (r[lattice] < 1.2)],
-        "walls": lattice[ns.kind[lattice] != vo.KIND_INTERIOR],
-        "surface": np.arange(ns.n - nsurf, ns.n),
+        "interior": idx[interior & (r > 2.0)],
+        "near body": idx[interior & (r < 1.2)],
+        "walls": idx[~interior & ~surface],
+        "surface": idx[surface],
     }
+    assert groups["surface"].size == ns.meta["surface_nodes"]
     picks = {k: rng.choice(v, size=min(per_kind, v.size), replace=False) for k, v in groups.items()}
     for k, v in groups.items():
         assert v.size > 0, k
