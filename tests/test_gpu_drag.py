@@ -1,65 +1,80 @@
-"""Steady flow past the circular cylinder at Re = 40 (Sec. 5, flow past a circular
-cylinder; the paper's table of cylinder results prints C_D = 1.536 at Re = 40), run
-on the GPU through the C ABI and post-processed on the host:
+"""Flow past the circular cylinder (Sec. 5, flow past a circular cylinder: steady
+and unsteady), run on the GPU through the C ABI and post-processed on the host
+(tests/forces.py: pressure and viscous traction summed over the body's surface
+nodes), against the paper's table of cylinder results:
 
-  C_D = 2 F_x / (rho U^2 D),  F = sum over the body's surface nodes of t ds,
-  t = -p n + (1/Re) (grad u + grad u^T) n,  n the unit normal out of the body,
+  * Re = 40, steady: C_D = 1.536, zero lift.  h = 1/16, impulsive start, run to
+    t = 60 (C_D steady to 4 digits by t = 50).
+  * Re = 100, periodic shedding: mean C_D = 1.328, lift amplitude C'_L = 0.31,
+    Strouhal number St = 0.164.  h = 1/16, a small v bump off the axis in the
+    near wake to start the shedding (the lift amplitude is steady to 3 digits from
+    t = 70 on), run to t = 120; the last 40 time units (about 6.6 periods) sampled
+    every 0.094.
 
-which on a no-slip wall equals the paper's traction -p n + nu du/dn.  Velocity
-gradients come from the GPU's MLS derivative tables (D10, D01), p from the state,
-ds = perimeter / (number of surface nodes).
-
-Setup: inflow u = 1, traction-free outlet, slip walls, impulsive start, h = 1/16,
-run to t = 60 (C_D steady to 4 digits by t = 50).  The channel is [-16,48]x[-16,16]
+Inflow u = 1, traction-free outlet, slip walls.  The channel is [-16,48]x[-16,16]
 (blockage D/H = 1/32): on the 16-wide channel of the bench workloads the walls
-raise C_D by 6 % (1.639), while halving h changes it by 1 % (1.655 at h = 1/32).
-Tolerance 3 % of the paper's value (its domain is given only in a figure); the
-symmetric flow has zero lift.
+raise the steady C_D by 6 % (1.639), while halving h changes it by 1 % (1.655 at
+h = 1/32).  The paper gives its domain only in a figure, so the bars are 3 % for
+C_D at Re = 40 and St, 6 % for the mean C_D and 15 % for C'_L at Re = 100.
 """
 import numpy as np
 import pytest
-import scipy.sparse as sp
 
 import workloads as w
-from oracle import vip_oracle as vo
+from forces import ForceProbe
 
 pytestmark = pytest.mark.gpu
 
 CD_PAPER_RE40 = 1.536
-
-
-def drag_lift(ctx, ns):
-    def csr(which):
-        ptr, col, val = ctx.vip_get_stencil(which)
-        return sp.csr_matrix((val, col, ptr), shape=(ns.n, ns.n))
-
-    # nodes are ordered by lattice row: the body's surface nodes are the wall nodes
-    # near the origin (the channel's own walls are far away)
-    r = np.hypot(ns.x, ns.y)
-    s = np.nonzero((ns.kind == vo.KIND_WALL) & (r < 2.0))[0]
-    assert s.size == ns.meta["surface_nodes"]
-    s = s[np.argsort(np.arctan2(ns.y[s], ns.x[s]))]
-    xs, ys = np.append(ns.x[s], ns.x[s][0]), np.append(ns.y[s], ns.y[s][0])
-    ds = np.sum(np.hypot(np.diff(xs), np.diff(ys))) / s.size
-    nbx, nby = -ns.nx[s], -ns.ny[s]  # the node set's normals point into the body
-    u, v, p, _ = ctx.vip_get_state()
-    D10, D01 = csr("D10"), csr("D01")
-    ux, uy, vx, vy = (D10 @ u)[s], (D01 @ u)[s], (D10 @ v)[s], (D01 @ v)[s]
-    tx = -p[s] * nbx + (2 * ux * nbx + (uy + vx) * nby) / ns.Re
-    ty = -p[s] * nby + ((uy + vx) * nbx + 2 * vy * nby) / ns.Re
-    return 2 * np.sum(tx) * ds, 2 * np.sum(ty) * ds
+CD_PAPER_RE100, CL_AMP_PAPER_RE100, ST_PAPER_RE100 = 1.328, 0.31, 0.164
 
 
 def test_cylinder_drag_re40(vip):
     ns = w.channel_body(1 / 16, ("circle", 0.5), Re=40.0, xlim=(-16, 48), ylim=(-16, 16))
     ctx = vip.solver_for(ns, precision=vip.VIP_PREC_FP64, rtol=1e-8)
+    probe = ForceProbe(ctx, ns)
     ctx.vip_step(int(round(50.0 / ns.dt)))
-    cd50, _ = drag_lift(ctx, ns)
+    cd50, _ = probe.coefficients()
     ctx.vip_step(int(round(10.0 / ns.dt)))
     st = ctx.vip_get_stats()
     assert st.status == 0
-    cd, cl = drag_lift(ctx, ns)
+    cd, cl = probe.coefficients()
     ctx.close()
     assert abs(cd - cd50) <= 1e-3 * cd, (cd50, cd)  # steady
     assert abs(cd - CD_PAPER_RE40) <= 0.03 * CD_PAPER_RE40, cd
     assert abs(cl) <= 1e-6, cl
+
+
+def strouhal(t, cl):
+    """Dominant frequency of a uniformly sampled signal: Hann-windowed spectrum, the
+    peak refined by a parabola through the log power of its three bins."""
+    x = (cl - cl.mean()) * np.hanning(cl.size)
+    P = np.abs(np.fft.rfft(x)) ** 2
+    i = int(np.argmax(P[1:])) + 1
+    a, b, c = np.log(P[i - 1]), np.log(P[i]), np.log(P[i + 1])
+    return (i + 0.5 * (a - c) / (a - 2 * b + c)) / (cl.size * (t[1] - t[0]))
+
+
+def test_cylinder_shedding_re100(vip):
+    ns = w.channel_body(1 / 16, ("circle", 0.5), Re=100.0, xlim=(-16, 48), ylim=(-16, 16))
+    ctx = vip.solver_for(ns, precision=vip.VIP_PREC_FP64, rtol=1e-8)
+    bump = 0.1 * np.exp(-((ns.x - 1.5) ** 2 + (ns.y - 0.3) ** 2) / 0.25) * (ns.kind == 0)
+    ctx.vip_set_state(ns.u0, ns.v0 + bump, ns.p0)
+    probe = ForceProbe(ctx, ns)
+    ctx.vip_step(int(round(80.0 / ns.dt)))
+    k = int(round(0.1 / ns.dt))
+    t, cd, cl = [], [], []
+    for i in range(int(round(40.0 / (k * ns.dt)))):
+        ctx.vip_step(k)
+        c = probe.coefficients()
+        t.append((i + 1) * k * ns.dt)
+        cd.append(c[0])
+        cl.append(c[1])
+    assert ctx.vip_get_stats().status == 0
+    ctx.close()
+    t, cd, cl = map(np.asarray, (t, cd, cl))
+    st = strouhal(t, cl)
+    amp = 0.5 * (cl.max() - cl.min())
+    assert abs(st - ST_PAPER_RE100) <= 0.03 * ST_PAPER_RE100, st
+    assert abs(cd.mean() - CD_PAPER_RE100) <= 0.06 * CD_PAPER_RE100, cd.mean()
+    assert abs(amp - CL_AMP_PAPER_RE100) <= 0.15 * CL_AMP_PAPER_RE100, amp
