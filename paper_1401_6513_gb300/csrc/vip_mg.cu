@@ -193,7 +193,8 @@ vip_status mg_set_params(vip_ctx* c, Multigrid& M, float omega, float corr) {
 }
 
 // Dense inverse of one geometry's coarsest operator, A (m x m, row-major), by
-// Gauss-Jordan elimination with partial pivoting in FP64 on the host (setup only).
+// Gauss-Jordan elimination with partial pivoting in FP64 on the host (setup only;
+// the row updates of each pivot step run on the host's cores with OpenMP).
 // Cells without a row (empty cells) are decoupled: their unknown stays 0.  The
 // result is stored row-major, inv[i * m + j] = (A^{-1})_{ij}.
 static void coarse_inverse(std::vector<double>& A, int m, double* inv) {
@@ -218,9 +219,11 @@ static void coarse_inverse(std::vector<double>& A, int m, double* inv) {
         const double di = std::fabs(d) > 1e-300 ? 1.0 / d : 0.0;
         double* rk = &T[(size_t)k * w];
         for (int j = 0; j < w; ++j) rk[j] *= di;
+        double* t0 = T.data();
+#pragma omp parallel for schedule(static) if (m >= 256)
         for (int i = 0; i < m; ++i) {
             if (i == k) continue;
-            double* ri = &T[(size_t)i * w];
+            double* ri = t0 + (size_t)i * w;
             const double f = ri[k];
             if (f == 0.0) continue;
             for (int j = k; j < w; ++j) ri[j] -= f * rk[j];

@@ -11,7 +11,7 @@ constexpr int MG_MAXLEV = 16;
 // inverse).  Open domains take a larger exact coarse solve (fewer iterations); a
 // closed domain's pinned constant mode makes large coarse operators nearly singular,
 // so contexts with a closed geometry keep it small.
-constexpr int MG_COARSEST_OPEN = 576;
+constexpr int MG_COARSEST_OPEN = 2200;
 constexpr int MG_COARSEST_CLOSED = 64;
 
 struct MgGeom {                   // background lattice of one geometry
