@@ -234,7 +234,7 @@ def run_reference(args, rank, ws):
 # divided by its iterations); every iteration streams the same operator and vectors,
 # so a launch's traffic scales with its iterations (profiles/k_bicgstab_poisson_bumpy_h64.md).
 # Re-measured whenever the kernel changes.
-TRAFFIC_PER_ITER = {("bumpy_h64", "fp64"): 59.183555328e9 / 73.0}
+TRAFFIC_PER_ITER = {("bumpy_h64", "fp64"): 57.911748608e9 / 62.0}
 
 # FP64 operations per clock per SM of GB300 (two FP64 FMAs), for the ALU roofline;
 # 152 SMs at 2070 MHz give 1.26 TFLOP/s, the part's nominal FP64 rate.
@@ -264,9 +264,16 @@ def poisson_flops_per_iter(nnz, rows):
     vector updates and dot products (p 6, two V-cycles' fine level 8 each, v 4, s 4,
     t 6, x/r 10) and 32 on the coarse levels (48 per level-1 cell per V-cycle: 3 x 3
     stencils down and up, smoothing, restriction, correction; a quarter of a cell
-    per row, 4/3 over all levels).  The dense coarsest solve (under 0.5 % of the
-    total on the benchmarked workloads) is not counted."""
+    per row, 4/3 over all levels).  The dense coarsest solves are added by the
+    caller (coarsest_per_iter)."""
     return 12 * nnz + 78 * rows
+
+
+def coarsest_per_iter(entries):
+    """Bytes and FP64 operations of the dense coarsest solves of one inner
+    iteration: each of the two V-cycles reads every entry of the coarsest inverses
+    once (FP64) and multiplies it into one sum (an FMA)."""
+    return 2 * 8 * entries, 2 * 2 * entries
 
 
 def poisson_bytes_per_pass(nnz, rows, tb):
@@ -366,6 +373,7 @@ def main():
     rows_p = int(ptr.size - 1)
     tb = 4 if prec == vip.VIP_PREC_MIXED else 8
     lay = ctx.vip_operator_layout("POISSON")
+    _, cinv_entries = ctx.vip_multigrid_info()
     # entries one operator pass streams, per real entry (exact for one geometry; a
     # batch's geometries are assigned the table's ratio)
     stream_ratio = (lay["other_entries"] + lay["uniform_entries"]) / max(nnz_p, 1)
@@ -383,6 +391,12 @@ def main():
         bytes_p += int(g_iters[gi]) * poisson_bytes_per_iter(nnz_g * stream_ratio, rows_g, tb)
         flops_p += int(g_iters[gi]) * poisson_flops_per_iter(nnz_g, rows_g)
         off += g.n
+    # dense coarsest solves: every geometry's inverse is read while the launch
+    # iterates (an overcount for a batch whose systems finish early; there the
+    # inverses are small)
+    cb, cf = coarsest_per_iter(cinv_entries)
+    bytes_p += it_p * cb
+    flops_p += it_p * cf
     bytes_p += out_p * poisson_bytes_per_pass(nnz_p, rows_p, tb)
     flops_p += out_p * (2 * nnz_p + 8 * rows_p)  # refinement: residual, 3 dots, x update
     t_pois = prof["poisson"] / 1e3

@@ -217,6 +217,13 @@ vip_status vip_stencil_info(vip_ctx* ctx, int which, int64_t* nrows, int64_t* nn
 vip_status vip_operator_layout(vip_ctx* ctx, int which, int64_t* slices, int64_t* uniform_slices,
                                int64_t* uniform_entries, int64_t* other_entries);
 
+/* Size of the Poisson preconditioner's hierarchy (not in the paper; see
+ * vip_set_multigrid): `levels` coarse levels, the last solved exactly by a dense
+ * inverse per geometry; `coarsest_entries` = sum over geometries of m_g^2, m_g the
+ * geometry's cells on that level (each V-cycle reads these FP64 entries once).
+ * Zeros without a multigrid.  Any output pointer may be NULL.  After vip_build. */
+vip_status vip_multigrid_info(vip_ctx* ctx, int32_t* levels, int64_t* coarsest_entries);
+
 /* Export table `which` as CSR: row_ptr[nrows+1], col[nnz], val[nnz], columns
  * ascending within a row.  Host or device pointers.  Synchronises. */
 vip_status vip_get_stencil(vip_ctx* ctx, int which, int64_t* row_ptr, int32_t* col,

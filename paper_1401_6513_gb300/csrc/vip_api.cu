@@ -698,6 +698,15 @@ vip_status vip_operator_layout(vip_ctx* c, int which, int64_t* slices, int64_t* 
     return VIP_OK;
 }
 
+vip_status vip_multigrid_info(vip_ctx* c, int32_t* levels, int64_t* coarsest_entries) {
+    if (!c) return VIP_ERR_ARG;
+    if (!c->built) return fail(c, VIP_ERR_ARG, "vip_multigrid_info before vip_build");
+    const bool on = c->use_mg && c->mg.built;
+    if (levels) *levels = on ? c->mg.nlev : 0;
+    if (coarsest_entries) *coarsest_entries = on ? c->mg.cinv_entries : 0;
+    return VIP_OK;
+}
+
 vip_status vip_get_stencil(vip_ctx* c, int which, int64_t* row_ptr, int32_t* col, double* val) {
     if (!c) return VIP_ERR_ARG;
     if (!c->built) return fail(c, VIP_ERR_ARG, "vip_get_stencil before vip_build");

@@ -454,6 +454,7 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
                 }
             coarse_inverse(Ad, m, hinv.data() + ioff[g]);
         }
+        M.cinv_entries = tot;
         VIP_CUDA(dalloc(c, &M.cinv, tot));
         VIP_CUDA(dalloc(c, &M.cinv_off, G));
         VIP_CUDA(cudaMemcpyAsync(M.cinv, hinv.data(), tot * 8, cudaMemcpyHostToDevice, st));

@@ -69,6 +69,7 @@ struct Multigrid {
     void* fx = nullptr;           // [R] fine smoothing scratch
     double* cinv = nullptr;       // dense inverse of each geometry's coarsest operator (row-major)
     int64_t* cinv_off = nullptr;  // [G] offset of geometry g's block in cinv
+    int64_t cinv_entries = 0;     // entries of all geometries' coarsest inverses
     int ngeom = 0;
     float omega = 1.0f;           // smoother damping (vip_set_multigrid / vip_autotune)
     float corr = 1.5f;            // scaling of the coarse-grid correction

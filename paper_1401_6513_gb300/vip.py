@@ -34,7 +34,8 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_get_stencil", "vip_apply", "vip_convection", "vip_solve", "vip_load_state",
            "vip_set_profiling", "vip_get_profile", "vip_ws_collect", "vip_ws_train",
            "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static",
-           "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout"]
+           "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout",
+           "vip_multigrid_info"]
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -117,6 +118,7 @@ def lib(path: str | Path | None = None):
         "vip_get_geometry_iters": ([vp, vp], C.c_int),
         "vip_operator_layout": ([vp, C.c_int, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64),
                                  C.POINTER(i64)], C.c_int),
+        "vip_multigrid_info": ([vp, C.POINTER(i32), C.POINTER(i64)], C.c_int),
         "vip_autotune": ([vp, C.POINTER(C.c_float), i32, C.POINTER(C.c_float), i32,
                           C.POINTER(TuneResult)], C.c_int),
     }
@@ -297,6 +299,13 @@ class Context:
         self._check(self.L.vip_operator_layout(self.h, w, *(C.byref(x) for x in v)))
         return dict(zip(("slices", "uniform_slices", "uniform_entries", "other_entries"),
                         (x.value for x in v)))
+
+    def vip_multigrid_info(self):
+        """(coarse levels, entries of the dense coarsest inverses) of the Poisson
+        preconditioner."""
+        lv, ce = C.c_int32(), C.c_int64()
+        self._check(self.L.vip_multigrid_info(self.h, C.byref(lv), C.byref(ce)))
+        return lv.value, ce.value
 
     def vip_get_stencil(self, which):
         """Return (row_ptr, col, val) of a table as numpy arrays."""

@@ -84,6 +84,8 @@ def test_full_size_poisson_solve_residual(full, vip):
     P = sp.csr_matrix((val, col, ptr), shape=(n, n))
     rng = np.random.default_rng(5)
     b = np.where(ns.kind == vo.KIND_INTERIOR, rng.standard_normal(n), 0.0)
+    # hierarchy of the 2049 x 1025 lattice: cells 1025 x 513, ..., 65 x 33 = 2145 <= 2200
+    assert ctx.vip_multigrid_info() == (5, 2145 ** 2)
     x, it, rr = ctx.vip_solve("POISSON", b, np.zeros(n), precision=vip.VIP_PREC_FP64, rtol=1e-8,
                               max_iters=20000)
     assert 0 < it < 1000 and rr <= 1e-8, (it, rr)
