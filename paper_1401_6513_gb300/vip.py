@@ -235,7 +235,7 @@ class Context:
     def vip_set_multigrid(self, omega=1.0, corr=1.5):
         self._check(self.L.vip_set_multigrid(self.h, float(omega), float(corr)))
 
-    def vip_autotune(self, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.7, 1.9, 2.1)) -> TuneResult:
+    def vip_autotune(self, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.6, 1.7, 1.8, 1.9, 2.1)) -> TuneResult:
         """Time the last step's pressure-increment solve for every (omega, corr) pair
         and apply the fastest; returns the report."""
         om = (C.c_float * len(omegas))(*omegas)
@@ -369,7 +369,7 @@ def geometry_signature(nodesets) -> str:
     return "|".join(parts) + "|" + hsh.hexdigest()[:16]
 
 
-def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.7, 1.9, 2.1),
+def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.6, 1.7, 1.8, 1.9, 2.1),
              refine=3, refine_steps=3):
     """Pick the multigrid parameters of a context built from `nodesets`: from the JSON
     file `cache` when it has this geometry signature, else in two stages, then store
