@@ -1,0 +1,104 @@
+"""Host logic of the binding's two-stage multigrid autotuner (vip.autotune), on a
+fake context (no GPU): stage 1 is vip_autotune's table of zero-guess solves; stage
+2 re-runs only the `refine` fastest converged pairs for `refine_steps` steps from
+the initial fields and keeps the one with the fewest Poisson iterations in the
+warm-started steps; the state is reset afterwards and the choice is cached per
+geometry signature."""
+import numpy as np
+
+import workloads as w
+from paper_1401_6513_gb300 import vip
+
+
+class FakeStats:
+    def __init__(self, total):
+        self.total_poisson_iters = total
+
+
+class FakeCtx:
+    """Zero-guess solve times and per-step iteration counts per (omega, corr)."""
+
+    def __init__(self, ms, step_iters):
+        self.ms, self.step_iters = ms, step_iters
+        self.params = (1.0, 1.5)
+        self.total = 0
+        self.calls = []
+        self.resets = 0
+
+    def vip_step(self, n):
+        self.calls.append(("step", n, self.params))
+        self.total += n * self.step_iters[self.params]
+
+    def vip_get_stats(self):
+        return FakeStats(self.total)
+
+    def vip_set_multigrid(self, omega, corr):
+        self.params = (round(omega, 4), round(corr, 4))
+
+    def vip_set_state(self, u, v, p):
+        self.resets += 1
+
+    def vip_autotune(self, omegas, corrs):
+        pairs = [(o, c) for o in omegas for c in corrs]
+        ms = self.ms
+
+        class Result:
+            def as_dict(self_inner):
+                best = min((k for k in pairs if ms[k] >= 0), key=lambda k: ms[k])
+                return {"omega": best[0], "corr": best[1],
+                        "candidates": [{"omega": o, "corr": c, "iters": 10, "ms": ms[(o, c)]}
+                                       for o, c in pairs]}
+        return Result()
+
+
+def make(ms_table, iters_table):
+    return FakeCtx(ms_table, iters_table)
+
+
+def test_refine_picks_fewest_warm_started_iterations(tmp_path):
+    ns = w.cavity(8, Re=100.0)
+    omegas, corrs = (0.9, 1.0), (1.5, 1.7, 1.9)
+    # zero-guess times: (0.9, 1.7) fastest, then (1.0, 1.7), then (1.0, 1.9); (0.9, 1.9)
+    # did not converge (ms < 0)
+    ms = {(0.9, 1.5): 9.0, (0.9, 1.7): 5.0, (0.9, 1.9): -1.0,
+          (1.0, 1.5): 8.0, (1.0, 1.7): 5.5, (1.0, 1.9): 6.0}
+    # warm-started steps: (1.0, 1.7) needs the fewest iterations; (1.0, 1.5) would be
+    # better still but is not among the three fastest
+    iters = {(0.9, 1.5): 40, (0.9, 1.7): 70, (0.9, 1.9): 10,
+             (1.0, 1.5): 30, (1.0, 1.7): 60, (1.0, 1.9): 65}
+    ctx = make(ms, iters)
+    cache = tmp_path / "tune.json"
+    entry = vip.autotune(ctx, [ns], cache=cache, omegas=omegas, corrs=corrs, refine=3, refine_steps=3)
+    assert (entry["omega"], entry["corr"]) == (1.0, 1.7)
+    assert ctx.params == (1.0, 1.7)
+    refined = [c for c in entry["candidates"] if "step_iters" in c]
+    assert sorted((c["omega"], c["corr"]) for c in refined) == [(0.9, 1.7), (1.0, 1.7), (1.0, 1.9)]
+    # each re-run: one step from the initial fields, then two scored steps
+    assert {c["step_iters"] for c in refined} == {2 * 70, 2 * 60, 2 * 65}
+    assert ctx.resets == 3 + 1  # before each re-run and once at the end
+    assert not entry["cached"] and entry["refined_on_steps"] == 2
+    # a second context with the same geometry takes the cached choice without tuning
+    ctx2 = make(ms, iters)
+    again = vip.autotune(ctx2, [ns], cache=cache, omegas=omegas, corrs=corrs)
+    assert again["cached"] and (again["omega"], again["corr"]) == (1.0, 1.7)
+    assert ctx2.calls == [] and ctx2.params == (1.0, 1.7)
+
+
+def test_single_converged_pair_skips_refinement():
+    ns = w.cavity(8, Re=100.0)
+    ms = {(1.0, 1.5): 4.0, (1.0, 1.7): -1.0}
+    ctx = make(ms, {(1.0, 1.5): 50, (1.0, 1.7): 5})
+    entry = vip.autotune(ctx, [ns], omegas=(1.0,), corrs=(1.5, 1.7))
+    assert (entry["omega"], entry["corr"]) == (1.0, 1.5)
+    assert "refined_on_steps" not in entry
+    assert [c for c in ctx.calls if c[0] == "step"] == [("step", 1, (1.0, 1.5))]
+
+
+def test_geometry_signature_tracks_nodes():
+    a, b = w.cavity(8, Re=100.0), w.cavity(9, Re=100.0)
+    assert vip.geometry_signature([a]) == vip.geometry_signature([w.cavity(8, Re=400.0)])
+    assert vip.geometry_signature([a]) != vip.geometry_signature([b])
+    moved = w.cavity(8, Re=100.0)
+    moved.x[3] += 1e-9
+    assert vip.geometry_signature([moved]) != vip.geometry_signature([a])
+    assert np.all(a.x == w.cavity(8, Re=100.0).x)
