@@ -650,19 +650,28 @@ __global__ void k_sell_compact(Sell A, const int64_t* __restrict__ usize,
     if (lane == 0) A.ucptr[s] = o;
 }
 
+// device scratch freed on every return path
+struct DeviceScratch {
+    void* p = nullptr;
+    ~DeviceScratch() {
+        if (p) cudaFree(p);
+    }
+};
+
 static vip_status sell_uniform(vip_ctx* c, Sell& S) {
     cudaStream_t st = c->stream;
-    int64_t* usize = nullptr;
-    int64_t* uoff = nullptr;
-    VIP_CUDA(cudaMalloc(&usize, S.nslices * sizeof(int64_t)));
-    VIP_CUDA(cudaMalloc(&uoff, (S.nslices + 1) * sizeof(int64_t)));
+    DeviceScratch s_usize, s_uoff;
+    VIP_CUDA(cudaMalloc(&s_usize.p, S.nslices * sizeof(int64_t)));
+    VIP_CUDA(cudaMalloc(&s_uoff.p, (S.nslices + 1) * sizeof(int64_t)));
+    int64_t* usize = static_cast<int64_t*>(s_usize.p);
+    int64_t* uoff = static_cast<int64_t*>(s_uoff.p);
     const int TB = 256;
     const unsigned grid = (unsigned)((S.nslices * 32 + TB - 1) / TB);
     k_sell_uniform<<<grid, TB, 0, st>>>(S, usize);
     VIP_CUDA(cudaGetLastError());
     VIP_CUDA(scan_excl<int64_t>(usize, uoff, S.nslices, st));
     VIP_CUDA(cudaMemcpyAsync(&S.nuentries, uoff + S.nslices, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    std::vector<int64_t> hs(S.nslices), hp(S.nslices + 1);
+    std::vector<int64_t> hs(S.nslices);
     std::vector<int32_t> hw(S.nslices);
     VIP_CUDA(cudaMemcpyAsync(hs.data(), usize, S.nslices * 8, cudaMemcpyDeviceToHost, st));
     VIP_CUDA(cudaMemcpyAsync(hw.data(), S.width, S.nslices * 4, cudaMemcpyDeviceToHost, st));
@@ -680,8 +689,6 @@ static vip_status sell_uniform(vip_ctx* c, Sell& S) {
     k_sell_compact<<<grid, TB, 0, st>>>(S, usize, uoff);
     VIP_CUDA(cudaGetLastError());
     VIP_CUDA(cudaStreamSynchronize(st));
-    cudaFree(usize);
-    cudaFree(uoff);
     return VIP_OK;
 }
 
