@@ -209,10 +209,11 @@ vip_status vip_stencil_info(vip_ctx* ctx, int which, int64_t* nrows, int64_t* nn
 /* Device storage of a Krylov operator (the Helmholtz operator of Eq. 12,
  * `which` = VIP_OP_HELM_U or VIP_OP_HELM_V, which share one table, or the Poisson
  * operator of Eq. 13, VIP_OP_POISSON; the storage itself is not in the paper), as
- * each operator application reads it: `slices` slices of 32 rows; `uniform_slices` of them hold the same stencil
- * in all 32 rows (the same value, bit for bit, at each entry, and columns at the
- * same offsets from the row or at the same column) and are read as one stencil of
- * `uniform_entries` entries in total; the other slices are read as
+ * each operator application reads it: `slices` slices of 32 rows;
+ * `uniform_slices` of them hold the same stencil in all 32 rows (the same value,
+ * bit for bit, at each entry, and columns at the same offsets from the row or at
+ * the same column) and are read as one stencil of `uniform_entries` entries in
+ * total; the other slices are read as
  * `other_entries` stored entries (8-byte value + 4-byte column each, padding
  * included).  Any output pointer may be NULL.  After vip_build. */
 vip_status vip_operator_layout(vip_ctx* ctx, int which, int64_t* slices, int64_t* uniform_slices,
