@@ -131,7 +131,7 @@ __global__ void k_mg_galerkin(int64_t nc, const int64_t* __restrict__ child,  //
 }
 
 // sliced copy of the stencils ([n/32][25][32]), the l1-Jacobi scaling
-// sign(a_cc) / sum_o |a_co| of the smoother (0 for empty and padding cells), and per
+// -1 / sum_o |a_co| of the smoother (0 for empty and padding cells), and per
 // slice of 32 cells whether any stencil has a nonzero outside the central 3 x 3
 // offsets.  Away from boundaries a 2 x 2 aggregate of the 13-point fine stencil, and
 // of a 3 x 3 coarse stencil, couples only to the adjacent cells, so most slices
@@ -150,8 +150,13 @@ __global__ void k_mg_finish(int64_t n, const double* __restrict__ coef, double* 
         const int dy = o / 5 - 2, dx = o % 5 - 2;
         if ((dx < -1 || dx > 1 || dy < -1 || dy > 1) && a != 0.0) outer = true;
     }
-    double d = coef[(int64_t)12 * n + c];
-    dinv[c] = (s != 0.0) ? (d < 0.0 ? -1.0 : 1.0) / s : 0.0;
+    // Every row of the Poisson operator that reaches the coarse levels is a node
+    // equation with a negative diagonal (Laplacian rows, and boundary rows scaled to
+    // match them); a Galerkin cell whose diagonal comes out positive is an artefact
+    // of an aggregate cut by the boundary, and smoothing it with the sign of that
+    // diagonal would push the error the wrong way.  So the step has the operator's
+    // sign on every cell.
+    dinv[c] = (s != 0.0) ? -1.0 / s : 0.0;
     const unsigned any = __ballot_sync(0xffffffffu, outer);
     if ((threadIdx.x & 31) == 0) ring[c >> 5] = any ? 1 : 0;
 }
