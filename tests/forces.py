@@ -42,3 +42,13 @@ class ForceProbe:
         tx = -p[s] * nbx + (2 * ux * nbx + (uy + vx) * nby) / Re
         ty = -p[s] * nby + ((uy + vx) * nbx + 2 * vy * nby) / Re
         return 2 * np.sum(tx) * self.ds, 2 * np.sum(ty) * self.ds
+
+
+def strouhal(t, cl):
+    """Dominant frequency of a uniformly sampled signal: Hann-windowed spectrum, the
+    peak refined by a parabola through the log power of its three bins."""
+    x = (cl - cl.mean()) * np.hanning(cl.size)
+    P = np.abs(np.fft.rfft(x)) ** 2
+    i = int(np.argmax(P[1:])) + 1
+    a, b, c = np.log(P[i - 1]), np.log(P[i]), np.log(P[i + 1])
+    return (i + 0.5 * (a - c) / (a - 2 * b + c)) / (cl.size * (t[1] - t[0]))

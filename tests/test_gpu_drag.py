@@ -1,7 +1,8 @@
 """Flow past the circular cylinder (Sec. 5, flow past a circular cylinder: steady
 and unsteady), run on the GPU through the C ABI and post-processed on the host
 (tests/forces.py: pressure and viscous traction summed over the body's surface
-nodes), against the paper's table of cylinder results:
+nodes), against the paper's table of cylinder results (Table 3, stored in
+tests/golden/cylinder_table.txt):
 
   * Re = 40, steady: C_D = 1.536, zero lift.  h = 1/16, impulsive start, run to
     t = 60 (C_D steady to 4 digits by t = 50).
@@ -21,12 +22,15 @@ import numpy as np
 import pytest
 
 import workloads as w
-from forces import ForceProbe
+from forces import ForceProbe, strouhal
+from paper_values import load
 
 pytestmark = pytest.mark.gpu
 
-CD_PAPER_RE40 = 1.536
-CD_PAPER_RE100, CL_AMP_PAPER_RE100, ST_PAPER_RE100 = 1.328, 0.31, 0.164
+TABLE = load("cylinder_table.txt")
+CD_PAPER_RE40 = TABLE["Re40.C_D"]
+CD_PAPER_RE100, CL_AMP_PAPER_RE100, ST_PAPER_RE100 = (
+    TABLE["Re100.C_D"], TABLE["Re100.CL_amp"], TABLE["Re100.St"])
 
 
 def test_cylinder_drag_re40(vip):
@@ -43,16 +47,6 @@ def test_cylinder_drag_re40(vip):
     assert abs(cd - cd50) <= 1e-3 * cd, (cd50, cd)  # steady
     assert abs(cd - CD_PAPER_RE40) <= 0.03 * CD_PAPER_RE40, cd
     assert abs(cl) <= 1e-6, cl
-
-
-def strouhal(t, cl):
-    """Dominant frequency of a uniformly sampled signal: Hann-windowed spectrum, the
-    peak refined by a parabola through the log power of its three bins."""
-    x = (cl - cl.mean()) * np.hanning(cl.size)
-    P = np.abs(np.fft.rfft(x)) ** 2
-    i = int(np.argmax(P[1:])) + 1
-    a, b, c = np.log(P[i - 1]), np.log(P[i]), np.log(P[i + 1])
-    return (i + 0.5 * (a - c) / (a - 2 * b + c)) / (cl.size * (t[1] - t[0]))
 
 
 def test_cylinder_shedding_re100(vip):
