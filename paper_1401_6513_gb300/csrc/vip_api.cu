@@ -237,8 +237,9 @@ vip_status vip_autotune(vip_ctx* c, const float* omegas, int32_t nomega, const f
     for (int i = 0; i < ncorr; ++i)
         if (!(corrs[i] > 0.0f && corrs[i] <= 3.0f)) return fail(c, VIP_ERR_ARG, "corr must be in (0, 3]");
     cudaStream_t st = c->stream;
-    double* x = nullptr;
-    VIP_CUDA(dalloc(c, &x, (size_t)c->R));
+    DeviceScratch xs;  // the candidates' solutions
+    VIP_CUDA(cudaMalloc(&xs.p, (size_t)c->R * sizeof(double)));
+    double* x = static_cast<double*>(xs.p);
     cudaEvent_t e0, e1;
     VIP_CUDA(cudaEventCreate(&e0));
     VIP_CUDA(cudaEventCreate(&e1));

@@ -650,14 +650,6 @@ __global__ void k_sell_compact(Sell A, const int64_t* __restrict__ usize,
     if (lane == 0) A.ucptr[s] = o;
 }
 
-// device scratch freed on every return path
-struct DeviceScratch {
-    void* p = nullptr;
-    ~DeviceScratch() {
-        if (p) cudaFree(p);
-    }
-};
-
 static vip_status sell_uniform(vip_ctx* c, Sell& S) {
     cudaStream_t st = c->stream;
     DeviceScratch s_usize, s_uoff;

@@ -218,7 +218,18 @@ void launch_project(vip_ctx* c, cudaStream_t s);
 void launch_spmv(const Sell& A, const double* x, double* y, cudaStream_t s);
 void launch_convection(vip_ctx* c, const double* u, const double* v, double* Nu, double* Nv,
                        cudaStream_t s);
-// memory helper
+// Device scratch that outlives no call: freed on every return path (cudaFree waits
+// for the work queued on it).  Not registered with the context.
+struct DeviceScratch {
+    void* p = nullptr;
+    DeviceScratch() = default;
+    DeviceScratch(const DeviceScratch&) = delete;
+    DeviceScratch& operator=(const DeviceScratch&) = delete;
+    ~DeviceScratch() {
+        if (p) cudaFree(p);
+    }
+};
+// memory helper: context-owned device memory, freed by vip_destroy
 template <class T>
 inline cudaError_t dalloc(vip_ctx* c, T** p, size_t n) {
     void* q = nullptr;
