@@ -255,6 +255,15 @@ vip_status vip_solve(vip_ctx* ctx, int which, const double* b, double* x, int pr
  * iteration count only, never the residual the solve stops at. */
 vip_status vip_set_multigrid(vip_ctx* ctx, float omega, float corr);
 
+/* Parity of the multigrid's first cell grid for geometry geom (-1: every geometry):
+ * level 1 aggregates the nodes of 2h x 2h cells of the geometry's background
+ * lattice; shift_x = 1 (shift_y = 1) moves the cell boundaries by one lattice
+ * spacing in x (y).  Not part of the paper's method; like omega and corr it changes
+ * the iteration count of the Eq. (13) solve, never the residual it stops at.
+ * Default 0, 0.  Shifts are 0 or 1, a periodic axis keeps 0.  Before vip_build
+ * (VIP_ERR_ARG after it, for a bad index or value). */
+vip_status vip_set_mg_shift(vip_ctx* ctx, int32_t geom, int32_t shift_x, int32_t shift_y);
+
 #define VIP_TUNE_MAX 16
 typedef struct {
     int32_t ncand;                 /* candidates tried (nomega x ncorr) */
@@ -270,8 +279,8 @@ typedef struct {
  * and corrs[0..ncorr) (at most VIP_TUNE_MAX pairs; omega in (0, 1.5], corr in (0, 3]),
  * apply the fastest pair that converged (as vip_set_multigrid) and report all of them.
  * Needs vip_build, the multigrid and at least one vip_step since vip_set_state; the
- * state is not changed.  Allocates one R-double scratch vector per call, owned by
- * the context (freed by vip_destroy).  Synchronous. */
+ * state is not changed.  Uses one R-double device scratch vector, freed before it
+ * returns.  Synchronous. */
 vip_status vip_autotune(vip_ctx* ctx, const float* omegas, int32_t nomega, const float* corrs,
                         int32_t ncorr, vip_tune_result* out);
 

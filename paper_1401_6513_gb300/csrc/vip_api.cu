@@ -204,6 +204,23 @@ vip_status vip_set_flow(vip_ctx* c, int32_t geom, double Re, double dt) {
     return VIP_OK;
 }
 
+vip_status vip_set_mg_shift(vip_ctx* c, int32_t geom, int32_t shift_x, int32_t shift_y) {
+    if (!c) return VIP_ERR_ARG;
+    if (c->built) return fail(c, VIP_ERR_ARG, "vip_set_mg_shift after vip_build");
+    if (geom < -1 || geom >= (int32_t)c->geoms.size()) return fail(c, VIP_ERR_ARG, "bad geometry index");
+    if ((shift_x != 0 && shift_x != 1) || (shift_y != 0 && shift_y != 1))
+        return fail(c, VIP_ERR_ARG, "vip_set_mg_shift: shifts must be 0 or 1");
+    for (int32_t g = 0; g < (int32_t)c->geoms.size(); ++g) {
+        if (geom != -1 && geom != g) continue;
+        const Geom& gg = c->geoms[g];
+        if ((shift_x && gg.Lx > 0) || (shift_y && gg.Ly > 0))
+            return fail(c, VIP_ERR_ARG, "vip_set_mg_shift: a periodic axis keeps shift 0");
+    }
+    for (int32_t g = 0; g < (int32_t)c->geoms.size(); ++g)
+        if (geom == -1 || geom == g) { c->geoms[g].mg_shift_x = shift_x; c->geoms[g].mg_shift_y = shift_y; }
+    return VIP_OK;
+}
+
 vip_status vip_get_geometry_iters(vip_ctx* c, int64_t* poisson_iters) {
     if (!c || !poisson_iters) return VIP_ERR_ARG;
     if (!c->built) return fail(c, VIP_ERR_ARG, "vip_get_geometry_iters before vip_build");

@@ -64,6 +64,9 @@ struct Geom {
     bool bordered = false;  // closed domain: Poisson bordered by mu
     bool has_outlet = false;
     int64_t pin = -1;       // bordered: caller index (within the geometry) of node k
+    // parity of the multigrid's first 2h x 2h cell grid: 1 moves the cell boundaries
+    // by one lattice spacing along that axis (non-periodic axes only)
+    int32_t mg_shift_x = 0, mg_shift_y = 0;
 };
 
 // Per-geometry constants visible to kernels.

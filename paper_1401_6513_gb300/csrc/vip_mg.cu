@@ -261,10 +261,13 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         m.h = hmin;
         m.periodic_x = gg.Lx > 0;
         m.periodic_y = gg.Ly > 0;
-        m.x0 = m.periodic_x ? 0.0 : x0;
-        m.y0 = m.periodic_y ? 0.0 : y0;
-        int NX = m.periodic_x ? (int)llround(gg.Lx / hmin) : (int)llround((x1 - x0) / hmin) + 1;
-        int NY = m.periodic_y ? (int)llround(gg.Ly / hmin) : (int)llround((y1 - y0) / hmin) + 1;
+        // a cell-grid shift moves the lattice origin back by one spacing and adds one
+        // lattice column (row), so that lattice index i falls in cell (i + 1) / 2
+        const int shx = m.periodic_x ? 0 : gg.mg_shift_x, shy = m.periodic_y ? 0 : gg.mg_shift_y;
+        m.x0 = m.periodic_x ? 0.0 : x0 - shx * hmin;
+        m.y0 = m.periodic_y ? 0.0 : y0 - shy * hmin;
+        int NX = m.periodic_x ? (int)llround(gg.Lx / hmin) : (int)llround((x1 - x0) / hmin) + 1 + shx;
+        int NY = m.periodic_y ? (int)llround(gg.Ly / hmin) : (int)llround((y1 - y0) / hmin) + 1 + shy;
         m.nx[0] = NX;
         m.ny[0] = NY;
         int l = 0;

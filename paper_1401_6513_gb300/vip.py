@@ -35,7 +35,7 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_set_profiling", "vip_get_profile", "vip_ws_collect", "vip_ws_train",
            "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static",
            "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout",
-           "vip_multigrid_info"]
+           "vip_multigrid_info", "vip_set_mg_shift"]
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -115,6 +115,7 @@ def lib(path: str | Path | None = None):
         "vip_bicgstab_static": ([C.c_int, vp, i64, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(i32),
                                  C.POINTER(dbl)], C.c_int),
         "vip_set_multigrid": ([vp, C.c_float, C.c_float], C.c_int),
+        "vip_set_mg_shift": ([vp, i32, i32, i32], C.c_int),
         "vip_get_geometry_iters": ([vp, vp], C.c_int),
         "vip_operator_layout": ([vp, C.c_int, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64),
                                  C.POINTER(i64)], C.c_int),
@@ -234,6 +235,11 @@ class Context:
 
     def vip_set_multigrid(self, omega=1.0, corr=1.5):
         self._check(self.L.vip_set_multigrid(self.h, float(omega), float(corr)))
+
+    def vip_set_mg_shift(self, geom, shift_x, shift_y):
+        """Parity (0 or 1 per axis) of geometry geom's first multigrid cell grid
+        (-1: every geometry); before vip_build."""
+        self._check(self.L.vip_set_mg_shift(self.h, int(geom), int(shift_x), int(shift_y)))
 
     def vip_autotune(self, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.6, 1.7, 1.8, 1.9, 2.1)) -> TuneResult:
         """Time the last step's pressure-increment solve for every (omega, corr) pair
@@ -355,6 +361,34 @@ def vip_bicgstab_static(device, stream, n, row_ptr, col, val, b, x, rtol=1e-10, 
     return st, it.value, rr.value
 
 
+MG_SHIFTS = ((0, 0), (1, 0), (0, 1), (1, 1))
+
+
+def choose_mg_shifts(nodesets, steps=2, make=None, **solver_kw):
+    """Cell-grid parity of the multigrid for every node set: one context per parity
+    in MG_SHIFTS (all node sets in it, a periodic axis kept at 0), `steps` steps
+    from the initial state, and for each node set the parity whose Poisson solves
+    took the fewest iterations (vip_get_geometry_iters).  A context whose steps fail
+    counts as the worst for all its node sets.  Returns (shifts, iterations [4, G])."""
+    if not isinstance(nodesets, (list, tuple)):
+        nodesets = [nodesets]
+    make = make or solver_for
+    its = np.full((len(MG_SHIFTS), len(nodesets)), np.iinfo(np.int64).max, np.int64)
+    for k, (sx, sy) in enumerate(MG_SHIFTS):
+        shifts = [(0 if ns.Lx > 0 else sx, 0 if ns.Ly > 0 else sy) for ns in nodesets]
+        ctx = make(nodesets, mg_shifts=shifts, **solver_kw)
+        try:
+            ctx.vip_step(steps)
+            its[k] = ctx.vip_get_geometry_iters()
+        except VipError:
+            pass
+        finally:
+            ctx.close()
+    best = its.argmin(axis=0)
+    return [(0 if ns.Lx > 0 else MG_SHIFTS[b][0], 0 if ns.Ly > 0 else MG_SHIFTS[b][1])
+            for ns, b in zip(nodesets, best)], its
+
+
 def geometry_signature(nodesets) -> str:
     """Key of a set of node sets for the autotuning cache: names, node counts and a
     hash of the coordinates and kinds."""
@@ -424,13 +458,19 @@ def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.6,
 
 def solver_for(nodesets, precision=VIP_PREC_MIXED, rtol=1e-8, max_iters=20000,
                identity=VIP_IDENTITY_EXACT, weight=VIP_W_CUBIC_SPLINE, support=2.2,
-               device=0, stream=None, set_state=True) -> Context:
-    """Create a context for one node set or a list of them, build it and set u0, v0, p0."""
+               device=0, stream=None, set_state=True, mg_shifts=None) -> Context:
+    """Create a context for one node set or a list of them, build it and set u0, v0, p0.
+    mg_shifts: one (shift_x, shift_y) per node set for vip_set_mg_shift (default 0, 0)."""
     if not isinstance(nodesets, (list, tuple)):
         nodesets = [nodesets]
     ctx = Context(device, stream)
     for ns in nodesets:
         ctx.add_nodeset(ns)
+    if mg_shifts is not None:
+        if len(mg_shifts) != len(nodesets):
+            raise ValueError("one (shift_x, shift_y) per node set")
+        for g, (sx, sy) in enumerate(mg_shifts):
+            ctx.vip_set_mg_shift(g, sx, sy)
     ctx.vip_set_mls(2, weight, support)
     ctx.vip_set_solver(precision, rtol, max_iters, identity)
     ctx.vip_build()

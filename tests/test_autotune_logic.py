@@ -102,3 +102,45 @@ def test_geometry_signature_tracks_nodes():
     moved.x[3] += 1e-9
     assert vip.geometry_signature([moved]) != vip.geometry_signature([a])
     assert np.all(a.x == w.cavity(8, Re=100.0).x)
+
+
+class ShiftCtx:
+    """Fake context for choose_mg_shifts: Poisson iterations per node set for the
+    context's cell-grid shifts; fails to step when told to."""
+
+    def __init__(self, table, shifts, fail):
+        self.table, self.shifts, self.fail = table, shifts, fail
+        self.closed = False
+
+    def vip_step(self, n):
+        if self.fail:
+            raise vip.VipError(vip.VIP_ERR_NOT_CONVERGED, "did not converge")
+
+    def vip_get_geometry_iters(self):
+        return np.array([self.table[g][s] for g, s in enumerate(self.shifts)], np.int64)
+
+    def close(self):
+        self.closed = True
+
+
+def test_choose_mg_shifts_takes_each_geometry_s_fewest_iterations():
+    a, b = w.cavity(8, Re=100.0), w.periodic_box(8)
+    # per node set: iterations for each (shift_x, shift_y) the context was built with
+    table = [{(0, 0): 90, (1, 0): 120, (0, 1): 40, (1, 1): 55},
+             {(0, 0): 30}]                       # periodic: always (0, 0)
+    made = []
+
+    def make(nodesets, mg_shifts, **kw):
+        assert kw == {"rtol": 1e-8}
+        ctx = ShiftCtx(table, mg_shifts, fail=(mg_shifts[0] == (1, 1)))
+        made.append((mg_shifts, ctx))
+        return ctx
+
+    shifts, its = vip.choose_mg_shifts([a, b], make=make, rtol=1e-8)
+    assert shifts == [(0, 1), (0, 0)]
+    assert [m[0] for m in made] == [[(0, 0), (0, 0)], [(1, 0), (0, 0)], [(0, 1), (0, 0)],
+                                    [(1, 1), (0, 0)]]
+    assert all(ctx.closed for _, ctx in made)
+    # the failed context counts as the worst for both node sets
+    assert its.shape == (4, 2) and its[3, 0] == its[3, 1] == np.iinfo(np.int64).max
+    assert list(its[:3, 0]) == [90, 120, 40]
