@@ -240,6 +240,13 @@ class Context:
         """Parity (0 or 1 per axis) of geometry geom's first multigrid cell grid
         (-1: every geometry); before vip_build."""
         self._check(self.L.vip_set_mg_shift(self.h, int(geom), int(shift_x), int(shift_y)))
+        self.__dict__.setdefault("_mg_shift_calls", []).append((int(geom), int(shift_x), int(shift_y)))
+
+    def mg_shift_key(self):
+        """The vip_set_mg_shift calls made on this context, as a suffix of the
+        autotuning cache key ("" when the parity is the default everywhere)."""
+        calls = self.__dict__.get("_mg_shift_calls", [])
+        return "|mg:" + ",".join(f"{g}:{x}{y}" for g, x, y in calls) if calls else ""
 
     def vip_autotune(self, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.6, 1.7, 1.8, 1.9, 2.1)) -> TuneResult:
         """Time the last step's pressure-increment solve for every (omega, corr) pair
@@ -406,7 +413,8 @@ def geometry_signature(nodesets) -> str:
 def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.6, 1.7, 1.8, 1.9, 2.1),
              refine=3, refine_steps=3):
     """Pick the multigrid parameters of a context built from `nodesets`: from the JSON
-    file `cache` when it has this geometry signature, else in two stages, then store
+    file `cache` when it has this geometry signature (with the context's cell-grid
+    parities), else in two stages, then store
     the choice there:
       1. vip_autotune after one step: every (omega, corr) pair solves that step's
          pressure-increment system from a zero guess, timed on the device;
@@ -417,7 +425,8 @@ def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.6,
     The state is reset to the initial fields afterwards.  Returns the chosen
     {"omega", "corr", ...} entry."""
     import json
-    key = geometry_signature(nodesets)
+    # the hierarchy, hence the best parameters, depends on the cell-grid parity too
+    key = geometry_signature(nodesets) + getattr(ctx, "mg_shift_key", lambda: "")()
     table = {}
     if cache is not None and Path(cache).exists():
         table = json.loads(Path(cache).read_text())

@@ -144,3 +144,19 @@ def test_choose_mg_shifts_takes_each_geometry_s_fewest_iterations():
     # the failed context counts as the worst for both node sets
     assert its.shape == (4, 2) and its[3, 0] == its[3, 1] == np.iinfo(np.int64).max
     assert list(its[:3, 0]) == [90, 120, 40]
+
+
+def test_cache_key_includes_the_cell_grid_parity(tmp_path):
+    """A choice tuned on one cell-grid parity is not reused for another."""
+    ns = w.cavity(8, Re=100.0)
+    ms = {(1.0, 1.5): 4.0, (1.0, 1.7): 5.0}
+    cache = tmp_path / "tune.json"
+    plain = make(ms, {(1.0, 1.5): 50, (1.0, 1.7): 40})
+    first = vip.autotune(plain, [ns], cache=cache, omegas=(1.0,), corrs=(1.5, 1.7))
+    assert not first["cached"]
+    shifted = make(ms, {(1.0, 1.5): 50, (1.0, 1.7): 40})
+    shifted.mg_shift_key = lambda: "|mg:0:11"
+    again = vip.autotune(shifted, [ns], cache=cache, omegas=(1.0,), corrs=(1.5, 1.7))
+    assert not again["cached"] and shifted.calls
+    third = make(ms, {})
+    assert vip.autotune(third, [ns], cache=cache, omegas=(1.0,), corrs=(1.5, 1.7))["cached"]
