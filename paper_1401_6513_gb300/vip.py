@@ -381,8 +381,13 @@ def choose_mg_shifts(nodesets, steps=2, make=None, **solver_kw):
         nodesets = [nodesets]
     make = make or solver_for
     its = np.full((len(MG_SHIFTS), len(nodesets)), np.iinfo(np.int64).max, np.int64)
+    seen = {}
     for k, (sx, sy) in enumerate(MG_SHIFTS):
         shifts = [(0 if ns.Lx > 0 else sx, 0 if ns.Ly > 0 else sy) for ns in nodesets]
+        if tuple(shifts) in seen:  # periodic axes make some parities coincide
+            its[k] = its[seen[tuple(shifts)]]
+            continue
+        seen[tuple(shifts)] = k
         ctx = make(nodesets, mg_shifts=shifts, **solver_kw)
         try:
             ctx.vip_step(steps)

@@ -160,3 +160,16 @@ def test_cache_key_includes_the_cell_grid_parity(tmp_path):
     assert not again["cached"] and shifted.calls
     third = make(ms, {})
     assert vip.autotune(third, [ns], cache=cache, omegas=(1.0,), corrs=(1.5, 1.7))["cached"]
+
+
+def test_choose_mg_shifts_builds_each_distinct_assignment_once():
+    boxes = [w.periodic_box(8), w.periodic_box(9)]
+    made = []
+
+    def make(nodesets, mg_shifts, **kw):
+        made.append(mg_shifts)
+        return ShiftCtx([{(0, 0): 12}, {(0, 0): 15}], mg_shifts, fail=False)
+
+    shifts, its = vip.choose_mg_shifts(boxes, make=make)
+    assert made == [[(0, 0), (0, 0)]]
+    assert shifts == [(0, 0), (0, 0)] and (its == [[12, 15]] * 4).all()
