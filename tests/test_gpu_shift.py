@@ -2,11 +2,11 @@
 
 Level 1 of the Poisson preconditioner aggregates 2h x 2h cells of the background
 lattice; a shift of one lattice spacing pairs different rows and columns.  On a
-channel, shifting by one row pairs a slip-wall row with the first interior row,
-and the NumPy model of the same hierarchy then needs about ten times the
-iterations (20 -> 230 on this case).  The parity changes only the iteration count:
-every solve still stops at its residual, recomputed here on the host from the
-exported operator.
+channel, shifting by one row pairs a slip-wall row with the first interior row, a
+far weaker hierarchy: the solve needs more iterations (about ten times as many on
+this case, from the same hierarchy assembled on the host from the oracle's
+operators).  The parity changes only the iteration count: every solve still stops
+at its residual, recomputed here on the host from the exported operator.
 """
 import numpy as np
 import pytest
