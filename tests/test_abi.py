@@ -31,3 +31,19 @@ def test_binding_refuses_missing_library(tmp_path):
     from paper_1401_6513_gb300 import vip
     with pytest.raises(ImportError):
         vip.lib(tmp_path / "libvip.so")
+
+
+def test_header_is_plain_c():
+    """The boundary is a C ABI: the header compiles as C99 (no C++ or torch types)
+    and as C++, with warnings as errors."""
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("gcc not found")
+    hdr = str(ROOT / "include" / "vip.h")
+    for lang, std in (("c", "-std=c99"), ("c++", "-std=c++17")):
+        r = subprocess.run([cc, "-fsyntax-only", std, "-Wall", "-Wextra", "-Werror", "-x", lang, hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, (lang, r.stderr)
