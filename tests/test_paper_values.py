@@ -220,3 +220,38 @@ def test_strouhal_estimator_on_synthetic_lift():
         for ph in rng.uniform(0.0, 2 * np.pi, 3):
             cl = 0.02 + 0.31 * np.sin(2 * np.pi * f * t + ph) + 0.01 * np.sin(4 * np.pi * f * t + 2 * ph)
             assert abs(strouhal(t, cl) / f - 1.0) <= 5e-3, (f, ph)
+
+
+# -- bumpy cylinders ---------------------------------------------------------------
+
+def test_bumpy_fixture_is_consistent():
+    g = load("bumpy_drag.txt")
+    assert g["m_b"] == [10.0 * k for k in range(1, 11)]
+    # the characteristic length is the body's largest radius
+    assert math.isclose(g["R"], g["r0"] * (1 + g["gamma"]), rel_tol=1e-12)
+    assert g["cd_peak_m_b"] in g["m_b"] and 0.0 < g["cd_reduction_min"] < 1.0
+
+
+def test_force_probe_on_a_bumpy_body_is_second_order():
+    """On the body r = r0 (1 + gamma cos(m_b theta)) (m_b = 10) the probe's sum over
+    surface nodes at equal arc length is a quadrature of second order in h: for a
+    mixed polynomial field its force approaches the divergence-theorem value
+    (area pi r0^2 (1 + gamma^2 / 2)) with error ratio ~4 when h halves."""
+    g = load("bumpy_drag.txt")
+    r0, gamma = g["r0"], g["gamma"]
+    a, b, pc = (np.asarray(c, float) for c in CASES["mixed"])
+    errs = []
+    for h in (1 / 32, 1 / 64):
+        ns = w.channel_body(h, ("bumps", r0, gamma, 10), Re=g["Re"], xlim=(-3.0, 4.0), ylim=(-3.0, 3.0))
+        x, y = ns.x, ns.y
+        mono = np.stack([np.ones_like(x), x, y, x * x, x * y, y * y])
+        s = np.nonzero((ns.kind == vo.KIND_WALL) & (np.hypot(x, y) < 2.0))[0]
+        probe = ForceProbe(FieldContext(ns, s, a @ mono, b @ mono, pc[0] + pc[1] * x + pc[2] * y), ns)
+        cd, cl = probe.coefficients()
+        area = math.pi * r0 * r0 * (1 + gamma * gamma / 2)
+        div_sigma = np.array([-pc[1] + (4 * a[3] + 2 * a[5] + b[4]) / ns.Re,
+                              -pc[2] + (2 * b[3] + 4 * b[5] + a[4]) / ns.Re])
+        expect = 2 * area * div_sigma
+        errs.append(max(abs(cd / expect[0] - 1), abs(cl / expect[1] - 1)))
+    assert errs[0] < 6e-3 and errs[1] < 1.5e-3, errs
+    assert 3.5 < errs[0] / errs[1] < 4.5, errs
