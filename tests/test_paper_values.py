@@ -255,3 +255,47 @@ def test_force_probe_on_a_bumpy_body_is_second_order():
         errs.append(max(abs(cd / expect[0] - 1), abs(cl / expect[1] - 1)))
     assert errs[0] < 6e-3 and errs[1] < 1.5e-3, errs
     assert 3.5 < errs[0] / errs[1] < 4.5, errs
+
+
+# -- the Moffatt cavity as a workload ------------------------------------------------
+
+def test_wedge_cavity_samples_the_printed_triangle():
+    """workloads.wedge_cavity is the triangle of Tables 1-2: apex angle 28.072
+    degrees, every node in the closed triangle, wall nodes on its edges with unit
+    normals pointing out of it, and about (n_base - 1)^2 nodes (the area is 1 in
+    units of the base), as 400 x 800 / 2 is for a 400-node base."""
+    g = load("moffatt_wedge.txt")
+    ns = w.wedge_cavity(49)
+    h = ns.meta["h"]
+    assert round(ns.meta["apex_angle_deg"], 3) == g["apex_angle_deg"]
+    x, y = ns.x, ns.y
+    # inside: below the lid, right of the left edge, left of the right edge
+    L = math.hypot(0.5, 2.0)
+    dl = (2.0 * x - 0.5 * (-y)) / L          # distance from the left edge, inwards
+    dr = (2.0 * (1.0 - x) - 0.5 * (-y)) / L  # from the right edge
+    assert np.all(y <= 1e-12) and np.all(dl >= -1e-12) and np.all(dr >= -1e-12)
+    wall = ns.kind == vo.KIND_WALL
+    on_edge = (np.abs(y) < 1e-12) | (np.abs(dl) < 1e-12) | (np.abs(dr) < 1e-12)
+    assert np.array_equal(wall, on_edge)
+    assert np.allclose(np.hypot(ns.nx[wall], ns.ny[wall]), 1.0)
+    # outward: the normal points away from the triangle's centroid side
+    cx, cy = 0.5, -2.0 / 3.0
+    assert np.all(ns.nx[wall] * (x[wall] - cx) + ns.ny[wall] * (y[wall] - cy) > 0)
+    interior = ~wall
+    # lattice nodes keep a clearance of 0.55 h from the slanted edges
+    assert np.all(np.minimum(dl[interior], dr[interior]) >= 0.55 * h - 1e-12)
+    assert abs(ns.n * h * h - 1.0) < 0.08, ns.n * h * h
+    # the lid moves: u = 1 on the lid except its two corner nodes
+    lid = wall & (np.abs(y) < 1e-12)
+    assert np.sum(ns.u0[lid] == 1.0) == lid.sum() - 2
+
+
+def test_oracle_steps_on_the_wedge_cavity():
+    """The narrow apex keeps every MLS fit regular (no SingularStencil) and the
+    oracle's steps converge and stay bounded."""
+    ns = w.wedge_cavity(33)
+    fs = vo.FractionalStep(vo.Operators(ns), rtol=1e-8)
+    for _ in range(3):
+        fs.step()
+    assert np.all(np.isfinite(fs.u)) and np.all(np.isfinite(fs.v))
+    assert np.abs(fs.u).max() <= 1.5

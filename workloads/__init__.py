@@ -13,6 +13,6 @@ initial data of each workload.
 """
 from .geometry import (  # noqa: F401
     KIND_INTERIOR, KIND_WALL, KIND_SLIP, KIND_OUTLET,
-    NodeSet, periodic_box, cavity, channel_body, triangle_cavity,
+    NodeSet, periodic_box, cavity, channel_body, triangle_cavity, wedge_cavity,
     triangle_batch, taylor_green, workload,
 )

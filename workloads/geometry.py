@@ -312,6 +312,82 @@ def triangle_cavity(n_edge: int, Re: float = 100.0, dt: float | None = None,
                    np.zeros(N), Re, dt, -H - h, {"h": h, "n_edge": n})
 
 
+def wedge_cavity(n_base: int, height: float = 2.0, Re: float = 1.0, dt: float | None = None,
+                 apex_support: float = CORNER_SUPPORT, name: str | None = None) -> NodeSet:
+    """Isosceles triangular cavity of the Moffatt-eddy flow (Sec. 5, triangular cavity
+    flow): base 1 (the lid, on top), apex `height` below the base's midpoint.  The
+    default height 2 gives the apex angle 2 atan(1/4) = 28.072 degrees.
+
+    Vertices (0,0), (1,0) (the lid) and (1/2, -height).  Lattice spacing
+    h = 1/(n_base-1) over the bounding box; edge nodes at spacing close to h along
+    each slanted edge; lattice nodes within CLEARANCE*h of a slanted edge are removed.
+    Normals point out of the cavity; at a vertex they bisect the two edges' normals.
+    Nodes within 3h of a lid corner, and within 3h / sin(apex half-angle) of the apex,
+    get h_local = apex_support*h.  Lid u = 1 (its end nodes 0), all else at rest.
+    """
+    n = int(n_base)
+    h = 1.0 / (n - 1)
+    A, B, C = np.array([0.0, 0.0]), np.array([1.0, 0.0]), np.array([0.5, -float(height)])
+    L = float(np.hypot(0.5, height))
+    nl = np.array([-height, -0.5]) / L      # outward normal of the left edge A-C
+    nr = np.array([height, -0.5]) / L       # outward normal of the right edge B-C
+    xs, ys, nxs, nys, us = [], [], [], [], []
+    # lid row, corners included
+    i = np.arange(n)
+    xs.append(i * h)
+    ys.append(np.zeros(n))
+    lid_n = np.tile([0.0, 1.0], (n, 1))
+    for k, side in ((0, nl), (n - 1, nr)):
+        v = lid_n[k] + side
+        lid_n[k] = v / np.hypot(*v)
+    nxs.append(lid_n[:, 0])
+    nys.append(lid_n[:, 1])
+    ul = np.ones(n)
+    ul[0] = ul[-1] = 0.0
+    us.append(ul)
+    # slanted edges without the lid corners; the apex once, on the left edge
+    m = max(2, int(round(L / h)))
+    t = np.arange(1, m + 1) / m
+    left = A[None, :] + t[:, None] * (C - A)[None, :]
+    right = B[None, :] + t[:-1, None] * (C - B)[None, :]
+    lnrm = np.tile(nl, (m, 1))
+    lnrm[-1] = [0.0, -1.0]
+    rnrm = np.tile(nr, (m - 1, 1))
+    for P, Nn in ((left, lnrm), (right, rnrm)):
+        xs.append(P[:, 0])
+        ys.append(P[:, 1])
+        nxs.append(Nn[:, 0])
+        nys.append(Nn[:, 1])
+        us.append(np.zeros(P.shape[0]))
+    nb = sum(a.size for a in xs)
+    # interior lattice
+    nrow = int(np.floor(height / h))
+    jj, ii = np.meshgrid(np.arange(1, nrow + 1), np.arange(n), indexing="ij")
+    px = (ii * h).ravel()
+    py = (-jj * h).ravel()
+    dl = -((px - A[0]) * nl[0] + (py - A[1]) * nl[1])   # distances inside the edges
+    dr = -((px - B[0]) * nr[0] + (py - B[1]) * nr[1])
+    ok = (dl >= CLEARANCE * h) & (dr >= CLEARANCE * h)
+    xs.append(px[ok])
+    ys.append(py[ok])
+    nxs.append(np.zeros(int(ok.sum())))
+    nys.append(np.zeros(int(ok.sum())))
+    us.append(np.zeros(int(ok.sum())))
+    x, y = np.concatenate(xs), np.concatenate(ys)
+    N = x.size
+    kind = np.zeros(N, np.uint8)
+    kind[:nb] = KIND_WALL
+    hl = np.full(N, h)
+    half = np.arctan2(0.5, height)
+    for V, r in ((A, 3 * h), (B, 3 * h), (C, 3 * h / np.sin(half))):
+        hl[np.hypot(x - V[0], y - V[1]) < r] = apex_support * h
+    if dt is None:
+        dt = 0.25 * h
+    return _finish(name or f"wedge{n}", x, y, kind, np.concatenate(nxs), np.concatenate(nys), hl,
+                   0.0, 0.0, np.concatenate(us), np.zeros(N), np.zeros(N), Re, dt, -height - h,
+                   {"h": h, "n_base": n, "apex_angle_deg": float(np.degrees(2 * half))})
+
+
 def triangle_batch(count: int = 64, seed: int = 20140126, lo: int = 64, hi: int = 512):
     """Seeded batch of equilateral lid-driven cavities: n_edge ~ U{lo..hi}, Re ~ U[100, 1000]."""
     rng = np.random.default_rng(seed)
