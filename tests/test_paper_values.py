@@ -291,8 +291,10 @@ def test_wedge_cavity_samples_the_printed_triangle():
 
 
 def test_oracle_steps_on_the_wedge_cavity():
-    """The narrow apex keeps every MLS fit regular (no SingularStencil) and the
-    oracle's steps converge and stay bounded."""
+    """Every MLS fit of the wedge is regular (no SingularStencil), and the oracle's
+    first steps converge.  Longer runs are not stable yet: velocity grows from the
+    lattice nodes near the 28-degree apex within 25-60 steps at every Re tried, so
+    a Moffatt run needs an apex treatment first."""
     ns = w.wedge_cavity(33)
     fs = vo.FractionalStep(vo.Operators(ns), rtol=1e-8)
     for _ in range(3):
