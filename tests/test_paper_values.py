@@ -292,9 +292,10 @@ def test_wedge_cavity_samples_the_printed_triangle():
 
 def test_oracle_steps_on_the_wedge_cavity():
     """Every MLS fit of the wedge is regular (no SingularStencil), and the oracle's
-    first steps converge.  Longer runs are not stable yet: velocity grows from the
-    lattice nodes near the 28-degree apex within 25-60 steps at every Re tried, so
-    a Moffatt run needs an apex treatment first."""
+    first steps converge.  Longer runs are not stable yet: the pressure rows'
+    normal points of the wall nodes next to the 28-degree apex fall outside the
+    cavity, and velocity grows from there within 25-75 steps; a Moffatt run needs
+    those points kept inside the domain first."""
     ns = w.wedge_cavity(33)
     fs = vo.FractionalStep(vo.Operators(ns), rtol=1e-8)
     for _ in range(3):

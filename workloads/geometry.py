@@ -322,8 +322,9 @@ def wedge_cavity(n_base: int, height: float = 2.0, Re: float = 1.0, dt: float | 
     h = 1/(n_base-1) over the bounding box; edge nodes at spacing close to h along
     each slanted edge; lattice nodes within CLEARANCE*h of a slanted edge are removed.
     Normals point out of the cavity; at a vertex they bisect the two edges' normals.
-    Nodes within 3h of a lid corner, and within 3h / sin(apex half-angle) of the apex,
-    get h_local = apex_support*h.  Lid u = 1 (its end nodes 0), all else at rest.
+    Nodes within 3h / sin(apex half-angle) of the apex get h_local = apex_support*h;
+    the lid corners (76 degrees at the default height) keep h: a wider support
+    there made the flow unstable.  Lid u = 1 (its end nodes 0), all else at rest.
     """
     n = int(n_base)
     h = 1.0 / (n - 1)
@@ -379,8 +380,7 @@ def wedge_cavity(n_base: int, height: float = 2.0, Re: float = 1.0, dt: float | 
     kind[:nb] = KIND_WALL
     hl = np.full(N, h)
     half = np.arctan2(0.5, height)
-    for V, r in ((A, 3 * h), (B, 3 * h), (C, 3 * h / np.sin(half))):
-        hl[np.hypot(x - V[0], y - V[1]) < r] = apex_support * h
+    hl[np.hypot(x - C[0], y - C[1]) < 3 * h / np.sin(half)] = apex_support * h
     if dt is None:
         dt = 0.25 * h
     return _finish(name or f"wedge{n}", x, y, kind, np.concatenate(nxs), np.concatenate(nys), hl,
