@@ -26,7 +26,10 @@ Pins (tests/test_oracle_*.py, all CPU):
   * BiCGSTAB: agrees with a sparse direct solve (scipy spsolve);
   * full step: observed second order in space and time on the decaying
     vortices (Sec. 5.1) and the divergence of the projected velocity at the
-    Poisson tolerance in the composite-operator reading (Eqs. 13-14).
+    Poisson tolerance in the composite-operator reading (Eqs. 13-14);
+  * normal points (flag probes="inside", tests/test_paper_values.py): inside
+    the exact edges of the 28-degree wedge cavity, unchanged on the square
+    cavity, and the wedge's steps stable with them and unstable without.
 """
 from __future__ import annotations
 
@@ -208,7 +211,7 @@ class Operators:
                -- the divergence (item 2) and gradient (item 3) of Sec. 4.1.
     """
 
-    def __init__(self, ns, weight="cubic_spline", support=2.2):
+    def __init__(self, ns, weight="cubic_spline", support=2.2, probes="normal"):
         x, y, h = ns.x, ns.y, ns.h
         N = ns.n
         self.N = N
@@ -252,9 +255,16 @@ class Operators:
         # q_i = (4 q(x_i + h n_in) - q(x_i + 2 h n_in)) / 3 with MLS values there).
         self.boundary = np.nonzero(ns.kind != KIND_INTERIOR)[0]
         bb = self.boundary
+        if probes == "normal":
+            step = h[bb].copy()
+        elif probes == "inside":
+            step = self._probe_steps_inside(ns, bb)
+        else:
+            raise ValueError(f"probes must be 'normal' or 'inside', not {probes!r}")
+        self.probe_step = step
         self.probe = {
-            1: (x[bb] - h[bb] * ns.nx[bb], y[bb] - h[bb] * ns.ny[bb]),
-            2: (x[bb] - 2.0 * h[bb] * ns.nx[bb], y[bb] - 2.0 * h[bb] * ns.ny[bb]),
+            1: (x[bb] - step * ns.nx[bb], y[bb] - step * ns.ny[bb]),
+            2: (x[bb] - 2.0 * step * ns.nx[bb], y[bb] - 2.0 * step * ns.ny[bb]),
         }
         self.B = {}
         for k, (qx, qy) in self.probe.items():
@@ -267,6 +277,27 @@ class Operators:
         sel[bb] = 1.0
         # Neumann operator: q_i - (4/3) q(probe 1) + (1/3) q(probe 2) on boundary rows
         self.Nb = (sp.diags(sel) - (4.0 / 3.0) * self.B[1] + (1.0 / 3.0) * self.B[2]).tocsr()
+
+    @staticmethod
+    def _probe_steps_inside(ns, bb):
+        """Reading (flag probes="inside"; the paper gives no boundary treatment for
+        phi): where walls meet at a narrow angle the normal points can pass through
+        the opposite wall.  A boundary node's step starts at its h_local and shrinks
+        by 0.7 (at most 12 times) until its second normal point lies on the inner
+        side of the tangent at the boundary node nearest to that point, by 5 % of
+        that node's spacing."""
+        bx, by = ns.x[bb], ns.y[bb]
+        tree = cKDTree(np.stack([bx, by], 1))
+        step = ns.h[bb].copy()
+        for _ in range(12):
+            qx, qy = bx - 2.0 * step * ns.nx[bb], by - 2.0 * step * ns.ny[bb]
+            _, j = tree.query(np.stack([qx, qy], 1))
+            side = (qx - bx[j]) * ns.nx[bb][j] + (qy - by[j]) * ns.ny[bb][j]
+            bad = side > -0.05 * ns.h[bb][j]
+            if not bad.any():
+                break
+            step = np.where(bad, 0.7 * step, step)
+        return step
 
     @staticmethod
     def _csr(ptr, idx, val, N):

@@ -292,10 +292,8 @@ def test_wedge_cavity_samples_the_printed_triangle():
 
 def test_oracle_steps_on_the_wedge_cavity():
     """Every MLS fit of the wedge is regular (no SingularStencil), and the oracle's
-    first steps converge.  Longer runs are not stable yet: the pressure rows'
-    normal points of the wall nodes next to the 28-degree apex fall outside the
-    cavity, and velocity grows from there within 25-75 steps; a Moffatt run needs
-    those points kept inside the domain first."""
+    first steps converge with the default normal points (longer runs need
+    probes="inside", below)."""
     ns = w.wedge_cavity(33)
     fs = vo.FractionalStep(vo.Operators(ns), rtol=1e-8)
     for _ in range(3):
@@ -321,3 +319,45 @@ def test_eddy_ratios_from_the_axis_velocity_of_the_corner_mode():
     assert rr.size >= 4 and ii.size >= 3, (rr, ii)
     assert np.allclose(rr, math.exp(math.pi / lam.imag), rtol=5e-3), rr
     assert np.allclose(ii, math.exp(math.pi * (lam.real - 1) / lam.imag), rtol=5e-3), ii
+
+
+def test_probes_inside_keep_the_normal_points_in_the_wedge():
+    """With probes="inside" every normal point of the wedge lies in the closed
+    triangle (checked against its exact edges); with the default placement the
+    second points of the wall nodes next to the apex pass through the opposite
+    wall.  On the square cavity the flag changes no boundary row."""
+    ns = w.wedge_cavity(33, Re=100.0)
+    L = math.hypot(0.5, 2.0)
+
+    def inside(qx, qy):
+        dl = (2.0 * qx - 0.5 * (-qy)) / L
+        dr = (2.0 * (1.0 - qx) - 0.5 * (-qy)) / L
+        return (qy <= 1e-12) & (dl >= -1e-12) & (dr >= -1e-12)
+
+    plain = vo.Operators(ns)
+    assert (~inside(*plain.probe[2])).sum() == 12
+    fixed = vo.Operators(ns, probes="inside")
+    for k in (1, 2):
+        assert inside(*fixed.probe[k]).all(), k
+    sq = w.cavity(24, Re=100.0)
+    a, b = vo.Operators(sq), vo.Operators(sq, probes="inside")
+    assert np.array_equal(a.probe_step, b.probe_step)
+    assert (a.Nb != b.Nb).nnz == 0
+
+
+def test_wedge_is_stable_only_with_the_normal_points_inside():
+    """The diagnosis of the wedge's instability: with the default normal points the
+    velocity grows from the apex within 100 steps (Re = 100, dt = h/4); with them
+    kept inside the cavity 300 steps stay bounded by the lid speed."""
+    def run(probes, steps):
+        ns = w.wedge_cavity(33, Re=100.0)
+        fs = vo.FractionalStep(vo.Operators(ns, probes=probes), rtol=1e-10)
+        for k in range(steps):
+            fs.step()
+            if not np.abs(fs.u).max() < 10:
+                return k + 1
+        return None
+
+    assert run("normal", 100) is not None
+    assert run("inside", 300) is None
+
