@@ -61,12 +61,24 @@ enum { VIP_NODE_INTERIOR = 0, VIP_NODE_WALL = 1, VIP_NODE_SLIP = 2, VIP_NODE_OUT
  *   PAPER         (1 - r^((1-r)^2))^4 for r < 1, 0 else (the printed form). */
 enum { VIP_W_CUBIC_SPLINE = 0, VIP_W_PAPER = 1 };
 
-/* Precision of the Krylov solves (Eqs. 12-13):
- *   FP64   BiCGSTAB in FP64 on FP64 operators;
- *   MIXED  FP64 residual b - A x on FP64 operators, correction equation solved
- *          by BiCGSTAB in FP32 on FP32 copies of the operators, repeated until
- *          the FP64 relative residual meets the tolerance. */
-enum { VIP_PREC_FP64 = 0, VIP_PREC_MIXED = 1 };
+/* Precision of the Krylov solves (Eqs. 12-13).  Every form stops on the same
+ * test, the FP64 relative residual ||b - A x|| / ||b|| <= rtol of the FP64
+ * operator, so they differ in cost and in the rounding of the solution only.
+ *   FP64   BiCGSTAB in FP64 on FP64 operators; the Poisson solve's multigrid
+ *          preconditioner in FP64;
+ *   MIXED  iterative refinement: FP64 residual b - A x on FP64 operators; the
+ *          correction equation A d = r solved by BiCGSTAB in FP32 arithmetic
+ *          on FP32 vectors and FP32 copies of the operators (stencil rows
+ *          applied in differenced form, sum_k a_ik (d_k - d_i) + rowsum_i d_i
+ *          with the FP64 row sum rounded to FP32), preconditioned by an FP32
+ *          V-cycle, to a relative tolerance set by vip_set_refinement; the
+ *          correction is accumulated in FP64; repeated until the FP64 residual
+ *          meets rtol;
+ *   MG32   BiCGSTAB in FP64 (operator applications, vectors, dot products)
+ *          whose multigrid preconditioner runs in FP32 (FP32 copies of every
+ *          level's operator, FP32 vectors); only the Poisson solve has a
+ *          preconditioner, so the Helmholtz solves run as FP64. */
+enum { VIP_PREC_FP64 = 0, VIP_PREC_MIXED = 1, VIP_PREC_MG32 = 2 };
 
 /* Identity operator wherever the paper writes I in Eq. (12):
  *   EXACT  the identity; MLS  the MLS approximant D^[0,0] (Eq. vip:1). */
@@ -148,10 +160,17 @@ vip_status vip_set_flow(vip_ctx* ctx, int32_t geom, double Re, double dt);
 
 /* Krylov settings: precision VIP_PREC_*, relative residual tolerance
  * ||b - A x||_2 <= rtol ||b||_2 for both solves, iteration limit per solve,
- * identity VIP_IDENTITY_*.  Defaults MIXED, 1e-8, 20000, EXACT.
+ * identity VIP_IDENTITY_*.  Defaults FP64, 1e-8, 20000, EXACT.
  * The identity mode must be set before vip_build. */
 vip_status vip_set_solver(vip_ctx* ctx, int precision, double rtol, int32_t max_iters,
                           int identity);
+
+/* Inner tolerance of the MIXED form's refinement loop (not in the paper; the
+ * solves of Eqs. 12-13 stop at the same FP64 residual whatever it is): each FP32
+ * BiCGSTAB pass stops when its recursive residual has fallen to inner_rtol times
+ * the FP64 residual it started from (or to rtol ||b|| / 2).  inner_rtol in
+ * (0, 1); default 1e-3.  VIP_ERR_ARG otherwise. */
+vip_status vip_set_refinement(vip_ctx* ctx, double inner_rtol);
 
 /* Build everything that depends only on the geometry and flow parameters:
  * neighbour search (nodes, VIPs, normal auxiliary points), MLS moment

@@ -307,7 +307,8 @@ vip_status vip_autotune(vip_ctx* c, const float* omegas, int32_t nomega, const f
 
 vip_status vip_set_solver(vip_ctx* c, int precision, double rtol, int32_t max_iters, int identity) {
     if (!c) return VIP_ERR_ARG;
-    if (precision != VIP_PREC_FP64 && precision != VIP_PREC_MIXED) return fail(c, VIP_ERR_ARG, "bad precision");
+    if (precision != VIP_PREC_FP64 && precision != VIP_PREC_MIXED && precision != VIP_PREC_MG32)
+        return fail(c, VIP_ERR_ARG, "bad precision");
     if (!(rtol > 0.0) || !(rtol < 1.0)) return fail(c, VIP_ERR_ARG, "rtol must be in (0, 1)");
     if (max_iters < 1) return fail(c, VIP_ERR_ARG, "max_iters must be >= 1");
     if (identity != VIP_IDENTITY_EXACT && identity != VIP_IDENTITY_MLS) return fail(c, VIP_ERR_ARG, "bad identity");
@@ -319,6 +320,17 @@ vip_status vip_set_solver(vip_ctx* c, int precision, double rtol, int32_t max_it
     c->rtol = rtol;
     c->max_iters = max_iters;
     c->identity = identity;
+    return VIP_OK;
+}
+
+vip_status vip_set_refinement(vip_ctx* c, double inner_rtol) {
+    if (!c) return VIP_ERR_ARG;
+    if (!(inner_rtol > 0.0) || !(inner_rtol < 1.0)) return fail(c, VIP_ERR_ARG, "inner_rtol must be in (0, 1)");
+    if (inner_rtol != c->inner_rtol && c->graph) {  // the step graph holds the launch arguments
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    c->inner_rtol = inner_rtol;
     return VIP_OK;
 }
 
@@ -821,7 +833,8 @@ vip_status vip_solve(vip_ctx* c, int which, const double* b, double* x, int prec
     if (!c->built) return fail(c, VIP_ERR_ARG, "vip_solve before vip_build");
     if (which != VIP_OP_HELM_U && which != VIP_OP_HELM_V && which != VIP_OP_POISSON)
         return fail(c, VIP_ERR_ARG, "vip_solve: system must be HELM_U, HELM_V or POISSON");
-    if (precision != VIP_PREC_FP64 && precision != VIP_PREC_MIXED) return fail(c, VIP_ERR_ARG, "bad precision");
+    if (precision != VIP_PREC_FP64 && precision != VIP_PREC_MIXED && precision != VIP_PREC_MG32)
+        return fail(c, VIP_ERR_ARG, "bad precision");
     if (!(rtol > 0.0)) return fail(c, VIP_ERR_ARG, "bad rtol");
     const int64_t R = c->R;
     bool pois = which == VIP_OP_POISSON;

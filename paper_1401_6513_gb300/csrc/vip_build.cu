@@ -601,6 +601,17 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
     if (i < n) b[i] = (float)a[i];
 }
 
+// FP64 row sums of a SELL table (entries in stored order), rounded to FP32: the
+// row sums of the FP32 differenced row form (see Sell::rs32).
+__global__ void k_sell_rowsum(Sell A, float* __restrict__ rs) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= A.nrows) return;
+    const int64_t base = A.sptr[r >> 5] + (r & 31);
+    double s = 0.0;
+    for (int k = 0; k < A.rowlen[r]; ++k) s += A.v64[base + (int64_t)k * SLICE];
+    rs[r] = (float)s;
+}
+
 // Uniform slices of a SELL table (see Sell): one warp per slice decides whether all
 // 32 rows hold the same stencil and writes its entry count (0 if not).
 __global__ void k_sell_uniform(Sell A, int64_t* __restrict__ usize) {
@@ -717,6 +728,8 @@ static vip_status build_table(vip_ctx* c, const AsmArgs& A, int tb, int64_t nrow
     if (f32) {  // the Krylov operators: FP32 copy and uniform slices
         VIP_CUDA(dalloc(c, &S.v32, S.nstored));
         k_to_f32<<<(unsigned)((S.nstored + TB - 1) / TB), TB, 0, st>>>(S.v64, S.v32, S.nstored);
+        VIP_CUDA(dalloc(c, &S.rs32, nrows));
+        k_sell_rowsum<<<(unsigned)((nrows + TB - 1) / TB), TB, 0, st>>>(S, S.rs32);
         VIP_CUDA(cudaGetLastError());
         return sell_uniform(c, S);
     }

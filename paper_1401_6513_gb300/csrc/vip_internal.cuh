@@ -39,6 +39,9 @@ struct Sell {
     int32_t* col = nullptr;       // [nstored]
     double* v64 = nullptr;        // [nstored]
     float* v32 = nullptr;         // [nstored] (only for Krylov operators)
+    // Krylov operators: FP64 row sums sum_k a_rk rounded to FP32, for rows applied
+    // in FP32 in differenced form, sum_k a_rk (x_k - x_r) + rowsum_r x_r
+    float* rs32 = nullptr;        // [nrows]
     // Uniform slices (Krylov operators only): a slice whose 32 rows hold the same
     // stencil (entry k has the same value, bit for bit, in every row, and a column
     // that is the row plus the same offset in every row or the same column in every
@@ -141,7 +144,7 @@ struct vip_ctx {
     int weight = VIP_W_CUBIC_SPLINE;
     double support = 2.2;
     int basis_order = 2;
-    int precision = VIP_PREC_MIXED;
+    int precision = VIP_PREC_FP64;
     double rtol = 1e-8;
     int32_t max_iters = 20000;
     int identity = VIP_IDENTITY_EXACT;

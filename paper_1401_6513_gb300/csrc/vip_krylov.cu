@@ -1,23 +1,34 @@
 // Krylov solves of Eqs. (12) and (13): one persistent cooperative launch solves a
 // batch of independent sparse systems (block-diagonal SELL-32 operator, each
-// system a contiguous range of slices) with unpreconditioned BiCGSTAB
-// (van der Vorst, 1992) inside an FP64 iterative-refinement loop:
+// system a contiguous range of slices) with BiCGSTAB (van der Vorst, 1992),
+// right-preconditioned by one V-cycle of the aggregation multigrid for Eq. (13),
+// inside an FP64 iterative-refinement loop:
 //
 //   repeat:  r = b - A x   (FP64 operator, FP64 vectors);  stop if ||r|| <= rtol ||b||
 //            solve A d = r by BiCGSTAB in precision T from d = 0 with r_hat = r,
 //            until ||r_d|| <= tol_in, or until |r_hat.r| or |r_hat.v| falls below
-//            1e-12 of its norms (restart);   x += d
+//            a small fraction of its norms (restart);   x += d
 //
-// T = double gives the plain FP64 form (tol_in = rtol ||b|| / 2); T = float gives
-// the mixed form (FP32 operator copy and FP32 vectors inside, tol_in =
-// max(inner_rtol ||r||, rtol ||b|| / 2)).
+// Two precisions: T for the Krylov vectors, operator applications and vector
+// updates, TM for the V-cycle (its vectors, operators and arithmetic).
+//   <double, double>  the plain FP64 form (tol_in = rtol ||b|| / 2: one pass);
+//   <float, float>    the mixed form: FP32 arithmetic on FP32 copies of the
+//                     operators and FP32 vectors inside, tol_in =
+//                     max(inner_rtol ||r||, rtol ||b|| / 2), the correction d
+//                     accumulated in FP64;
+//   <double, float>   FP64 Krylov iteration with an FP32 V-cycle.
+// FP32 applications of the fine operator use the differenced row form
+// sum_k a_ik (x_k - x_i) + rowsum_i x_i with the FP64 row sum rounded to FP32: on
+// the smooth vectors of a Poisson solve x_k - x_i is small and exact, so the
+// large, nearly cancelling products a_ik x_k of the plain form never appear.
 //
 // Every system keeps its own scalars; all systems advance in lock step, and the
 // slices of the systems still iterating are re-spread over all blocks whenever a
-// system finishes.  Dot products are reduced deterministically: warp
-// shuffles, per-warp partials summed in warp order, per-block partials summed in
-// block order by every block, so all blocks hold identical scalars.  Blocks
-// meet at a grid barrier whose wait is bounded (2 s, then VIP_ERR_TIMEOUT).
+// system finishes.  Dot products are reduced deterministically: per-lane sums in
+// registers, warp shuffles, per-warp partials summed in warp order, per-block
+// partials summed in block order by every block, so all blocks hold identical
+// scalars.  Blocks meet at a grid barrier whose wait is bounded (2 s, then
+// VIP_ERR_TIMEOUT).
 #include <cstdio>
 #include <cstring>
 #include <type_traits>
@@ -84,17 +95,20 @@ __device__ bool grid_sync(uint32_t* bar, unsigned nblocks, int32_t* status) {
     return s_ok != 0;
 }
 
-template <class T>
+template <class T, class TM>
 struct KArgs {
     const int64_t* sptr;
     const int32_t* width;
     const int32_t* col;
-    const double* a64;
-    const T* aT;
+    const double* a64;      // FP64 operator (refinement residual)
+    const T* aT;            // the operator in T (Krylov applications)
+    const TM* aM;           // the operator in TM (the V-cycle's fine level)
     const int64_t* ucptr;   // uniform slices (null: none)
     const int32_t* ucode;
     const double* u64;
     const T* uT;
+    const TM* uM;
+    const float* rs32;      // FP64 row sums rounded to FP32 (FP32 differenced rows)
     const int32_t* slice_sys;
     const int32_t* blk_s0;
     const int32_t* blk_s1;
@@ -109,7 +123,8 @@ struct KArgs {
     int nsys;
     const double* b;
     double* x;
-    T *r, *rhat, *p, *v, *s, *t, *dx;
+    double* dx;          // the pass's correction, accumulated in FP64
+    T *r, *rhat, *p, *v, *s, *t;
     double rtol, inner_rtol;
     int max_iters, max_outer, max_pass;
     int32_t* out_iters;
@@ -118,7 +133,7 @@ struct KArgs {
     int32_t* out_status;
     int32_t* status;
     int use_mg;          // right preconditioning by one multigrid V-cycle
-    MgDev<T> mg;
+    MgDev<TM> mg;
     T *phat, *shat;      // M^{-1} p and M^{-1} s (alias p and s without a preconditioner)
 };
 
@@ -133,7 +148,16 @@ struct SysState {
     double r0_in;      // ||r|| at the start of the pass
     int pass_cap;      // iteration cap of the current pass (halved after a discarded pass)
     int iters, outer, pass_iters, status;
+    float alpha_f, omega_f, beta_f;  // the scalars rounded to FP32 (FP32 vector updates)
 };
+
+// the scalar of precision T: the FP64 value, or its FP32 rounding
+template <class T>
+__device__ __forceinline__ T sc(double d, float f);
+template <>
+__device__ __forceinline__ double sc<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float sc<float>(double, float f) { return f; }
 
 // A reduced value is usable if finite.
 __device__ __forceinline__ bool fin(double v) { return isfinite(v); }
@@ -152,27 +176,31 @@ template <class T>
 __device__ __forceinline__ T ldm(const T* p) { return __ldcs(p); }
 
 // warp sum (fixed butterfly order)
-__device__ __forceinline__ double wsum(double v) {
+template <class V>
+__device__ __forceinline__ V wsum(V v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
 // sum_k A[row, k] f(col[row, k]) over the SELL entries of one row (lane of the
-// slice's warp), in entry order.  The column indices and values of U entries are
-// loaded before their U gathers, so each warp keeps several loads in flight.  A
-// uniform slice (ucptr[sl] >= 0, warp-uniform) reads its single stored stencil
-// instead (the same values and columns, so the same sum): one broadcast load per
-// entry for the whole warp in place of 32 value and 32 column loads.
-template <int U, class TA, class F>
-__device__ __forceinline__ double sell_row(const int64_t* __restrict__ sptr,
-                                           const int32_t* __restrict__ width,
-                                           const int32_t* __restrict__ col, const TA* __restrict__ A,
-                                           const int64_t* __restrict__ ucptr,
-                                           const int32_t* __restrict__ ucode,
-                                           const TA* __restrict__ uA, int64_t sl, int lane, F&& f) {
+// slice's warp), in entry order, in precision TA.  DIFF: the differenced form
+// sum_k A[row, k] (f(col) - xi) + rs xi, xi the row's own value and rs its row
+// sum (FP32 applications of the fine operator).  The column indices and values of
+// U entries are loaded before their U gathers, so each warp keeps several loads in
+// flight.  A uniform slice (ucptr[sl] >= 0, warp-uniform) reads its single stored
+// stencil instead (the same values and columns, so the same sum): one broadcast
+// load per entry for the whole warp in place of 32 value and 32 column loads.
+template <int U, bool DIFF, class TA, class F>
+__device__ __forceinline__ TA sell_row(const int64_t* __restrict__ sptr,
+                                       const int32_t* __restrict__ width,
+                                       const int32_t* __restrict__ col, const TA* __restrict__ A,
+                                       const int64_t* __restrict__ ucptr,
+                                       const int32_t* __restrict__ ucode,
+                                       const TA* __restrict__ uA, int64_t sl, int lane, TA xi, TA rs,
+                                       F&& f) {
     const int w = __ldg(width + sl);
-    double sum = 0.0;
+    TA sum = (TA)0;
     int k = 0;
     const int64_t up = ucptr ? __ldg(ucptr + sl) : -1;
     if (up >= 0) {
@@ -181,43 +209,55 @@ __device__ __forceinline__ double sell_row(const int64_t* __restrict__ sptr,
         const TA* ua = uA + up;
         for (; k + U <= w; k += U) {
             int c[U];
-            double av[U], xv[U];
+            TA av[U], xv[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int32_t code = __ldg(uc + k + u);
                 c[u] = (code & 1) ? (code >> 1) : row + (code >> 1);
-                av[u] = (double)__ldg(ua + k + u);
+                av[u] = __ldg(ua + k + u);
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) xv[u] = f(c[u]);
+            for (int u = 0; u < U; ++u) {
+                xv[u] = f(c[u]);
+                if (DIFF) xv[u] -= xi;
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) sum += av[u] * xv[u];
         }
         for (; k < w; ++k) {
             const int32_t code = __ldg(uc + k);
-            sum += (double)__ldg(ua + k) * f((code & 1) ? (code >> 1) : row + (code >> 1));
+            TA xk = f((code & 1) ? (code >> 1) : row + (code >> 1));
+            if (DIFF) xk -= xi;
+            sum += __ldg(ua + k) * xk;
         }
+        if (DIFF) sum += rs * xi;
         return sum;
     }
     const int64_t base = __ldg(sptr + sl) + lane;
     for (; k + U <= w; k += U) {
         int c[U];
-        double av[U], xv[U];
+        TA av[U], xv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t e = base + (int64_t)(k + u) * SLICE;
             c[u] = ldm(col + e);
-            av[u] = (double)ldm(A + e);
+            av[u] = ldm(A + e);
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = f(c[u]);
+        for (int u = 0; u < U; ++u) {
+            xv[u] = f(c[u]);
+            if (DIFF) xv[u] -= xi;
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) sum += av[u] * xv[u];
     }
     for (; k < w; ++k) {
         const int64_t e = base + (int64_t)k * SLICE;
-        sum += (double)ldm(A + e) * f(ldm(col + e));
+        TA xk = f(ldm(col + e));
+        if (DIFF) xk -= xi;
+        sum += ldm(A + e) * xk;
     }
+    if (DIFF) sum += rs * xi;
     return sum;
 }
 
@@ -327,15 +367,18 @@ __device__ __noinline__ void partition_update(Partition& P, const SysState* S, i
     }
 }
 
-template <class T>
-__global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
+template <class T, class TM>
+__global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
     // |r_hat . r| below this fraction of ||r_hat|| ||r|| is rounding noise in T
     // (FP32 vectors of ~1e6 rows: ~6e-8 / sqrt(n) relative noise in a dot product)
     const double bd_tol = sizeof(T) == 8 ? 1e-14 : 1e-9;
+    constexpr bool K32 = std::is_same_v<T, float>;   // FP32 Krylov iteration
+    constexpr bool M32 = std::is_same_v<TM, float>;  // FP32 V-cycle
     __shared__ double sacc[KWARPS][MAXSYS_PB][NQ];
     __shared__ double stot[MAXSYS][NQ];
     __shared__ SysState S[MAXSYS];
-    extern __shared__ double s_tile[];  // multigrid: a coarse tile and its halo, 36 x 36
+    extern __shared__ double s_tile_raw[];  // multigrid: a coarse tile and its halo, 36 x 36
+    TM* s_tile = reinterpret_cast<TM*>(s_tile_raw);
     __shared__ int s_any;
     __shared__ Partition P;  // this block's share of the work
     const int bid = blockIdx.x;
@@ -388,26 +431,34 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     // warp's rows of one system and reduced across the warp once per phase (the
     // FP64 butterfly is costly on this GPU's FP64 pipe); a warp whose slices change
     // system flushes at the change.  The order is fixed, so sums are deterministic.
+    // Contributions in T go to qacck (FP32 per-lane sums in the FP32 iteration,
+    // widened once per flush), FP64 ones (refinement residual) to qacc.
     double qacc[NQ];
+    T qacck[NQ];
     int qj = -1, qg = -1;
     auto flush_acc = [&](int nq) {  // warp-uniform
         if (qj >= 0)
             for (int k = 0; k < nq; ++k) {
-                const double w = wsum(qacc[k]);
+                const double w = wsum(qacc[k] + (double)qacck[k]);
                 if (lane == 0) sacc[warp][qj][k] += w;
             }
         qj = -1;
         qg = -1;
     };
     // accumulate a row's contributions q[0..nq) for system g (warp-uniform g)
-    auto acc = [&](int g, int nq, const double* q) {
+    auto acc = [&](int g, int nq, const auto* q) {
+        using Q = std::remove_cv_t<std::remove_pointer_t<decltype(q)>>;
         if (g != qg) {
             flush_acc(nq);
             qg = g;
             qj = P.j[g];
-            for (int k = 0; k < nq; ++k) qacc[k] = 0.0;
+            for (int k = 0; k < nq; ++k) { qacc[k] = 0.0; qacck[k] = (T)0; }
         }
-        for (int k = 0; k < nq; ++k) qacc[k] += q[k];
+        if constexpr (std::is_same_v<Q, double>) {
+            for (int k = 0; k < nq; ++k) qacc[k] += q[k];
+        } else {
+            for (int k = 0; k < nq; ++k) qacck[k] += q[k];
+        }
     };
     // block partials -> global, barrier, totals of every system -> stot.
     // Layout partial[(g * NQ + k) * nb + block]: the blocks of one system are a
@@ -449,14 +500,32 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
         __syncthreads();
         return s_any != 0;
     };
-    // y_row = sum_k A[row,k] * vec[col] for the warp's slice (lane = row)
-    auto spmv_row = [&](int64_t sl, const auto* A, const auto* vec) -> double {
-        using TA = std::remove_cv_t<std::remove_pointer_t<decltype(A)>>;
-        const TA* uA;
-        if constexpr (std::is_same_v<TA, double>) uA = a.u64;
-        else uA = a.uT;
-        return sell_row<4>(a.sptr, a.width, a.col, A, a.ucptr, a.ucode, uA, sl, lane,
-                           [&](int j) { return (double)ldv(vec + j); });
+    // (A vec)_row for the warp's slice (lane = row): FP64 with the FP64 operator; in
+    // the Krylov precision T; in the V-cycle's precision TM (FP32: differenced rows)
+    auto spmv64 = [&](int64_t sl, const double* vec) -> double {
+        return sell_row<4, false, double>(a.sptr, a.width, a.col, a.a64, a.ucptr, a.ucode, a.u64, sl,
+                                          lane, 0.0, 0.0, [&](int j) { return ldv(vec + j); });
+    };
+    auto spmvK = [&](int64_t sl, const T* vec) -> T {
+        if constexpr (K32) {
+            const int64_t row = sl * 32 + lane;
+            return sell_row<4, true, float>(a.sptr, a.width, a.col, a.aT, a.ucptr, a.ucode, a.uT, sl,
+                                            lane, ldv(vec + row), __ldg(a.rs32 + row),
+                                            [&](int j) { return ldv(vec + j); });
+        } else {
+            return spmv64(sl, vec);
+        }
+    };
+    auto spmvM = [&](int64_t sl, const TM* vec) -> TM {
+        if constexpr (M32) {
+            const int64_t row = sl * 32 + lane;
+            return sell_row<4, true, float>(a.sptr, a.width, a.col, a.aM, a.ucptr, a.ucode, a.uM, sl,
+                                            lane, ldv(vec + row), __ldg(a.rs32 + row),
+                                            [&](int j) { return ldv(vec + j); });
+        } else {
+            return sell_row<4, false, double>(a.sptr, a.width, a.col, a.aM, a.ucptr, a.ucode, a.uM, sl,
+                                              lane, 0.0, 0.0, [&](int j) { return ldv(vec + j); });
+        }
     };
 
     // One V-cycle z = M^{-1} v of the aggregation multigrid: a V(1,1)-cycle with
@@ -484,16 +553,16 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     // Only rows of systems still in their inner pass are touched on the fine level.
     const int64_t gtid = (int64_t)blockIdx.x * KTHREADS + threadIdx.x;
     const int64_t gstride = (int64_t)nb * KTHREADS;
-    const double mcorr = (double)a.mg.corr;
+    const TM mcorr = (TM)a.mg.corr;
     // s_tile[36 r + c] = f(cell, x, y) for the 32 x th tile at (x0, y0) and its halo (0
     // outside a non-periodic lattice; periodic directions wrap)
     auto stage = [&](const MgLevGeom& q, int x0, int y0, int th, auto&& f) {
-        double v[2];
+        TM v[2];
         const int nst = 36 * (th + 4);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = threadIdx.x + h * KTHREADS;
-            v[h] = 0.0;
+            v[h] = (TM)0;
             if (k < nst) {
                 int xx = x0 - 2 + k % 36, yy = y0 - 2 + k / 36;
                 bool ok = true;
@@ -511,9 +580,9 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     // sum_o A_l[c, o] s_tile[36 (warp + dy) + lane + dx] for the thread's cell c, in offset
     // order; a warp whose slices hold no nonzero outside the 3 x 3 core (wide false,
     // warp-uniform) skips the zero products, which leaves the sum unchanged
-    auto stencil = [&](int l, int64_t c, bool wide) -> double {
-        const double* cp = a.mg.coefs[l] + (c >> 5) * 800 + (c & 31);
-        double acc = 0.0;
+    auto stencil = [&](int l, int64_t c, bool wide) -> TM {
+        const TM* cp = a.mg.coefs[l] + (c >> 5) * 800 + (c & 31);
+        TM acc = (TM)0;
         if (wide) {
 #pragma unroll
             for (int o = 0; o < 25; ++o) acc += ldm(cp + o * 32) * s_tile[(warp + o / 5) * 36 + lane + o % 5];
@@ -528,43 +597,43 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
     };
     // z = M^{-1} v, given v and f = w Df^{-1} v on the rows of active systems
     auto vcycle = [&](const T* v, T* z) -> bool {
-        const MgDev<T>& M = a.mg;
+        const MgDev<TM>& M = a.mg;
         const int L = M.nlev;
         for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
             const int sl = vslice(iv, sg);
             const int g = a.slice_sys[sl];
             const int64_t row = (int64_t)sl * 32 + lane;
-            T res = (T)0;
-            if (S[g].inner_active) res = (T)((double)ldv(v + row) - spmv_row(sl, a.aT, M.fx));
+            TM res = (TM)0;
+            if (S[g].inner_active) res = (TM)ldv(v + row) - spmvM(sl, M.fx);
             M.fr[row] = res;
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int64_t c = gtid; c < M.n[1]; c += gstride) {
-            double sum = 0.0;
+            TM sum = (TM)0;
             const int64_t q1 = __ldg(M.cptr + c + 1);
-            for (int64_t q = __ldg(M.cptr + c); q < q1; ++q) sum += (double)ldv(M.fr + __ldg(M.crow + q));
-            M.b[1][c] = (T)sum;
+            for (int64_t q = __ldg(M.cptr + c); q < q1; ++q) sum += ldv(M.fr + __ldg(M.crow + q));
+            M.b[1][c] = sum;
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int l = 1; l < L; ++l) {
-            const T* bl = M.b[l];
-            const double* wdl = M.wdinv[l];
+            const TM* bl = M.b[l];
+            const TM* wdl = M.wdinv[l];
             const int th = M.th[l];
             for (int64_t t = blockIdx.x; t < M.ntiles[l]; t += nb) {
                 const MgTile tile = M.tiles[l][t];
                 if (!S[tile.g].inner_active) continue;  // that geometry's solve is done
                 const MgLevGeom q = M.lg[l][tile.g];
                 __syncthreads();  // the previous tile's reads of s_tile are done
-                stage(q, tile.x0, tile.y0, th, [&](int64_t j, int, int) {
-                    return __ldg(wdl + j) * (double)ldv(bl + j);
+                stage(q, tile.x0, tile.y0, th, [&](int64_t j, int, int) -> TM {
+                    return __ldg(wdl + j) * ldv(bl + j);
                 });
                 __syncthreads();
                 const int x = tile.x0 + lane, y = tile.y0 + warp;
                 const bool in = warp < th && x < q.nx && y < q.ny;
                 const int64_t c = q.off + (int64_t)y * q.sx + x;
                 const bool wide = __any_sync(0xffffffffu, in && __ldg(M.ring[l] + (c >> 5)));
-                double r = 0.0;
-                if (in) r = (double)ldv(bl + c) - stencil(l, c, wide);
+                TM r = (TM)0;
+                if (in) r = ldv(bl + c) - stencil(l, c, wide);
                 __syncthreads();
                 if (warp < th) s_tile[warp * 32 + lane] = r;
                 __syncthreads();
@@ -573,10 +642,10 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                     const MgLevGeom qp = M.lg[l + 1][tile.g];
                     const int X = (tile.x0 >> 1) + px, Y = (tile.y0 >> 1) + py;
                     if (X < qp.nx && Y < qp.ny) {
-                        const double* rs = s_tile;
+                        const TM* rs = s_tile;
                         const int k0 = (2 * py) * 32 + 2 * px;
                         M.b[l + 1][qp.off + (int64_t)Y * qp.sx + X] =
-                            (T)((rs[k0] + rs[k0 + 1]) + (rs[k0 + 32] + rs[k0 + 33]));
+                            (rs[k0] + rs[k0 + 1]) + (rs[k0 + 32] + rs[k0 + 33]);
                     }
                 }
             }
@@ -597,18 +666,18 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             const int64_t m = (int64_t)q.nx * q.ny;
             const int64_t i = c - q.off;
             if (i >= m || !S[lo].inner_active) continue;  // padding, or a finished geometry (warp-uniform)
-            const double* Ai = M.cinv + __ldg(M.cinv_off + lo) + i * m;
-            const T* bL = M.b[L] + q.off;
-            double sum = 0.0;
-            for (int64_t j = lane; j < m; j += 32) sum += __ldg(Ai + j) * (double)ldv(bL + j);
+            const TM* Ai = M.cinv + __ldg(M.cinv_off + lo) + i * m;
+            const TM* bL = M.b[L] + q.off;
+            TM sum = (TM)0;
+            for (int64_t j = lane; j < m; j += 32) sum += __ldg(Ai + j) * ldv(bL + j);
             sum = wsum(sum);
-            if (lane == 0) M.x[L][c] = (T)sum;
+            if (lane == 0) M.x[L][c] = sum;
         }
         if (!grid_sync(a.bar, nb, a.status)) return false;
         for (int l = L - 1; l >= 1; --l) {
-            const T* sol = (l + 1 == L) ? M.x[L] : M.y[l + 1];
-            const T* bl = M.b[l];
-            const double* wdl = M.wdinv[l];
+            const TM* sol = (l + 1 == L) ? M.x[L] : M.y[l + 1];
+            const TM* bl = M.b[l];
+            const TM* wdl = M.wdinv[l];
             const int th = M.th[l];
             for (int64_t t = blockIdx.x; t < M.ntiles[l]; t += nb) {
                 const MgTile tile = M.tiles[l][t];
@@ -616,9 +685,9 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 const MgLevGeom q = M.lg[l][tile.g];
                 const MgLevGeom qp = M.lg[l + 1][tile.g];
                 __syncthreads();
-                stage(q, tile.x0, tile.y0, th, [&](int64_t j, int xx, int yy) {
-                    return __ldg(wdl + j) * (double)ldv(bl + j) +
-                           mcorr * (double)ldv(sol + qp.off + (int64_t)(yy >> 1) * qp.sx + (xx >> 1));
+                stage(q, tile.x0, tile.y0, th, [&](int64_t j, int xx, int yy) -> TM {
+                    return __ldg(wdl + j) * ldv(bl + j) +
+                           mcorr * ldv(sol + qp.off + (int64_t)(yy >> 1) * qp.sx + (xx >> 1));
                 });
                 __syncthreads();
                 const int x = tile.x0 + lane, y = tile.y0 + warp;
@@ -626,15 +695,15 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 const int64_t c = q.off + (int64_t)y * q.sx + x;
                 const bool wide = __any_sync(0xffffffffu, in && __ldg(M.ring[l] + (c >> 5)));
                 if (in) {
-                    const double r = (double)ldv(bl + c) - stencil(l, c, wide);
-                    const T y = (T)(s_tile[(warp + 2) * 36 + lane + 2] + __ldg(wdl + c) * r);
+                    const TM r = ldv(bl + c) - stencil(l, c, wide);
+                    const TM y = s_tile[(warp + 2) * 36 + lane + 2] + __ldg(wdl + c) * r;
                     if (l > 1) {
                         M.y[l][c] = y;
                     } else {  // fine prolongation f += corr y_1 over the cell's rows
                         const int64_t q1 = __ldg(M.cptr + c + 1);
                         for (int64_t qq = __ldg(M.cptr + c); qq < q1; ++qq) {
                             const int32_t row = __ldg(M.crow + qq);
-                            M.fx[row] = (T)((double)ldv(M.fx + row) + mcorr * (double)y);
+                            M.fx[row] = ldv(M.fx + row) + mcorr * y;
                         }
                     }
                 }
@@ -644,13 +713,13 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
         // fine prolongation f += corr s_1(agg) when level 1 is the coarsest; otherwise
         // the level-1 pass above did it
         if (L == 1) {
-            const T* sol1 = M.x[1];
+            const TM* sol1 = M.x[1];
             for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
                 if (!S[a.slice_sys[sl]].inner_active) continue;
                 const int64_t rw = (int64_t)sl * 32 + lane;
                 const int32_t cc = __ldg(M.agg + rw);
-                if (cc >= 0) M.fx[rw] = (T)((double)ldv(M.fx + rw) + mcorr * (double)ldv(sol1 + cc));
+                if (cc >= 0) M.fx[rw] = ldv(M.fx + rw) + mcorr * ldv(sol1 + cc);
             }
             if (!grid_sync(a.bar, nb, a.status)) return false;
         }
@@ -659,8 +728,8 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             const int g = a.slice_sys[sl];
             if (!S[g].inner_active) continue;
             const int64_t row = (int64_t)sl * 32 + lane;
-            const double r = (double)ldv(v + row) - spmv_row(sl, a.aT, M.fx);
-            z[row] = (T)((double)ldv(M.fx + row) + __ldg(M.fwdinv + row) * r);
+            const TM r = (TM)ldv(v + row) - spmvM(sl, M.fx);
+            z[row] = (T)(ldv(M.fx + row) + __ldg(M.fwdinv + row) * r);
         }
         return grid_sync(a.bar, nb, a.status);
     };
@@ -672,6 +741,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
         st.outer_active = 1; st.inner_active = 0; st.s_conv = 0; st.zero_x = 0;
         st.pass_bad = 0; st.bad_passes = 0; st.r0_in = 0; st.pass_cap = a.max_pass;
         st.iters = 0; st.outer = 0; st.pass_iters = 0; st.status = 0;
+        st.alpha_f = st.omega_f = 1.0f; st.beta_f = 0.0f;
     }
     __syncthreads();
 
@@ -686,7 +756,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 int64_t row = (int64_t)sl * 32 + lane;
                 if (S[g].zero_x) a.x[row] = 0.0;
                 else if (S[g].outer_active && !S[g].pass_bad)
-                    a.x[row] = __ldcg(a.x + row) + (double)ldv(a.dx + row);
+                    a.x[row] = __ldcg(a.x + row) + ldv(a.dx + row);
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
         }
@@ -698,13 +768,13 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             if (!S[g].outer_active) continue;
             int64_t row = (int64_t)sl * 32 + lane;
             double bi = __ldg(a.b + row);
-            double ri = bi - spmv_row(sl, a.a64, a.x);
+            double ri = bi - spmv64(sl, a.x);
             T rt = (T)ri;
             a.r[row] = rt;
             a.rhat[row] = rt;
             a.p[row] = (T)0;
             a.v[row] = (T)0;
-            a.dx[row] = (T)0;
+            a.dx[row] = 0.0;
             double q[3] = {ri * ri, bi * bi, (double)rt * (double)rt};
             acc(g, 3, q);
         }
@@ -741,6 +811,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                         st.rhat_norm = sqrt(st.rho);
                         st.r0_in = st.rhat_norm;
                         st.rho_old = st.alpha = st.omega = 1.0;
+                        st.alpha_f = st.omega_f = 1.0f;
                         st.bad_passes = st.pass_bad ? st.bad_passes + 1 : 0;
                         st.pass_cap = st.pass_bad ? max(st.pass_iters / 2, 20)
                                                   : min(2 * st.pass_cap, a.max_pass);
@@ -776,7 +847,10 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
             // A: beta, p = r + beta (p - omega v)
             if (threadIdx.x < nsys) {
                 SysState& st = S[threadIdx.x];
-                if (st.inner_active) st.beta = (st.rho / st.rho_old) * (st.alpha / st.omega);
+                if (st.inner_active) {
+                    st.beta = (st.rho / st.rho_old) * (st.alpha / st.omega);
+                    st.beta_f = (float)st.beta;
+                }
             }
             __syncthreads();
             for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
@@ -784,10 +858,10 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
-                double pn = (double)ldv(a.r + row) +
-                            S[g].beta * ((double)ldv(a.p + row) - S[g].omega * (double)ldv(a.v + row));
-                a.p[row] = (T)pn;
-                if (a.use_mg) a.mg.fx[row] = (T)(__ldg(a.mg.fwdinv + row) * (double)(T)pn);
+                const T be = sc<T>(S[g].beta, S[g].beta_f), om = sc<T>(S[g].omega, S[g].omega_f);
+                const T pn = ldv(a.r + row) + be * (ldv(a.p + row) - om * ldv(a.v + row));
+                a.p[row] = pn;
+                if (a.use_mg) a.mg.fx[row] = __ldg(a.mg.fwdinv + row) * (TM)pn;
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
             if (a.use_mg && !vcycle(a.p, a.phat)) { alive = false; break; }
@@ -798,9 +872,9 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
-                double vi = spmv_row(sl, a.aT, a.phat);
-                a.v[row] = (T)vi;
-                double q[2] = {(double)ldv(a.rhat + row) * (double)(T)vi, (double)(T)vi * (double)(T)vi};
+                const T vi = spmvK(sl, a.phat);
+                a.v[row] = vi;
+                const T q[2] = {ldv(a.rhat + row) * vi, vi * vi};
                 acc(g, 2, q);
             }
             if (!reduce(2)) { alive = false; break; }
@@ -815,6 +889,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                         st.inner_active = 0;  // restart from the current x
                     } else {
                         st.alpha = st.rho / rv;
+                        st.alpha_f = (float)st.alpha;
                     }
                 }
             }
@@ -825,9 +900,9 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
-                const T si = (T)((double)ldv(a.r + row) - S[g].alpha * (double)ldv(a.v + row));
+                const T si = ldv(a.r + row) - sc<T>(S[g].alpha, S[g].alpha_f) * ldv(a.v + row);
                 a.s[row] = si;
-                if (a.use_mg) a.mg.fx[row] = (T)(__ldg(a.mg.fwdinv + row) * (double)si);
+                if (a.use_mg) a.mg.fx[row] = __ldg(a.mg.fwdinv + row) * (TM)si;
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
             if (a.use_mg && !vcycle(a.s, a.shat)) { alive = false; break; }
@@ -838,10 +913,10 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
-                T ti = (T)spmv_row(sl, a.aT, a.shat);
+                const T ti = spmvK(sl, a.shat);
                 a.t[row] = ti;
-                double si = (double)ldv(a.s + row);
-                double q[3] = {(double)ti * si, (double)ti * (double)ti, si * si};
+                const T si = ldv(a.s + row);
+                const T q[3] = {ti * si, ti * ti, si * si};
                 acc(g, 3, q);
             }
             if (!reduce(3)) { alive = false; break; }
@@ -862,6 +937,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                     } else {
                         st.omega = ts / tt;
                     }
+                    st.omega_f = (float)st.omega;
                 }
             }
             __syncthreads();
@@ -872,14 +948,11 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T> a) {
                 int g = a.slice_sys[sl];
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
-                double al = S[g].alpha, om = S[g].omega;
-                double si = (double)ldv(a.s + row);
-                double d = (double)ldv(a.dx + row) + al * (double)ldv(a.phat + row) +
-                           om * (double)ldv(a.shat + row);
-                a.dx[row] = (T)d;
-                T rn = (T)(si - om * (double)ldv(a.t + row));
+                const double al = S[g].alpha, om = S[g].omega;
+                a.dx[row] = ldv(a.dx + row) + al * (double)ldv(a.phat + row) + om * (double)ldv(a.shat + row);
+                const T rn = ldv(a.s + row) - sc<T>(om, S[g].omega_f) * ldv(a.t + row);
                 a.r[row] = rn;
-                double q[2] = {(double)ldv(a.rhat + row) * (double)rn, (double)rn * (double)rn};
+                const T q[2] = {ldv(a.rhat + row) * rn, rn * rn};
                 acc(g, 2, q);
             }
             if (!reduce(2)) { alive = false; break; }
@@ -926,19 +999,22 @@ vip_status krylov_plan(vip_ctx* c, KrylovPlan& P, const Sell& A, const std::vect
         return VIP_ERR_ARG;
     }
     // the coarse tile lives in dynamic shared memory (above the static 48 KB limit
-    // together with the rest; set here, outside any graph capture)
-    VIP_CUDA(cudaFuncSetAttribute(k_bicgstab<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSMEM_DYN));
-    VIP_CUDA(cudaFuncSetAttribute(k_bicgstab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, KSMEM_DYN));
-    // as much L1 as possible for the vector gathers: the smallest shared-memory
-    // configuration that holds the block's ~51 KB
-    VIP_CUDA(cudaFuncSetAttribute(k_bicgstab<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  cudaSharedmemCarveoutMaxL1));
-    VIP_CUDA(cudaFuncSetAttribute(k_bicgstab<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  cudaSharedmemCarveoutMaxL1));
-    int occ64 = 0, occ32 = 0;
-    VIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_bicgstab<double>, KTHREADS, KSMEM_DYN));
-    VIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_bicgstab<float>, KTHREADS, KSMEM_DYN));
-    int occ = std::max(1, std::min(std::min(occ64, occ32), 1));
+    // together with the rest; set here, outside any graph capture); as much L1 as
+    // possible for the vector gathers: the smallest shared-memory configuration that
+    // holds the block's ~52 KB
+    int occ = 1;
+    {
+        const void* kern[] = {(const void*)k_bicgstab<double, double>, (const void*)k_bicgstab<float, float>,
+                              (const void*)k_bicgstab<double, float>};
+        for (const void* k : kern) {
+            VIP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, KSMEM_DYN));
+            VIP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          cudaSharedmemCarveoutMaxL1));
+            int o = 0;
+            VIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, KTHREADS, KSMEM_DYN));
+            if (o < 1) { c->err = "the Krylov kernel does not fit on an SM"; return VIP_ERR_CUDA; }
+        }
+    }
     const int64_t nsl = A.nslices;
     std::vector<int32_t> slice_sys(nsl, -1);
     for (int g = 0; g < nsys; ++g) {
@@ -1001,6 +1077,13 @@ vip_status krylov_plan(vip_ctx* c, KrylovPlan& P, const Sell& A, const std::vect
     return VIP_OK;
 }
 
+// the array of precision T: the FP64 one or its FP32 copy
+template <class T>
+static const T* pick(const double* d, const float* f) {
+    if constexpr (std::is_same_v<T, double>) return d;
+    else return f;
+}
+
 template <class T>
 static MgDev<T> mg_view(const Multigrid& M) {
     MgDev<T> d;
@@ -1008,7 +1091,7 @@ static MgDev<T> mg_view(const Multigrid& M) {
     d.nlev = M.nlev;
     d.ngeom = M.ngeom;
     d.agg = M.agg; d.cptr = M.cptr; d.crow = M.crow;
-    d.fwdinv = M.fwdinv;
+    d.fwdinv = pick<T>(M.fwdinv, M.fwdinv32);
     d.fr = (T*)M.fr; d.fx = (T*)M.fx;
     for (int l = 1; l <= M.nlev; ++l) {
         const MgLevel& v = M.lev[l];
@@ -1016,35 +1099,43 @@ static MgDev<T> mg_view(const Multigrid& M) {
         d.ntiles[l] = v.ntiles;
         d.lg[l] = v.lg;
         d.tiles[l] = v.tiles;
-        d.coefs[l] = v.coefs;
+        d.coefs[l] = pick<T>(v.coefs, v.coefs32);
         d.ring[l] = v.ring;
         d.th[l] = v.th;
-        d.wdinv[l] = v.wdinv;
+        d.wdinv[l] = pick<T>(v.wdinv, v.wdinv32);
         d.x[l] = (T*)v.x; d.b[l] = (T*)v.b; d.y[l] = (T*)v.y;
     }
     d.corr = M.corr;
-    d.cinv = M.cinv;
+    d.cinv = pick<T>(M.cinv, M.cinv32);
     d.cinv_off = M.cinv_off;
     return d;
 }
 
-template <class T>
+template <class T, class TM>
 static vip_status launch(vip_ctx* c, const KrylovPlan& P, const Sell& A, const double* b, double* x,
                          double rtol, int32_t max_iters, double inner_rtol, const Multigrid* mg) {
     KrylovWork& W = sizeof(T) == 8 ? c->work64 : c->work32;
-    if (W.n < A.nrows) { c->err = "Krylov workspace too small"; return VIP_ERR_ARG; }
-    KArgs<T> a;
+    if (W.n < A.nrows || c->work64.n < A.nrows) { c->err = "Krylov workspace too small"; return VIP_ERR_ARG; }
+    if ((sizeof(T) == 4 || sizeof(TM) == 4) && (!A.v32 || !A.rs32)) {
+        c->err = "operator has no FP32 copy";
+        return VIP_ERR_ARG;
+    }
+    KArgs<T, TM> a;
     a.sptr = A.sptr; a.width = A.width; a.col = A.col; a.a64 = A.v64;
-    a.aT = sizeof(T) == 8 ? (const T*)A.v64 : (const T*)A.v32;
+    a.aT = pick<T>(A.v64, A.v32);
+    a.aM = pick<TM>(A.v64, A.v32);
     a.ucptr = A.ucptr; a.ucode = A.ucode; a.u64 = A.uv64;
-    a.uT = sizeof(T) == 8 ? (const T*)A.uv64 : (const T*)A.uv32;
+    a.uT = pick<T>(A.uv64, A.uv32);
+    a.uM = pick<TM>(A.uv64, A.uv32);
+    a.rs32 = A.rs32;
     a.slice_sys = P.slice_sys; a.blk_s0 = P.blk_s0; a.blk_s1 = P.blk_s1; a.blk_g0 = P.blk_g0;
     a.blk_ng = P.blk_ng;
     a.sys_b0 = P.sys_b0; a.sys_b1 = P.sys_b1; a.partial = P.partial; a.bar = P.bar;
     a.sys_s0 = P.sys_s0; a.sys_s1 = P.sys_s1;
     a.nsys = P.nsys; a.b = b; a.x = x;
     a.r = (T*)W.r; a.rhat = (T*)W.rhat; a.p = (T*)W.p; a.v = (T*)W.v; a.s = (T*)W.s;
-    a.t = (T*)W.t; a.dx = (T*)W.dx;
+    a.t = (T*)W.t;
+    a.dx = (double*)c->work64.dx;  // the correction is accumulated in FP64 in every form
     a.rtol = rtol; a.inner_rtol = inner_rtol; a.max_iters = max_iters;
     // FP32 passes are re-anchored on the FP64 residual at least every 4000 iterations
     a.max_outer = 1000;
@@ -1053,7 +1144,7 @@ static vip_status launch(vip_ctx* c, const KrylovPlan& P, const Sell& A, const d
     a.out_status = P.out_status; a.status = c->d_status;
     a.use_mg = (mg && mg->built) ? 1 : 0;
     if (a.use_mg) {
-        a.mg = mg_view<T>(*mg);
+        a.mg = mg_view<TM>(*mg);
         a.phat = (T*)c->phat;
         a.shat = (T*)c->shat;
     } else {
@@ -1072,7 +1163,7 @@ static vip_status launch(vip_ctx* c, const KrylovPlan& P, const Sell& A, const d
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    VIP_CUDA(cudaLaunchKernelEx(&cfg, k_bicgstab<T>, a));
+    VIP_CUDA(cudaLaunchKernelEx(&cfg, k_bicgstab<T, TM>, a));
     return VIP_OK;
 }
 
@@ -1080,8 +1171,10 @@ vip_status krylov_solve(vip_ctx* c, const KrylovPlan& P, const Sell& A, const do
                         int precision, double rtol, int32_t max_iters, double inner_rtol,
                         const Multigrid* mg) {
     if (precision == VIP_PREC_MIXED)
-        return launch<float>(c, P, A, b, x, rtol, max_iters, inner_rtol, mg);
-    return launch<double>(c, P, A, b, x, rtol, max_iters, inner_rtol, mg);
+        return launch<float, float>(c, P, A, b, x, rtol, max_iters, inner_rtol, mg);
+    if (precision == VIP_PREC_MG32 && mg && mg->built)
+        return launch<double, float>(c, P, A, b, x, rtol, max_iters, inner_rtol, mg);
+    return launch<double, double>(c, P, A, b, x, rtol, max_iters, inner_rtol, mg);
 }
 
 }  // namespace vip

@@ -175,10 +175,21 @@ __global__ void k_mg_fine_diag(Sell A, double* __restrict__ dinv) {
     dinv[r] = s != 0.0 ? (d < 0.0 ? -1.0 : 1.0) / s : 0.0;
 }
 
-// w[i] = omega * d[i]
-__global__ void k_mg_scale(int64_t n, double omega, const double* __restrict__ d, double* __restrict__ w) {
+// w[i] = omega * d[i], and its FP32 rounding
+__global__ void k_mg_scale(int64_t n, double omega, const double* __restrict__ d, double* __restrict__ w,
+                           float* __restrict__ w32) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) w[i] = omega * d[i];
+    if (i < n) {
+        const double v = omega * d[i];
+        w[i] = v;
+        w32[i] = (float)v;
+    }
+}
+
+// b[i] = a[i] rounded to FP32
+__global__ void k_mg_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
 }
 
 vip_status mg_set_params(vip_ctx* c, Multigrid& M, float omega, float corr) {
@@ -187,10 +198,12 @@ vip_status mg_set_params(vip_ctx* c, Multigrid& M, float omega, float corr) {
     if (!M.built || M.scaled_omega == omega) return VIP_OK;
     const int TB = 256;
     cudaStream_t st = c->stream;
-    k_mg_scale<<<(unsigned)((c->R + TB - 1) / TB), TB, 0, st>>>(c->R, (double)omega, M.fdinv, M.fwdinv);
+    k_mg_scale<<<(unsigned)((c->R + TB - 1) / TB), TB, 0, st>>>(c->R, (double)omega, M.fdinv, M.fwdinv,
+                                                                 M.fwdinv32);
     for (int l = 1; l <= M.nlev; ++l) {
         const MgLevel& lv = M.lev[l];
-        k_mg_scale<<<(unsigned)((lv.n + TB - 1) / TB), TB, 0, st>>>(lv.n, (double)omega, lv.dinv, lv.wdinv);
+        k_mg_scale<<<(unsigned)((lv.n + TB - 1) / TB), TB, 0, st>>>(lv.n, (double)omega, lv.dinv, lv.wdinv,
+                                                                     lv.wdinv32);
     }
     VIP_CUDA(cudaGetLastError());
     M.scaled_omega = omega;
@@ -327,8 +340,10 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         VIP_CUDA(dalloc(c, &lv.parent, n));
         VIP_CUDA(dalloc(c, &lv.coef, 25 * n));
         VIP_CUDA(dalloc(c, &lv.coefs, 25 * n));
+        VIP_CUDA(dalloc(c, &lv.coefs32, 25 * n));
         VIP_CUDA(dalloc(c, &lv.dinv, n));
         VIP_CUDA(dalloc(c, &lv.wdinv, n));
+        VIP_CUDA(dalloc(c, &lv.wdinv32, n));
         VIP_CUDA(dalloc(c, &lv.ring, n / 32));
         {
             // Tile height: a level with few 32 x 32 tiles would keep most SMs idle
@@ -433,6 +448,7 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
             MgLevel& lv = M.lev[l];
             k_mg_finish<<<(unsigned)((lv.n + TB - 1) / TB), TB, 0, st>>>(lv.n, lv.coef, lv.coefs, lv.dinv,
                                                                           lv.ring);
+            k_mg_f32<<<(unsigned)((25 * lv.n + TB - 1) / TB), TB, 0, st>>>(25 * lv.n, lv.coefs, lv.coefs32);
             VIP_CUDA(cudaGetLastError());
         }
     }
@@ -467,11 +483,15 @@ vip_status mg_build(vip_ctx* c, Multigrid& M) {
         VIP_CUDA(dalloc(c, &M.cinv_off, G));
         VIP_CUDA(cudaMemcpyAsync(M.cinv, hinv.data(), tot * 8, cudaMemcpyHostToDevice, st));
         VIP_CUDA(cudaMemcpyAsync(M.cinv_off, ioff.data(), G * 8, cudaMemcpyHostToDevice, st));
+        VIP_CUDA(dalloc(c, &M.cinv32, tot));
+        k_mg_f32<<<(unsigned)((tot + TB - 1) / TB), TB, 0, st>>>(tot, M.cinv, M.cinv32);
+        VIP_CUDA(cudaGetLastError());
         VIP_CUDA(cudaStreamSynchronize(st));
         M.ngeom = G;
     }
     VIP_CUDA(dalloc(c, &M.fdinv, R));
     VIP_CUDA(dalloc(c, &M.fwdinv, R));
+    VIP_CUDA(dalloc(c, &M.fwdinv32, R));
     k_mg_fine_diag<<<(unsigned)((R + TB - 1) / TB), TB, 0, st>>>(A, M.fdinv);
     VIP_CUDA(cudaGetLastError());
     {

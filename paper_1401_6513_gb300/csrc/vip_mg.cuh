@@ -45,8 +45,10 @@ struct MgLevel {                  // coarse level (all geometries concatenated)
     int64_t* child = nullptr;     // [4][n] cells of the level above (-1: none)
     double* coef = nullptr;       // [25][n] Galerkin stencil (setup layout)
     double* coefs = nullptr;      // the same, sliced: [n/32][25][32] (V-cycle layout)
+    float* coefs32 = nullptr;     // coefs rounded to FP32 (the FP32 V-cycle)
     double* dinv = nullptr;       // [n] l1-Jacobi scaling (0 for empty and padding cells)
     double* wdinv = nullptr;      // [n] omega * dinv (the smoother's step)
+    float* wdinv32 = nullptr;     // [n] omega * dinv rounded to FP32
     uint8_t* ring = nullptr;      // [n/32] 1 if a cell of the slice has a nonzero outside its 3 x 3 core
     MgLevGeom* lg = nullptr;      // [G] lattice of each geometry on this level
     MgTile* tiles = nullptr;      // 32 x th tiles covering every geometry's lattice
@@ -65,9 +67,11 @@ struct Multigrid {
     int32_t* crow = nullptr;
     double* fdinv = nullptr;      // [R] l1-Jacobi scaling of the fine operator
     double* fwdinv = nullptr;     // [R] omega * fdinv
+    float* fwdinv32 = nullptr;    // [R] omega * fdinv rounded to FP32
     void* fr = nullptr;           // [R] fine residual scratch
     void* fx = nullptr;           // [R] fine smoothing scratch
     double* cinv = nullptr;       // dense inverse of each geometry's coarsest operator (row-major)
+    float* cinv32 = nullptr;      // the same rounded to FP32
     int64_t* cinv_off = nullptr;  // [G] offset of geometry g's block in cinv
     int64_t cinv_entries = 0;     // entries of all geometries' coarsest inverses
     int ngeom = 0;
@@ -76,7 +80,8 @@ struct Multigrid {
     float scaled_omega = -1.0f;   // the omega that fwdinv and wdinv hold
 };
 
-// Device view of the hierarchy, vectors in precision T (operators in FP64).
+// Device view of the hierarchy with vectors, operators and arithmetic in precision
+// T (FP64, or FP32 copies of every operator for the FP32 V-cycle).
 template <class T>
 struct MgDev {
     int nlev;
@@ -84,22 +89,22 @@ struct MgDev {
     const int32_t* agg;
     const int64_t* cptr;
     const int32_t* crow;
-    const double* fwdinv;   // omega * fine l1-Jacobi scaling
+    const T* fwdinv;        // omega * fine l1-Jacobi scaling
     T* fr;
     T* fx;
     int64_t n[MG_MAXLEV + 1];
     int64_t ntiles[MG_MAXLEV + 1];
     const MgLevGeom* lg[MG_MAXLEV + 1];
     const MgTile* tiles[MG_MAXLEV + 1];
-    const double* coefs[MG_MAXLEV + 1];       // sliced stencils
+    const T* coefs[MG_MAXLEV + 1];            // sliced stencils
     const uint8_t* ring[MG_MAXLEV + 1];       // slices whose stencils reach beyond 3 x 3
     int32_t th[MG_MAXLEV + 1];                // tile heights
-    const double* wdinv[MG_MAXLEV + 1];       // omega * l1-Jacobi scaling
+    const T* wdinv[MG_MAXLEV + 1];            // omega * l1-Jacobi scaling
     T* x[MG_MAXLEV + 1];
     T* b[MG_MAXLEV + 1];
     T* y[MG_MAXLEV + 1];
     float corr;        // scaling of the coarse-grid correction (piecewise-constant prolongation)
-    const double* cinv;
+    const T* cinv;
     const int64_t* cinv_off;
 };
 

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_SINGULAR_STENCIL",
                 7: "ERR_TIMEOUT", 8: "ERR_OOM"}
 VIP_NODE_INTERIOR, VIP_NODE_WALL, VIP_NODE_SLIP, VIP_NODE_OUTLET = 0, 1, 2, 3
 VIP_W_CUBIC_SPLINE, VIP_W_PAPER = 0, 1
-VIP_PREC_FP64, VIP_PREC_MIXED = 0, 1
+VIP_PREC_FP64, VIP_PREC_MIXED, VIP_PREC_MG32 = 0, 1, 2
 VIP_IDENTITY_EXACT, VIP_IDENTITY_MLS = 0, 1
 OPS = ["NBR", "D00", "D10", "D01", "D20", "D11", "D02", "LAPLACE", "VIP_E", "VIP_W", "VIP_N",
        "VIP_S", "GX", "GY", "HELM_U", "HELM_V", "POISSON"]
@@ -35,7 +35,7 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_set_profiling", "vip_get_profile", "vip_ws_collect", "vip_ws_train",
            "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static",
            "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout",
-           "vip_multigrid_info", "vip_set_mg_shift"]
+           "vip_multigrid_info", "vip_set_mg_shift", "vip_set_refinement"]
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -92,6 +92,7 @@ def lib(path: str | Path | None = None):
         "vip_set_mls": ([vp, C.c_int, C.c_int, dbl], C.c_int),
         "vip_set_flow": ([vp, i32, dbl, dbl], C.c_int),
         "vip_set_solver": ([vp, C.c_int, dbl, i32, C.c_int], C.c_int),
+        "vip_set_refinement": ([vp, dbl], C.c_int),
         "vip_build": ([vp], C.c_int),
         "vip_set_state": ([vp, vp, vp, vp], C.c_int),
         "vip_step": ([vp, i32], C.c_int),
@@ -200,9 +201,12 @@ class Context:
     def vip_set_flow(self, geom, Re, dt):
         self._check(self.L.vip_set_flow(self.h, int(geom), float(Re), float(dt)))
 
-    def vip_set_solver(self, precision=VIP_PREC_MIXED, rtol=1e-8, max_iters=20000,
+    def vip_set_solver(self, precision=VIP_PREC_FP64, rtol=1e-8, max_iters=20000,
                        identity=VIP_IDENTITY_EXACT):
         self._check(self.L.vip_set_solver(self.h, precision, float(rtol), int(max_iters), identity))
+
+    def vip_set_refinement(self, inner_rtol=1e-3):
+        self._check(self.L.vip_set_refinement(self.h, float(inner_rtol)))
 
     def vip_build(self):
         self._check(self.L.vip_build(self.h))
@@ -470,7 +474,7 @@ def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.6,
     return dict(entry, cached=False)
 
 
-def solver_for(nodesets, precision=VIP_PREC_MIXED, rtol=1e-8, max_iters=20000,
+def solver_for(nodesets, precision=VIP_PREC_FP64, rtol=1e-8, max_iters=20000,
                identity=VIP_IDENTITY_EXACT, weight=VIP_W_CUBIC_SPLINE, support=2.2,
                device=0, stream=None, set_state=True, mg_shifts=None) -> Context:
     """Create a context for one node set or a list of them, build it and set u0, v0, p0.

@@ -120,7 +120,7 @@ def test_apply_and_convection(case):
     assert np.max(np.abs(Nu - Ru)) <= 1e-12 * sc and np.max(np.abs(Nv - Rv)) <= 1e-12 * sc, name
 
 
-@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+@pytest.mark.parametrize("prec", ["FP64", "MIXED", "MG32"])
 def test_poisson_solve(case, vip, prec):
     name, ns, ctx, ops, fs = case
     P = fs.P
@@ -128,7 +128,7 @@ def test_poisson_solve(case, vip, prec):
     b = np.where(np.append(fs.b_rows, False) if fs.bordered else fs.b_rows,
                  rng.standard_normal(P.shape[0]), 0.0)
     x_ref = sp.linalg.spsolve(P.tocsc(), b)
-    p = vip.VIP_PREC_FP64 if prec == "FP64" else vip.VIP_PREC_MIXED
+    p = {"FP64": vip.VIP_PREC_FP64, "MIXED": vip.VIP_PREC_MIXED, "MG32": vip.VIP_PREC_MG32}[prec]
     x, it, rr = ctx.vip_solve("POISSON", b, np.zeros_like(b), precision=p, rtol=1e-10,
                               max_iters=20000)
     assert rr <= 1e-10, (name, rr)
