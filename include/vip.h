@@ -72,8 +72,9 @@ enum { VIP_W_CUBIC_SPLINE = 0, VIP_W_PAPER = 1 };
  *          applied in differenced form, sum_k a_ik (d_k - d_i) + rowsum_i d_i
  *          with the FP64 row sum rounded to FP32), preconditioned by an FP32
  *          V-cycle, to a relative tolerance set by vip_set_refinement; the
- *          correction is accumulated in FP64; repeated until the FP64 residual
- *          meets rtol;
+ *          correction is accumulated without rounding loss (an FP32 pair per
+ *          row, error-free sums and products); repeated until the FP64
+ *          residual meets rtol;
  *   MG32   BiCGSTAB in FP64 (operator applications, vectors, dot products)
  *          whose multigrid preconditioner runs in FP32 (FP32 copies of every
  *          level's operator, FP32 vectors); only the Poisson solve has a
@@ -231,8 +232,9 @@ vip_status vip_stencil_info(vip_ctx* ctx, int which, int64_t* nrows, int64_t* nn
  * each operator application reads it: `slices` slices of 32 rows;
  * `uniform_slices` of them hold the same stencil in all 32 rows (the same value,
  * bit for bit, at each entry, and columns at the same offsets from the row or at
- * the same column) and are read as one stencil of `uniform_entries` entries in
- * total; the other slices are read as
+ * the same column) and read it from a table of distinct stencils (uniform slices
+ * with equal stencils share one copy) of `uniform_entries` entries in total; the
+ * other slices are read as
  * `other_entries` stored entries (8-byte value + 4-byte column each, padding
  * included).  Any output pointer may be NULL.  After vip_build. */
 vip_status vip_operator_layout(vip_ctx* ctx, int which, int64_t* slices, int64_t* uniform_slices,

@@ -53,7 +53,8 @@ struct Sell {
     double* uv64 = nullptr;
     float* uv32 = nullptr;
     int64_t nuniform = 0;         // uniform slices
-    int64_t nuentries = 0;        // their stencil entries
+    int64_t nuentries = 0;        // entries of their stored stencils (slices with the same
+                                  // stencil share one copy)
     int64_t nstored_other = 0;    // stored entries of the other slices
 };
 

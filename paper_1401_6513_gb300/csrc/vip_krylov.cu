@@ -15,7 +15,8 @@
 //   <float, float>    the mixed form: FP32 arithmetic on FP32 copies of the
 //                     operators and FP32 vectors inside, tol_in =
 //                     max(inner_rtol ||r||, rtol ||b|| / 2), the correction d
-//                     accumulated in FP64;
+//                     accumulated as an FP32 (hi, lo) pair by error-free
+//                     transformations (no FP64 operation per row inside);
 //   <double, float>   FP64 Krylov iteration with an FP32 V-cycle.
 // FP32 applications of the fine operator use the differenced row form
 // sum_k a_ik (x_k - x_i) + rowsum_i x_i with the FP64 row sum rounded to FP32: on
@@ -123,7 +124,8 @@ struct KArgs {
     int nsys;
     const double* b;
     double* x;
-    double* dx;          // the pass's correction, accumulated in FP64
+    double* dx;          // the pass's correction: FP64, or an FP32 (hi, lo) pair per row in the
+                         // FP32 iteration (the same 8 bytes), accumulated without rounding loss
     T *r, *rhat, *p, *v, *s, *t;
     double rtol, inner_rtol;
     int max_iters, max_outer, max_pass;
@@ -261,6 +263,37 @@ __device__ __forceinline__ TA sell_row(const int64_t* __restrict__ sptr,
     return sum;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (TMA; p 16-byte aligned, bytes a multiple
+// of 16).  A hint: no register receives data and nothing waits for it.
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Error-free FP32 transformations (Knuth's TwoSum; the product's rounding error
+// by one fused multiply-add).  The _rn intrinsics are never contracted into a
+// fused multiply-add, which would change the rounding these formulas rely on.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += al * ph + om * sh with FP32 operations only: the two products are
+// split exactly into rounded value and error, the rounded values are added to hi
+// by TwoSum, and every error term goes into lo; the pair is then renormalised.
+// The pair carries the sum to about 2^-44 of its size, so the correction of a
+// refinement pass keeps the digits an FP64 accumulator would.
+__device__ __forceinline__ float2 dd_axpy2(float2 d, float al, float ph, float om, float sh) {
+    const float p1 = __fmul_rn(al, ph), e1 = fmaf(al, ph, -p1);
+    const float p2 = __fmul_rn(om, sh), e2 = fmaf(om, sh, -p2);
+    float s1, t1, s2, t2;
+    two_sum(d.x, p1, s1, t1);
+    two_sum(s1, p2, s2, t2);
+    const float lo = __fadd_rn(d.y, __fadd_rn(__fadd_rn(t1, t2), __fadd_rn(e1, e2)));
+    const float hi = __fadd_rn(s2, lo);
+    return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, s2)));
+}
+
 // Work partition of one block of the Krylov launch (see k_bicgstab): this block's
 // slices are nv "virtual" slices in nseg segments, segment k being the slices
 // segs[k] + [0, segv[k+1] - segv[k]); its dot-product slots j < ng belong to systems
@@ -374,6 +407,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
     const double bd_tol = sizeof(T) == 8 ? 1e-14 : 1e-9;
     constexpr bool K32 = std::is_same_v<T, float>;   // FP32 Krylov iteration
     constexpr bool M32 = std::is_same_v<TM, float>;  // FP32 V-cycle
+
     __shared__ double sacc[KWARPS][MAXSYS_PB][NQ];
     __shared__ double stot[MAXSYS][NQ];
     __shared__ SysState S[MAXSYS];
@@ -491,6 +525,28 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
         __syncthreads();
         return true;
     };
+    // system of a slice (a launch of one system needs no lookup)
+    auto sysof = [&](int sl) -> int { return nsys == 1 ? 0 : __ldg(a.slice_sys + sl); };
+    // L2 prefetch of this block's rows of a row-indexed vector (elem bytes per row)
+    // by bulk copies (one thread per segment, chunks of at most 64 KB), so that a
+    // phase's streamed inputs are on their way from DRAM while its warps start:
+    // each warp walks its slices one after another, and 32 warps per SM alone keep
+    // too few loads in flight to cover the DRAM latency.  Slices start on 128-byte
+    // boundaries, so every copy is 16-byte aligned with a size that is a multiple
+    // of 16, as the bulk copy requires.
+    auto prefetch = [&](const void* vec, int elem) {
+        const int ns = P.nseg;
+        for (int k = threadIdx.x; k < ns; k += KTHREADS) {
+            const char* p0 = static_cast<const char*>(vec) + (int64_t)P.segs[k] * SLICE * elem;
+            uint64_t left = (uint64_t)(P.segv[k + 1] - P.segv[k]) * SLICE * elem;
+            while (left > 0) {
+                const uint32_t n = left > 65536u ? 65536u : (uint32_t)left;
+                l2_prefetch(p0, n);
+                p0 += n;
+                left -= n;
+            }
+        }
+    };
     auto any_of = [&](int which) {
         if (threadIdx.x == 0) {
             int any = 0;
@@ -599,9 +655,12 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
     auto vcycle = [&](const T* v, T* z) -> bool {
         const MgDev<TM>& M = a.mg;
         const int L = M.nlev;
+        prefetch(v, sizeof(T));
+        prefetch(M.fx, sizeof(TM));
+        if constexpr (M32) prefetch(a.rs32, 4);
         for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
             const int sl = vslice(iv, sg);
-            const int g = a.slice_sys[sl];
+            const int g = sysof(sl);
             const int64_t row = (int64_t)sl * 32 + lane;
             TM res = (TM)0;
             if (S[g].inner_active) res = (TM)ldv(v + row) - spmvM(sl, M.fx);
@@ -716,16 +775,20 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
             const TM* sol1 = M.x[1];
             for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
-                if (!S[a.slice_sys[sl]].inner_active) continue;
+                if (!S[sysof(sl)].inner_active) continue;
                 const int64_t rw = (int64_t)sl * 32 + lane;
                 const int32_t cc = __ldg(M.agg + rw);
                 if (cc >= 0) M.fx[rw] = ldv(M.fx + rw) + mcorr * ldv(sol1 + cc);
             }
             if (!grid_sync(a.bar, nb, a.status)) return false;
         }
+        prefetch(v, sizeof(T));
+        prefetch(M.fx, sizeof(TM));
+        prefetch(M.fwdinv, sizeof(TM));
+        if constexpr (M32) prefetch(a.rs32, 4);
         for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
             const int sl = vslice(iv, sg);
-            const int g = a.slice_sys[sl];
+            const int g = sysof(sl);
             if (!S[g].inner_active) continue;
             const int64_t row = (int64_t)sl * 32 + lane;
             const TM r = (TM)ldv(v + row) - spmvM(sl, M.fx);
@@ -752,11 +815,17 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
         if (outer > 0) {
             for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
-                int g = a.slice_sys[sl];
+                int g = sysof(sl);
                 int64_t row = (int64_t)sl * 32 + lane;
                 if (S[g].zero_x) a.x[row] = 0.0;
-                else if (S[g].outer_active && !S[g].pass_bad)
-                    a.x[row] = __ldcg(a.x + row) + ldv(a.dx + row);
+                else if (S[g].outer_active && !S[g].pass_bad) {
+                    if constexpr (K32) {
+                        const float2 d = ldv(reinterpret_cast<const float2*>(a.dx) + row);
+                        a.x[row] = __ldcg(a.x + row) + ((double)d.x + (double)d.y);
+                    } else {
+                        a.x[row] = __ldcg(a.x + row) + ldv(a.dx + row);
+                    }
+                }
             }
             if (!grid_sync(a.bar, nb, a.status)) { alive = false; break; }
         }
@@ -764,7 +833,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
         clear_acc();
         for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
             const int sl = vslice(iv, sg);
-            int g = a.slice_sys[sl];
+            int g = sysof(sl);
             if (!S[g].outer_active) continue;
             int64_t row = (int64_t)sl * 32 + lane;
             double bi = __ldg(a.b + row);
@@ -774,7 +843,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
             a.rhat[row] = rt;
             a.p[row] = (T)0;
             a.v[row] = (T)0;
-            a.dx[row] = 0.0;
+            a.dx[row] = 0.0;  // also the pair (0, 0)
             double q[3] = {ri * ri, bi * bi, (double)rt * (double)rt};
             acc(g, 3, q);
         }
@@ -834,7 +903,7 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
             if (any_zero) {  // final zeroing pass
                 for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
                     const int sl = vslice(iv, sg);
-                    int g = a.slice_sys[sl];
+                    int g = sysof(sl);
                     if (S[g].zero_x) a.x[(int64_t)sl * 32 + lane] = 0.0;
                 }
             }
@@ -853,9 +922,13 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
                 }
             }
             __syncthreads();
+            prefetch(a.r, sizeof(T));
+            prefetch(a.p, sizeof(T));
+            prefetch(a.v, sizeof(T));
+            if (a.use_mg) prefetch(a.mg.fwdinv, sizeof(TM));
             for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
-                int g = a.slice_sys[sl];
+                int g = sysof(sl);
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
                 const T be = sc<T>(S[g].beta, S[g].beta_f), om = sc<T>(S[g].omega, S[g].omega_f);
@@ -867,9 +940,12 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
             if (a.use_mg && !vcycle(a.p, a.phat)) { alive = false; break; }
             // B: v = A phat, rhat . v
             clear_acc();
+            prefetch(a.phat, sizeof(T));
+            prefetch(a.rhat, sizeof(T));
+            if constexpr (K32) prefetch(a.rs32, 4);
             for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
-                int g = a.slice_sys[sl];
+                int g = sysof(sl);
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
                 const T vi = spmvK(sl, a.phat);
@@ -895,9 +971,12 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
             }
             __syncthreads();
             // C: s = r - alpha v
+            prefetch(a.r, sizeof(T));
+            prefetch(a.v, sizeof(T));
+            if (a.use_mg) prefetch(a.mg.fwdinv, sizeof(TM));
             for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
-                int g = a.slice_sys[sl];
+                int g = sysof(sl);
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
                 const T si = ldv(a.r + row) - sc<T>(S[g].alpha, S[g].alpha_f) * ldv(a.v + row);
@@ -908,9 +987,12 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
             if (a.use_mg && !vcycle(a.s, a.shat)) { alive = false; break; }
             // D: t = A shat; t.s, t.t, s.s
             clear_acc();
+            prefetch(a.shat, sizeof(T));
+            prefetch(a.s, sizeof(T));
+            if constexpr (K32) prefetch(a.rs32, 4);
             for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
-                int g = a.slice_sys[sl];
+                int g = sysof(sl);
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
                 const T ti = spmvK(sl, a.shat);
@@ -943,14 +1025,26 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
             __syncthreads();
             // E: d += alpha p + omega s; r = s - omega t; rhat.r, r.r
             clear_acc();
+            prefetch(a.dx, 8);
+            prefetch(a.phat, sizeof(T));
+            prefetch(a.shat, sizeof(T));
+            prefetch(a.s, sizeof(T));
+            prefetch(a.t, sizeof(T));
+            prefetch(a.rhat, sizeof(T));
             for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
-                int g = a.slice_sys[sl];
+                int g = sysof(sl);
                 if (!S[g].inner_active) continue;
                 int64_t row = (int64_t)sl * 32 + lane;
-                const double al = S[g].alpha, om = S[g].omega;
-                a.dx[row] = ldv(a.dx + row) + al * (double)ldv(a.phat + row) + om * (double)ldv(a.shat + row);
-                const T rn = ldv(a.s + row) - sc<T>(om, S[g].omega_f) * ldv(a.t + row);
+                if constexpr (K32) {
+                    float2* dx2 = reinterpret_cast<float2*>(a.dx);
+                    dx2[row] = dd_axpy2(ldv(dx2 + row), S[g].alpha_f, ldv(a.phat + row), S[g].omega_f,
+                                        ldv(a.shat + row));
+                } else {
+                    a.dx[row] = ldv(a.dx + row) + S[g].alpha * (double)ldv(a.phat + row) +
+                                S[g].omega * (double)ldv(a.shat + row);
+                }
+                const T rn = ldv(a.s + row) - sc<T>(S[g].omega, S[g].omega_f) * ldv(a.t + row);
                 a.r[row] = rn;
                 const T q[2] = {ldv(a.rhat + row) * rn, rn * rn};
                 acc(g, 2, q);
