@@ -170,7 +170,7 @@ vip_status vip_set_solver(vip_ctx* ctx, int precision, double rtol, int32_t max_
  * solves of Eqs. 12-13 stop at the same FP64 residual whatever it is): each FP32
  * BiCGSTAB pass stops when its recursive residual has fallen to inner_rtol times
  * the FP64 residual it started from (or to rtol ||b|| / 2).  inner_rtol in
- * (0, 1); default 1e-3.  VIP_ERR_ARG otherwise. */
+ * (0, 1); default 1e-4.  VIP_ERR_ARG otherwise. */
 vip_status vip_set_refinement(vip_ctx* ctx, double inner_rtol);
 
 /* Build everything that depends only on the geometry and flow parameters:

@@ -149,7 +149,7 @@ struct vip_ctx {
     double rtol = 1e-8;
     int32_t max_iters = 20000;
     int identity = VIP_IDENTITY_EXACT;
-    double inner_rtol = 1e-3;     // FP32 inner solve target relative to the FP64 residual
+    double inner_rtol = 1e-4;     // FP32 inner solve target relative to the FP64 residual
     bool built = false;
     bool use_graph = true;
     int64_t N = 0;                // nodes

@@ -301,6 +301,7 @@ __device__ __forceinline__ float2 dd_axpy2(float2 d, float al, float ph, float o
 // blocks [b0[g], b1[g]).
 struct Partition {
     int nv, nseg, ng, valid;
+    int mixed;                     // 1: the static partition (a segment may span systems)
     int segv[MAXSYS_PB + 1], segs[MAXSYS_PB];
     int b0[MAXSYS], b1[MAXSYS], j[MAXSYS], sys[MAXSYS_PB];
     int ss0[MAXSYS], ss1[MAXSYS];  // slices [ss0[g], ss1[g]) of system g
@@ -380,8 +381,10 @@ __device__ __noinline__ void partition_update(Partition& P, const SysState* S, i
                 P.b1[g] = b + 1;
             }
         }
+        P.mixed = 0;
         if (!ok) {  // the static partition: every system of the block's range
             const int g0 = blk_g0[bid];
+            P.mixed = 1;
             P.nseg = 1;
             P.segs[0] = blk_s0[bid];
             P.segv[0] = 0;
@@ -527,6 +530,28 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
     };
     // system of a slice (a launch of one system needs no lookup)
     auto sysof = [&](int sl) -> int { return nsys == 1 ? 0 : __ldg(a.slice_sys + sl); };
+    // The FP32 streaming phases take four consecutive rows per thread with 16-byte
+    // loads (consecutive threads, consecutive rows: a warp covers four slices).  A
+    // warp walks its rows one group after another and each group waits for one
+    // round trip to memory, so four rows per trip instead of one cut those phases'
+    // latency.  body(row0, g) for row0 a multiple of 4 in a slice of system g still
+    // in its pass; segments hold one system each unless the partition is the
+    // static one (P.mixed), which the callers handle by slices instead.  Threads of
+    // a warp may have rows or not (a segment's last rows), so a phase with dot
+    // products first makes every thread register the segment's system (enter(g),
+    // all threads together): the warp-wide flush of the per-lane sums then only
+    // ever runs with the whole warp.
+    auto quads = [&](auto&& enter, auto&& body) {
+        for (int k = 0; k < P.nseg; ++k) {
+            const int64_t r0 = (int64_t)P.segs[k] * SLICE;
+            const int64_t n4 = (int64_t)(P.segv[k + 1] - P.segv[k]) * (SLICE / 4);
+            const int g = sysof(P.segs[k]);
+            if (!S[g].inner_active) continue;
+            enter(g);
+            for (int64_t q = threadIdx.x; q < n4; q += KTHREADS) body(r0 + 4 * q, g);
+        }
+    };
+    auto no_enter = [](int) {};
     // L2 prefetch of this block's rows of a row-indexed vector (elem bytes per row)
     // by bulk copies (one thread per segment, chunks of at most 64 KB), so that a
     // phase's streamed inputs are on their way from DRAM while its warps start:
@@ -913,6 +938,10 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
         // ---- inner BiCGSTAB pass
         while (any_of(1)) {
             repartition(1);
+            // the FP32 streaming phases take rows four at a time (quads); their slice
+            // loops then have nothing left to do
+            const bool by_quads = K32 && M32 && !P.mixed;
+            const int nvq = by_quads ? 0 : nv;
             // A: beta, p = r + beta (p - omega v)
             if (threadIdx.x < nsys) {
                 SysState& st = S[threadIdx.x];
@@ -926,7 +955,27 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
             prefetch(a.p, sizeof(T));
             prefetch(a.v, sizeof(T));
             if (a.use_mg) prefetch(a.mg.fwdinv, sizeof(TM));
-            for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+            if constexpr (K32 && M32) {
+                if (by_quads) {
+                    quads(no_enter, [&](int64_t r0, int g) {
+                        const float be = S[g].beta_f, om = S[g].omega_f;
+                        const float4 rr = *reinterpret_cast<const float4*>(a.r + r0);
+                        float4 pp = *reinterpret_cast<const float4*>(a.p + r0);
+                        const float4 vv = *reinterpret_cast<const float4*>(a.v + r0);
+                        pp.x = rr.x + be * (pp.x - om * vv.x);
+                        pp.y = rr.y + be * (pp.y - om * vv.y);
+                        pp.z = rr.z + be * (pp.z - om * vv.z);
+                        pp.w = rr.w + be * (pp.w - om * vv.w);
+                        *reinterpret_cast<float4*>(a.p + r0) = pp;
+                        if (a.use_mg) {
+                            const float4 wd = __ldg(reinterpret_cast<const float4*>(a.mg.fwdinv + r0));
+                            *reinterpret_cast<float4*>(a.mg.fx + r0) =
+                                make_float4(wd.x * pp.x, wd.y * pp.y, wd.z * pp.z, wd.w * pp.w);
+                        }
+                    });
+                }
+            }
+            for (int iv = warp, sg = 0; iv < nvq; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
                 int g = sysof(sl);
                 if (!S[g].inner_active) continue;
@@ -974,7 +1023,24 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
             prefetch(a.r, sizeof(T));
             prefetch(a.v, sizeof(T));
             if (a.use_mg) prefetch(a.mg.fwdinv, sizeof(TM));
-            for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+            if constexpr (K32 && M32) {
+                if (by_quads) {
+                    quads(no_enter, [&](int64_t r0, int g) {
+                        const float al = S[g].alpha_f;
+                        const float4 rr = *reinterpret_cast<const float4*>(a.r + r0);
+                        const float4 vv = *reinterpret_cast<const float4*>(a.v + r0);
+                        const float4 ss = make_float4(rr.x - al * vv.x, rr.y - al * vv.y, rr.z - al * vv.z,
+                                                      rr.w - al * vv.w);
+                        *reinterpret_cast<float4*>(a.s + r0) = ss;
+                        if (a.use_mg) {
+                            const float4 wd = __ldg(reinterpret_cast<const float4*>(a.mg.fwdinv + r0));
+                            *reinterpret_cast<float4*>(a.mg.fx + r0) =
+                                make_float4(wd.x * ss.x, wd.y * ss.y, wd.z * ss.z, wd.w * ss.w);
+                        }
+                    });
+                }
+            }
+            for (int iv = warp, sg = 0; iv < nvq; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
                 int g = sysof(sl);
                 if (!S[g].inner_active) continue;
@@ -1031,7 +1097,36 @@ __global__ void __launch_bounds__(KTHREADS, 1) k_bicgstab(KArgs<T, TM> a) {
             prefetch(a.s, sizeof(T));
             prefetch(a.t, sizeof(T));
             prefetch(a.rhat, sizeof(T));
-            for (int iv = warp, sg = 0; iv < nv; iv += KWARPS) {
+            if constexpr (K32 && M32) {
+                if (!P.mixed) {
+                    const float zero2[2] = {0.0f, 0.0f};
+                    quads([&](int g) { acc(g, 2, zero2); }, [&](int64_t r0, int g) {
+                        const SysState& q = S[g];
+                        const float al = q.alpha_f, om = q.omega_f;
+                        float4* dx4 = reinterpret_cast<float4*>(a.dx + r0);  // rows r0, r0 + 1 | r0 + 2, r0 + 3
+                        float4 d01 = dx4[0], d23 = dx4[1];
+                        const float4 ph = *reinterpret_cast<const float4*>(a.phat + r0);
+                        const float4 sh = *reinterpret_cast<const float4*>(a.shat + r0);
+                        const float4 ss = *reinterpret_cast<const float4*>(a.s + r0);
+                        const float4 tt = *reinterpret_cast<const float4*>(a.t + r0);
+                        const float4 rh = *reinterpret_cast<const float4*>(a.rhat + r0);
+                        float2 d;
+                        d = dd_axpy2(make_float2(d01.x, d01.y), al, ph.x, om, sh.x); d01.x = d.x; d01.y = d.y;
+                        d = dd_axpy2(make_float2(d01.z, d01.w), al, ph.y, om, sh.y); d01.z = d.x; d01.w = d.y;
+                        d = dd_axpy2(make_float2(d23.x, d23.y), al, ph.z, om, sh.z); d23.x = d.x; d23.y = d.y;
+                        d = dd_axpy2(make_float2(d23.z, d23.w), al, ph.w, om, sh.w); d23.z = d.x; d23.w = d.y;
+                        dx4[0] = d01;
+                        dx4[1] = d23;
+                        const float4 rn = make_float4(ss.x - om * tt.x, ss.y - om * tt.y, ss.z - om * tt.z,
+                                                      ss.w - om * tt.w);
+                        *reinterpret_cast<float4*>(a.r + r0) = rn;
+                        const float qq[2] = {((rh.x * rn.x + rh.y * rn.y) + (rh.z * rn.z + rh.w * rn.w)),
+                                             ((rn.x * rn.x + rn.y * rn.y) + (rn.z * rn.z + rn.w * rn.w))};
+                        acc(g, 2, qq);
+                    });
+                }
+            }
+            for (int iv = warp, sg = 0; iv < nvq; iv += KWARPS) {
                 const int sl = vslice(iv, sg);
                 int g = sysof(sl);
                 if (!S[g].inner_active) continue;

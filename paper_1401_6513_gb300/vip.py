@@ -205,7 +205,7 @@ class Context:
                        identity=VIP_IDENTITY_EXACT):
         self._check(self.L.vip_set_solver(self.h, precision, float(rtol), int(max_iters), identity))
 
-    def vip_set_refinement(self, inner_rtol=1e-3):
+    def vip_set_refinement(self, inner_rtol=1e-4):
         self._check(self.L.vip_set_refinement(self.h, float(inner_rtol)))
 
     def vip_build(self):
