@@ -7,9 +7,17 @@ of the dominant kernel (the Poisson BiCGSTAB launch).
 
 Workload (default): flow past the bumpy cylinder r = 1 + 0.05 sin 12t + 0.02 sin 31t
 in the channel [-8,24]x[-8,8] at h = 1/64 (about 2.1M nodes), Re = 200, dt = h/10,
-multigrid-preconditioned FP64 Krylov solves, synthetic (generated) node set and an
-impulsively started uniform inflow.  Its working set (several GB) exceeds the
+synthetic (generated) node set and an impulsively started uniform inflow, solved
+in the mixed form (FP32 inner BiCGSTAB and V-cycle under FP64 refinement, every
+solve stopped on the FP64 residual).  Its working set (several GB) exceeds the
 129 MB L2, so no flush is needed between timed steps.
+
+The timed steps run three times from one checkpoint of the state: on the device
+(the headline value, no host synchronisation inside), with per-phase CUDA events
+(the Poisson launch's duration for the roofline), and end to end through the C
+ABI with the state loaded from and read back to pinned host memory every step.
+The same steps are then timed in the plain all-FP64 form, and the batch of 64
+equilateral cavities in both forms (extra keys; --no-batch skips it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -46,8 +54,14 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="bumpy_h64",
                     choices=["bumpy_h64", "cylinder_h32", "cavity_256", "triangles64"])
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
-    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--precision", choices=["auto", "mixed", "fp64", "mg32"], default="auto",
+                    help="form of the Krylov solves; auto: the fastest of the three over two "
+                         "steps from the warmed-up state (vip.choose_precision, untimed)")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip timing the same steps in the plain all-FP64 form")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batch of 64 equilateral cavities (extra keys)")
+    ap.add_argument("--batch-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--warm-start", choices=["previous", "learned"], default="previous",
                     help="initial guess of the pressure-increment solve: the previous "
@@ -234,56 +248,126 @@ def run_reference(args, rank, ws):
 
 
 # DRAM bytes per inner iteration of the Poisson launch, from one ncu capture of the
-# same workload and kernel (dram__bytes_read.sum + dram__bytes_write.sum of one launch
-# divided by its iterations); every iteration streams the same operator and vectors,
-# so a launch's traffic scales with its iterations (profiles/k_bicgstab_poisson_bumpy_h64.md).
-# Re-measured whenever the kernel changes.
-TRAFFIC_PER_ITER = {("bumpy_h64", "fp64"): 57.911748608e9 / 62.0}
+# same workload, form and kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch divided by its inner iterations; profiles/): every iteration streams the same
+# operator and vectors, so a launch's traffic scales with its iterations.  Keyed by
+# workload and form; a form whose kernel changed since its capture has no entry.
+TRAFFIC_PER_ITER = {}
 
 # FP64 operations per clock per SM of GB300 (two FP64 FMAs), for the ALU roofline;
 # 152 SMs at 2070 MHz give 1.26 TFLOP/s, the part's nominal FP64 rate.
 FP64_FLOPS_PER_CLK_SM = 4
 
+PREC_BYTES = {"fp64": (8, 8), "mixed": (4, 4), "mg32": (8, 4)}  # Krylov vectors, V-cycle
 
-def poisson_bytes_per_iter(streamed, rows, tb):
+
+def poisson_bytes_per_iter(streamed, rows, tb, tm):
     """Algorithmic DRAM bytes of one inner iteration of the multigrid-preconditioned
-    BiCGSTAB (vectors of tb bytes, int32 columns):
-      * six passes over the operator as stored (value + column per streamed entry:
-        the stored entries of ordinary slices plus one stencil per slice whose 32
-        rows share it; vip_operator_layout): two Krylov SpMVs and the two fine-level
-        residuals of each of the two V-cycles;
-      * 48 row-sized vector accesses: p update 6, each V-cycle's fine level 11.5
-        (residual 3, restriction 1.5, prolongation 3, smoothing 4), v 3, s 5, t 3,
-        x/r update 8;
-      * the coarse levels, 188 B per level-1 cell per V-cycle (down: b and the
+    BiCGSTAB, Krylov vectors of tb bytes and V-cycle vectors and operators of tm
+    bytes (int32 columns):
+      * six passes over the fine operator as stored (value + column per streamed
+        entry: the stored entries of ordinary slices plus the distinct stencils of
+        the uniform slices; vip_operator_layout), two in the Krylov precision and
+        the four fine-level applications of the two V-cycles in the V-cycle's, plus
+        the FP32 row sum of every row in each FP32 application (differenced rows);
+      * the row-sized vector accesses: p update 4 tb + 2 tm, each V-cycle's fine
+        level 3 tb + 8.5 tm (residual, restriction, prolongation, smoothing), v 3 tb,
+        s 3 tb + 2 tm, t 3 tb, x/r update 6 tb + 16 (the correction, read and
+        written, is 8 bytes in every form) -- 48 accesses in the FP64 form;
+      * the coarse levels, 188 B per level-1 cell per V-cycle in FP64 (down: b and the
         inverse diagonal, the 9 coefficients of the 3 x 3 stencil core, a quarter
-        of b_{l+1}; up: the same plus the parent's correction and y), a quarter of a
-        cell per row and 4/3 of it over all levels: 63 B per row per V-cycle."""
-    return 6 * streamed * (tb + 4) + 48 * tb * rows + 2 * 63 * rows
+        of b_{l+1}; up: the same plus the parent's correction and y), half in FP32,
+        a quarter of a cell per row and 4/3 of it over all levels."""
+    ops = 2 * streamed * (tb + 4) + 4 * streamed * (tm + 4)
+    ops += rows * 4 * ((2 if tb == 4 else 0) + (4 if tm == 4 else 0))
+    vec = rows * (25 * tb + 21 * tm + 16)
+    coarse = 2 * 63 * rows * tm / 8
+    return ops + vec + coarse
 
 
 def poisson_flops_per_iter(nnz, rows):
-    """Algorithmic FP64 operations of one inner iteration (an FMA counts 2): six
-    operator applications (2 nnz each); per row 46 in the Krylov and fine-level
-    vector updates and dot products (p 6, two V-cycles' fine level 8 each, v 4, s 4,
-    t 6, x/r 10) and 32 on the coarse levels (48 per level-1 cell per V-cycle: 3 x 3
-    stencils down and up, smoothing, restriction, correction; a quarter of a cell
-    per row, 4/3 over all levels).  The dense coarsest solves are added by the
-    caller (coarsest_per_iter)."""
+    """Algorithmic floating-point operations of one inner iteration (an FMA counts
+    2): six operator applications (2 nnz each); per row 46 in the Krylov and
+    fine-level vector updates and dot products (p 6, two V-cycles' fine level 8 each,
+    v 4, s 4, t 6, x/r 10) and 32 on the coarse levels (48 per level-1 cell per
+    V-cycle: 3 x 3 stencils down and up, smoothing, restriction, correction; a
+    quarter of a cell per row, 4/3 over all levels).  The dense coarsest solves are
+    added by the caller (coarsest_per_iter).  In the FP64 form all of them are FP64
+    operations; the mixed form does them in FP32."""
     return 12 * nnz + 78 * rows
 
 
-def coarsest_per_iter(entries):
-    """Bytes and FP64 operations of the dense coarsest solves of one inner
-    iteration: each of the two V-cycles reads every entry of the coarsest inverses
-    once (FP64) and multiplies it into one sum (an FMA)."""
-    return 2 * 8 * entries, 2 * 2 * entries
+def coarsest_per_iter(entries, tm):
+    """Bytes and operations of the dense coarsest solves of one inner iteration:
+    each of the two V-cycles reads every entry of the coarsest inverses once and
+    multiplies it into one sum (an FMA)."""
+    return 2 * tm * entries, 2 * 2 * entries
 
 
 def poisson_bytes_per_pass(nnz, rows, tb):
     """One FP64 refinement pass: the FP64 residual SpMV, b, x and the five vectors it
     initialises, and the correction x += d."""
-    return nnz * 12 + rows * (8 + 8 + 5 * tb) + rows * (8 + 8 + tb)
+    return nnz * 12 + rows * (8 + 8 + 5 * tb) + rows * (8 + 8 + 8)
+
+
+def timed_steps(ctx, stream, k):
+    """Device time (ms) of k steps on the library's stream, CUDA events on that stream."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.vip_step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def form_run(vip, ctx, stream, ckpt, k, prec):
+    """The k steps after the checkpoint in precision form prec: ms, Poisson inner
+    iterations and refinement passes per step, last relative residual, status."""
+    ctx.vip_set_solver(prec, 1e-8, 50000, vip.VIP_IDENTITY_EXACT)
+    ctx.vip_checkpoint(False, ckpt)
+    ctx.vip_step(1)  # captures this form's step graph outside the timed region
+    ctx.vip_checkpoint(False, ckpt)
+    s0 = ctx.vip_get_stats()
+    ms = timed_steps(ctx, stream, k)
+    s1 = ctx.vip_get_stats()
+    return {"ms_per_step": ms / k,
+            "poisson_iters_per_step": (s1.total_poisson_iters - s0.total_poisson_iters) / k,
+            "poisson_outer_per_step": (s1.total_poisson_outer - s0.total_poisson_outer) / k,
+            "last_poisson_relres": s1.poisson_relres, "status": s1.status}
+
+
+def ALL_FORMS(vip):
+    return (vip.VIP_PREC_MIXED, vip.VIP_PREC_FP64, vip.VIP_PREC_MG32)
+
+
+def batch_lines(vip, dev, stream, steps, prec):
+    """The batch of 64 equilateral cavities (one context, each geometry's multigrid
+    cell-grid parity chosen, multigrid parameters tuned; untimed setup) in the given
+    form and in the plain FP64 form, over the same steps from one checkpoint."""
+    nss, cfg = make_workload("triangles64")
+    N = int(sum(g.n for g in nss))
+    t0 = time.perf_counter()
+    shifts, _ = vip.choose_mg_shifts(nss, steps=2, precision=prec, rtol=1e-8, max_iters=50000,
+                                     device=dev, stream=stream.cuda_stream)
+    ctx = vip.solver_for(nss, precision=prec, rtol=1e-8, max_iters=50000, device=dev,
+                         stream=stream.cuda_stream, mg_shifts=shifts)
+    tune = vip.autotune(ctx, nss)
+    ctx.vip_step(3)
+    best, table = vip.choose_precision(ctx, ALL_FORMS(vip))
+    ckpt = ctx.vip_checkpoint(True)
+    setup = time.perf_counter() - t0
+    out = {"workload": cfg["workload"], "nodes": N, "geometries": len(nss), "steps": steps,
+           "setup_s": round(setup, 1), "multigrid": {"omega": tune["omega"], "corr": tune["corr"]},
+           "chosen_form": vip.PREC_NAMES[best], "form_trials": table}
+    for name, p in (("chosen", best), ("fp64", vip.VIP_PREC_FP64)):
+        r = form_run(vip, ctx, stream, ckpt, steps, p)
+        r["node_updates_per_s"] = N / (r["ms_per_step"] / 1e3)
+        out[name] = r
+    ctx.close()
+    return out
 
 
 def main():
@@ -303,7 +387,9 @@ def main():
     stream = torch.cuda.current_stream(dev)
     ns, cfg = make_workload(args.workload)
     nss = ns if isinstance(ns, list) else [ns]
-    prec = vip.VIP_PREC_MIXED if args.precision == "mixed" else vip.VIP_PREC_FP64
+    PREC = {"mixed": vip.VIP_PREC_MIXED, "fp64": vip.VIP_PREC_FP64, "mg32": vip.VIP_PREC_MG32,
+            "auto": vip.VIP_PREC_MIXED}
+    prec = PREC[args.precision]
     t0 = time.perf_counter()
     shifts = None
     if args.mg_shift == "auto":
@@ -313,20 +399,11 @@ def main():
                          stream=stream.cuda_stream, mg_shifts=shifts)
     setup_s = time.perf_counter() - t0
     N = int(sum(g.n for g in nss))
-    # multigrid parameters tuned on this workload (one step, then back to the initial
-    # fields; untimed)
+    # multigrid parameters tuned on this workload (untimed; back to the initial fields)
     tune = vip.autotune(ctx, nss) if not args.no_autotune else None
     ctx.vip_step(args.warmup)
     ws_info = None
-    twin = None
     if args.warm_start == "learned":
-        # a twin context takes the same steps with the previous-increment guess, so the
-        # iteration counts compare step for step at the same residual
-        twin = vip.solver_for(nss, precision=prec, rtol=1e-8, max_iters=50000, device=dev,
-                              stream=stream.cuda_stream, mg_shifts=shifts)
-        if tune:
-            twin.vip_set_multigrid(tune["omega"], tune["corr"])
-        twin.vip_step(args.warmup + args.ws_samples + 2)
         # collect solved increments, train, then use the network's guess (untimed)
         t1 = time.perf_counter()
         ctx.vip_ws_collect(True, args.ws_samples)
@@ -338,48 +415,47 @@ def main():
         ws_info = {"guess": "learned", "samples": args.ws_samples, "epochs": args.ws_epochs,
                    "first_loss": tc.first_loss, "final_loss": tc.final_loss,
                    "collect_train_s": round(time.perf_counter() - t1, 2)}
+    form_trials = None
+    if args.precision == "auto":
+        prec, form_trials = vip.choose_precision(ctx, ALL_FORMS(vip))
+    form = vip.PREC_NAMES[prec]
+    tb, tm = PREC_BYTES[form]
     torch.cuda.synchronize()
-    s0 = ctx.vip_get_stats()
-    g0_iters = ctx.vip_get_geometry_iters()
+    ckpt = ctx.vip_checkpoint(True)
     # ---- timed region: K steps, device time by CUDA events on the library's stream
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         uuid = str(dev)
+    s0 = ctx.vip_get_stats()
+    g0_iters = ctx.vip_get_geometry_iters()
     clocks = Clocks(uuid)
-    ctx.vip_set_profiling(True)
     barrier(ws)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ctx.vip_step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms = timed_steps(ctx, stream, args.steps)
     barrier(ws)
-    ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    ctx.vip_set_profiling(False)
-    prof, nprof = ctx.vip_get_profile()
     s1 = ctx.vip_get_stats()
-    if twin is not None:
-        t0s = twin.vip_get_stats()
-        twin.vip_step(args.steps)
-        t1s = twin.vip_get_stats()
-        twin.close()
-        ws_info["poisson_iters_per_step_previous_guess_same_steps"] = \
-            (t1s.total_poisson_iters - t0s.total_poisson_iters) / max(args.steps, 1)
+    g_iters = ctx.vip_get_geometry_iters() - g0_iters
     ms_max = max_over_ranks(ms, ws)
     value = throughput(N, args.steps, ws, ms_max)
-    # ---- roofline of the Poisson BiCGSTAB launch (one per step)
     it_p = s1.total_poisson_iters - s0.total_poisson_iters
     out_p = s1.total_poisson_outer - s0.total_poisson_outer
     it_h = s1.total_helm_iters - s0.total_helm_iters
+    # ---- the same steps again with per-phase events (the Poisson launch's duration)
+    ctx.vip_checkpoint(False, ckpt)
+    ctx.vip_set_profiling(True)
+    sp0 = ctx.vip_get_stats()
+    ctx.vip_step(args.steps)
+    torch.cuda.synchronize()
+    ctx.vip_set_profiling(False)
+    prof, nprof = ctx.vip_get_profile()
+    sp1 = ctx.vip_get_stats()
+    it_prof = sp1.total_poisson_iters - sp0.total_poisson_iters
+    # ---- roofline of the Poisson BiCGSTAB launch (one per step)
     ptr, _, _ = ctx.vip_get_stencil("POISSON")
     nnz_p = int(ptr[-1])
     rows_p = int(ptr.size - 1)
-    tb = 4 if prec == vip.VIP_PREC_MIXED else 8
     lay = ctx.vip_operator_layout("POISSON")
     _, cinv_entries = ctx.vip_multigrid_info()
     # entries one operator pass streams, per real entry (exact for one geometry; a
@@ -387,7 +463,6 @@ def main():
     stream_ratio = (lay["other_entries"] + lay["uniform_entries"]) / max(nnz_p, 1)
     # per geometry: a converged system stops iterating inside the shared launch, so the
     # algorithmic bytes are summed over geometries with their own iteration counts
-    g_iters = ctx.vip_get_geometry_iters() - g0_iters
     bytes_p, flops_p, off, kb = 0, 0, 0, 0
     for gi, g in enumerate(nss):
         nnz_g = int(ptr[off + g.n] - ptr[off])
@@ -396,19 +471,20 @@ def main():
             nnz_g += int(ptr[N + kb + 1] - ptr[N + kb])
             rows_g += 1
             kb += 1
-        bytes_p += int(g_iters[gi]) * poisson_bytes_per_iter(nnz_g * stream_ratio, rows_g, tb)
+        bytes_p += int(g_iters[gi]) * poisson_bytes_per_iter(nnz_g * stream_ratio, rows_g, tb, tm)
         flops_p += int(g_iters[gi]) * poisson_flops_per_iter(nnz_g, rows_g)
         off += g.n
     # dense coarsest solves: every geometry's inverse is read while the launch
     # iterates (an overcount for a batch whose systems finish early; there the
     # inverses are small)
-    cb, cf = coarsest_per_iter(cinv_entries)
+    cb, cf = coarsest_per_iter(cinv_entries, tm)
     bytes_p += it_p * cb
     flops_p += it_p * cf
+    fp64_flops = flops_p if form == "fp64" else 0
     bytes_p += out_p * poisson_bytes_per_pass(nnz_p, rows_p, tb)
-    flops_p += out_p * (2 * nnz_p + 8 * rows_p)  # refinement: residual, 3 dots, x update
+    fp64_flops += out_p * (2 * nnz_p + 8 * rows_p)  # refinement: residual, 3 dots, x update
     t_pois = prof["poisson"] / 1e3
-    tpi = TRAFFIC_PER_ITER.get((args.workload, args.precision))
+    tpi = TRAFFIC_PER_ITER.get((args.workload, form))
     traffic = tpi * it_p / max(args.steps, 1) if tpi else None  # per launch (one per step)
     pk, pk_src = peaks()
     hbm = float(pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
@@ -416,7 +492,7 @@ def main():
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
     fp64_peak = FP64_FLOPS_PER_CLK_SM * torch.cuda.get_device_properties(0).multi_processor_count \
         * sm_mhz * 1e6 / 1e12
-    fp64_achieved = flops_p / t_pois / 1e12 if t_pois > 0 else 0.0
+    fp64_achieved = fp64_flops / t_pois / 1e12 if t_pois > 0 else 0.0
     roof_hbm = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": f"hbm_gbs {pk_src}",
                 "bytes_per_step": bytes_p / max(args.steps, 1)}
@@ -424,27 +500,30 @@ def main():
                 "frac": fp64_achieved / fp64_peak,
                 "peak_source": f"FP64: {FP64_FLOPS_PER_CLK_SM} flops/clk/SM x SMs x sm_max_mhz "
                                f"{sm_mhz:.0f} ({pk_src})",
-                "flops_per_step": flops_p / max(args.steps, 1)}
+                "fp64_flops_per_step": fp64_flops / max(args.steps, 1)}
     # the binding roof is the one the kernel is closest to; the other is reported beside it
-    if prec == vip.VIP_PREC_FP64 and roof_alu["frac"] > roof_hbm["frac"]:
+    if roof_alu["frac"] > roof_hbm["frac"]:
         roof, roof_other = roof_alu, roof_hbm
     else:
         roof, roof_other = roof_hbm, roof_alu
-    roof = dict(roof, traffic=traffic, kernel="k_bicgstab (Poisson)",
-                operator_layout=lay)
-    # ---- end to end through the C ABI with pinned host buffers: every step loads the
-    # state from host memory, steps, and reads the new state back into host memory,
-    # from which the next step starts (the integration continues; same work per step)
-    k2 = args.e2e_steps or args.steps
+    kname = {"mixed": "k_bicgstab<float,float>", "fp64": "k_bicgstab<double,double>",
+             "mg32": "k_bicgstab<double,float>"}[form]
+    roof = dict(roof, traffic=traffic, kernel=kname + " (Poisson)", operator_layout=lay,
+                launch_ms_per_step=t_pois * 1e3 / max(nprof, 1))
+    # ---- end to end through the C ABI with pinned host buffers, the same steps: every
+    # step loads the state from host memory, steps, and reads the new state back into
+    # host memory, from which the next step starts
+    ctx.vip_checkpoint(False, ckpt)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
     u, v, p, phi = ctx.vip_get_state()
     bufs = [(pin(u), pin(v), pin(p)), tuple(torch.empty(N, dtype=torch.float64).pin_memory()
                                             for _ in range(3))]
     oph = torch.empty(N, dtype=torch.float64).pin_memory()
+    se0 = ctx.vip_get_stats()
     torch.cuda.synchronize()
     barrier(ws)
     t0 = time.perf_counter()
-    for k in range(k2):
+    for k in range(args.steps):
         hu, hv, hp = bufs[k % 2]
         ou, ov, op = bufs[(k + 1) % 2]
         ctx.vip_load_state(hu, hv, hp)
@@ -453,38 +532,57 @@ def main():
     e2e_s = time.perf_counter() - t0
     barrier(ws)
     e2e_s = max_over_ranks(e2e_s, ws)
-    st = ctx.vip_get_stats()
+    se1 = ctx.vip_get_stats()
+    it_e2e = se1.total_poisson_iters - se0.total_poisson_iters
+    st = se1
+    # ---- the plain all-FP64 form on the same steps (same context, multigrid, checkpoint)
+    fp64_cmp = None
+    if form != "fp64" and not args.no_fp64_compare:
+        fp64_cmp = form_run(vip, ctx, stream, ckpt, args.steps, vip.VIP_PREC_FP64)
+        fp64_cmp["node_updates_per_s"] = N / (fp64_cmp["ms_per_step"] / 1e3)
+        fp64_cmp["chosen_over_fp64"] = value / ws / fp64_cmp["node_updates_per_s"]
     ctx.close()
+    batch = None
+    if ws == 1 and not args.no_batch and args.workload != "triangles64":
+        batch = batch_lines(vip, dev, stream, args.batch_steps, prec)
     if rank != 0:
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", "1")
-        cpu = time_oracle(args.workload, 1, 0)
-    cfg.update({"global_batch": len(nss), "parallelism": f"replicas x{ws}", "precision": args.precision,
+        cpu = time_oracle(args.workload, 2, 1)
+    cfg.update({"global_batch": len(nss), "parallelism": f"replicas x{ws}", "precision": form,
+                "precision_choice": ({"by": "measurement (vip.choose_precision, 2 steps each)",
+                                      "trials": form_trials} if form_trials else "fixed by --precision"),
                 "l2": "working set > L2 (no flush needed)", "setup_s": round(setup_s, 2),
                 "poisson_iters_per_step": it_p / max(args.steps, 1),
                 "poisson_outer_per_step": out_p / max(args.steps, 1),
                 "helmholtz_iters_per_step": it_h / max(args.steps, 1),
                 "phase_ms_per_step": {k: round(v / max(nprof, 1), 3) for k, v in prof.items()},
+                "same_steps_iters": {"timed": it_p, "profiled": it_prof, "e2e": it_e2e},
                 "last_poisson_relres": st.poisson_relres, "status": st.status,
                 "warm_start": ws_info or {"guess": "previous increment"},
                 "multigrid": tune or {"omega": 1.0, "corr": 1.5, "autotuned": False},
                 "mg_cell_shift": ("per geometry, chosen: " + " ".join(
                     f"{sx}{sy}" for sx, sy in shifts)) if shifts else "0 0 (all geometries)"})
+    dtype = {"mixed": "f32 inner / f64 residual", "fp64": "f64", "mg32": "f64 Krylov / f32 V-cycle"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32-inner/f64" if args.precision == "mixed" else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype[form],
             "data": "synthetic", "config": cfg,
             "roofline": roof,
             "roofline_other": roof_other,
-            "e2e": {"value": N * k2 * ws / e2e_s, "unit": UNIT,
-                    "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 4 * 8 * N},
+            "e2e": {"value": N * args.steps * ws / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 4 * 8 * N,
+                    "same_steps_as_value": it_e2e == it_p},
             # per step: rhs, Helmholtz, divergence, Poisson, stats, projection; the
             # learned guess adds scales, scatter, six convolutions and gather
             "gpu_launches": (6 + (9 if ws_info else 0)) * args.steps,
             "clocks": clk}
+    if fp64_cmp is not None:
+        line["fp64_same_steps"] = fp64_cmp
+    if batch is not None:
+        line["batch_64_cavities"] = batch
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

@@ -200,6 +200,28 @@ vip_status vip_step(vip_ctx* ctx, int32_t nsteps);
  * last pressure increment.  Synchronises the stream. */
 vip_status vip_get_state(vip_ctx* ctx, double* u, double* v, double* p, double* phi);
 
+/* ---- checkpoint and resume (not in the paper) --------------------------------
+ * A checkpoint holds everything the next fractional step depends on: u^n, v^n,
+ * p^n, the last pressure increment phi (the Poisson solve's initial guess), the
+ * convection term N^{n-1} of the Adams-Bashforth extrapolation (Eq. 12), the held
+ * Dirichlet values and the step counter (which selects the first step's Euler
+ * start).  Restoring it makes the following vip_step calls repeat, bit for bit,
+ * the steps that followed the save (the kernels' reductions are deterministic).
+ * Statistics counters (vip_get_stats totals, vip_get_geometry_iters) are not part
+ * of it.  Layout: a 64-byte header (magic, node/row/geometry counts, host step
+ * count, checksum = the sum modulo 2^64 of the body's 64-bit words), then eight
+ * arrays of R doubles in the padded row space, then the step counter; R is an
+ * internal size, so buffers are sized by vip_checkpoint_size.
+ *
+ * vip_checkpoint_size: *bytes = the buffer size for this context.  After vip_build.
+ * vip_checkpoint: save != 0 writes a checkpoint to buf (host or device memory of
+ * `bytes` bytes, caller-owned); save == 0 restores one, returning VIP_ERR_ARG
+ * (state unchanged) if buf holds no checkpoint of a context of the same sizes or
+ * its checksum does not match.  Synchronous; uses a device scratch buffer of the
+ * checkpoint's size when buf is host memory, freed before it returns. */
+vip_status vip_checkpoint_size(vip_ctx* ctx, int64_t* bytes);
+vip_status vip_checkpoint(vip_ctx* ctx, int save, void* buf);
+
 /* enable != 0: vip_step waits for each step and adds the CUDA-event time of
  * every phase (VIP_PHASE_*) to a running total; 0 stops it.  Enabling resets
  * the totals. */

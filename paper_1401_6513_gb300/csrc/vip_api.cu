@@ -39,6 +39,26 @@ __global__ void k_stats(const int32_t* __restrict__ it, const int32_t* __restric
     }
 }
 
+// Sum of the 64-bit words of a buffer modulo 2^64 (order-free, so deterministic
+// with atomics): the checkpoint's checksum.
+__global__ void k_word_sum(const uint64_t* __restrict__ w, int64_t n, unsigned long long* out) {
+    unsigned long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += w[i];
+    atomicAdd(out, s);
+}
+
+// Checkpoint layout: this header, then the arrays of ckpt_arrays() in that order,
+// R doubles each (padded row space), then the step counter (int64).
+struct CkptHeader {
+    uint64_t magic;      // "VIPCKPT1"
+    int64_t n_nodes, n_rows, n_geoms;
+    int64_t host_steps;
+    uint64_t checksum;   // k_word_sum of everything after the header
+    uint64_t pad[2];
+};
+constexpr uint64_t CKPT_MAGIC = 0x3154504B43504956ull;
+
 vip_status fail(vip_ctx* c, vip_status s, const char* msg) {
     if (c) c->err = msg;
     return s;
@@ -549,6 +569,76 @@ vip_status vip_get_state(vip_ctx* c, double* u, double* v, double* p, double* ph
     if (p && (s = gather_out(c, c->p, p)) != VIP_OK) return s;
     if (phi && (s = gather_out(c, c->phi, phi)) != VIP_OK) return s;
     VIP_CUDA(cudaStreamSynchronize(c->stream));
+    return VIP_OK;
+}
+
+vip_status vip_checkpoint_size(vip_ctx* c, int64_t* bytes) {
+    if (!c || !bytes) return VIP_ERR_ARG;
+    if (!c->built) return fail(c, VIP_ERR_ARG, "vip_checkpoint_size before vip_build");
+    *bytes = (int64_t)sizeof(CkptHeader) + 8 * c->R * 8 + 8;
+    return VIP_OK;
+}
+
+vip_status vip_checkpoint(vip_ctx* c, int save, void* buf) {
+    if (!c || !buf) return VIP_ERR_ARG;
+    if (!c->built) return fail(c, VIP_ERR_ARG, "vip_checkpoint before vip_build");
+    VIP_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = c->stream;
+    double* arrays[8] = {c->u, c->v, c->p, c->phi, c->nu_prev, c->nv_prev, c->ubc, c->vbc};
+    char* body = static_cast<char*>(buf) + sizeof(CkptHeader);
+    const int64_t nbody = 8 * c->R * 8 + 8;
+    // checksum of the body as it lies in buf (host or device): summed on the device
+    auto checksum = [&](uint64_t* out) -> vip_status {
+        DeviceScratch d_body, d_sum;
+        cudaPointerAttributes at{};
+        const bool on_dev = cudaPointerGetAttributes(&at, buf) == cudaSuccess &&
+                            (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+        cudaGetLastError();
+        const uint64_t* w = reinterpret_cast<const uint64_t*>(body);
+        if (!on_dev) {
+            VIP_CUDA(cudaMalloc(&d_body.p, nbody));
+            VIP_CUDA(cudaMemcpyAsync(d_body.p, body, nbody, cudaMemcpyDefault, st));
+            w = static_cast<const uint64_t*>(d_body.p);
+        }
+        VIP_CUDA(cudaMalloc(&d_sum.p, 8));
+        VIP_CUDA(cudaMemsetAsync(d_sum.p, 0, 8, st));
+        k_word_sum<<<152, 256, 0, st>>>(w, nbody / 8, static_cast<unsigned long long*>(d_sum.p));
+        VIP_CUDA(cudaGetLastError());
+        VIP_CUDA(cudaMemcpyAsync(out, d_sum.p, 8, cudaMemcpyDeviceToHost, st));
+        VIP_CUDA(cudaStreamSynchronize(st));
+        return VIP_OK;
+    };
+    vip_status s;
+    if (save) {
+        for (int k = 0; k < 8; ++k)
+            VIP_CUDA(cudaMemcpyAsync(body + (int64_t)k * c->R * 8, arrays[k], c->R * 8, cudaMemcpyDefault, st));
+        VIP_CUDA(cudaMemcpyAsync(body + 8 * c->R * 8, c->d_step, 8, cudaMemcpyDefault, st));
+        VIP_CUDA(cudaStreamSynchronize(st));
+        CkptHeader h{};
+        h.magic = CKPT_MAGIC;
+        h.n_nodes = c->N;
+        h.n_rows = c->R;
+        h.n_geoms = (int64_t)c->geoms.size();
+        h.host_steps = c->host_steps;
+        if ((s = checksum(&h.checksum)) != VIP_OK) return s;
+        VIP_CUDA(cudaMemcpyAsync(buf, &h, sizeof(h), cudaMemcpyDefault, st));
+        VIP_CUDA(cudaStreamSynchronize(st));
+        return VIP_OK;
+    }
+    CkptHeader h{};
+    VIP_CUDA(cudaMemcpyAsync(&h, buf, sizeof(h), cudaMemcpyDefault, st));
+    VIP_CUDA(cudaStreamSynchronize(st));
+    if (h.magic != CKPT_MAGIC || h.n_nodes != c->N || h.n_rows != c->R || h.n_geoms != (int64_t)c->geoms.size())
+        return fail(c, VIP_ERR_ARG, "vip_checkpoint: the buffer holds no checkpoint of this context");
+    uint64_t sum = 0;
+    if ((s = checksum(&sum)) != VIP_OK) return s;
+    if (sum != h.checksum) return fail(c, VIP_ERR_ARG, "vip_checkpoint: checksum mismatch");
+    for (int k = 0; k < 8; ++k)
+        VIP_CUDA(cudaMemcpyAsync(arrays[k], body + (int64_t)k * c->R * 8, c->R * 8, cudaMemcpyDefault, st));
+    VIP_CUDA(cudaMemcpyAsync(c->d_step, body + 8 * c->R * 8, 8, cudaMemcpyDefault, st));
+    VIP_CUDA(cudaMemsetAsync(c->d_status, 0, 4, st));
+    VIP_CUDA(cudaStreamSynchronize(st));
+    c->host_steps = h.host_steps;
     return VIP_OK;
 }
 

@@ -35,7 +35,8 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_set_profiling", "vip_get_profile", "vip_ws_collect", "vip_ws_train",
            "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static",
            "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout",
-           "vip_multigrid_info", "vip_set_mg_shift", "vip_set_refinement"]
+           "vip_multigrid_info", "vip_set_mg_shift", "vip_set_refinement", "vip_checkpoint_size",
+           "vip_checkpoint"]
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -93,6 +94,8 @@ def lib(path: str | Path | None = None):
         "vip_set_flow": ([vp, i32, dbl, dbl], C.c_int),
         "vip_set_solver": ([vp, C.c_int, dbl, i32, C.c_int], C.c_int),
         "vip_set_refinement": ([vp, dbl], C.c_int),
+        "vip_checkpoint_size": ([vp, C.POINTER(i64)], C.c_int),
+        "vip_checkpoint": ([vp, C.c_int, vp], C.c_int),
         "vip_build": ([vp], C.c_int),
         "vip_set_state": ([vp, vp, vp, vp], C.c_int),
         "vip_step": ([vp, i32], C.c_int),
@@ -296,6 +299,23 @@ class Context:
         self._check(self.L.vip_get_state(self.h, _ptr(u), _ptr(v), _ptr(p), _ptr(phi)))
         return u, v, p, phi
 
+    def vip_checkpoint_size(self) -> int:
+        n = C.c_int64()
+        self._check(self.L.vip_checkpoint_size(self.h, C.byref(n)))
+        return n.value
+
+    def vip_checkpoint(self, save, buf=None):
+        """save=True: write a checkpoint into buf (a uint8 numpy array or a tensor of
+        vip_checkpoint_size() bytes; allocated on the host if None) and return it;
+        save=False: restore the checkpoint held in buf."""
+        if buf is None:
+            if not save:
+                raise ValueError("restoring needs a buffer")
+            buf = np.zeros(self.vip_checkpoint_size(), np.uint8)
+        ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else buf.ctypes.data
+        self._check(self.L.vip_checkpoint(self.h, 1 if save else 0, C.c_void_p(ptr)))
+        return buf
+
     def vip_get_stats(self) -> StepStats:
         s = StepStats()
         self._check(self.L.vip_get_stats(self.h, C.byref(s)))
@@ -403,6 +423,52 @@ def choose_mg_shifts(nodesets, steps=2, make=None, **solver_kw):
     best = its.argmin(axis=0)
     return [(0 if ns.Lx > 0 else MG_SHIFTS[b][0], 0 if ns.Ly > 0 else MG_SHIFTS[b][1])
             for ns, b in zip(nodesets, best)], its
+
+
+PREC_NAMES = {VIP_PREC_FP64: "fp64", VIP_PREC_MIXED: "mixed", VIP_PREC_MG32: "mg32"}
+
+
+def choose_precision(ctx, candidates=(VIP_PREC_MIXED, VIP_PREC_FP64), steps=2, rtol=1e-8,
+                     max_iters=50000, identity=VIP_IDENTITY_EXACT):
+    """Precision form of the Krylov solves chosen by measurement: from one checkpoint of
+    the context's current state, every form in `candidates` takes one untimed step
+    (its step graph is captured) and then, again from the checkpoint, `steps` steps
+    whose device time is the sum of the step phases' CUDA-event times
+    (vip_set_profiling).  A form whose steps fail (any device status) is left out.
+    The fastest form is set on the context and the state restored, so the caller
+    continues from where it was.  Every form stops its solves on the same FP64
+    residual, so the choice changes cost, not the tolerance.  Returns (precision,
+    table of {precision, ms, poisson_iters, error})."""
+    ck = ctx.vip_checkpoint(True)
+    table, times = [], {}
+    for prec in candidates:
+        rec = {"precision": PREC_NAMES.get(prec, prec), "ms": None}
+        try:
+            ctx.vip_set_solver(prec, rtol, max_iters, identity)
+            ctx.vip_checkpoint(False, ck)
+            ctx.vip_step(1)
+            ctx.vip_checkpoint(False, ck)
+            s0 = ctx.vip_get_stats()
+            ctx.vip_set_profiling(True)
+            try:
+                ctx.vip_step(steps)
+                s1 = ctx.vip_get_stats()
+                phase_ms, n = ctx.vip_get_profile()
+            finally:
+                ctx.vip_set_profiling(False)
+            rec["ms"] = sum(phase_ms.values()) / max(n, 1)
+            rec["poisson_iters"] = (s1.total_poisson_iters - s0.total_poisson_iters) / steps
+            times[prec] = rec["ms"]
+        except VipError as e:
+            rec["error"] = str(e)
+        table.append(rec)
+    if not times:
+        ctx.vip_checkpoint(False, ck)
+        raise VipError(VIP_ERR_NOT_CONVERGED, "choose_precision: no form completed its steps")
+    best = min(times, key=times.get)
+    ctx.vip_set_solver(best, rtol, max_iters, identity)
+    ctx.vip_checkpoint(False, ck)
+    return best, table
 
 
 def geometry_signature(nodesets) -> str:

@@ -173,3 +173,80 @@ def test_choose_mg_shifts_builds_each_distinct_assignment_once():
     shifts, its = vip.choose_mg_shifts(boxes, make=make)
     assert made == [[(0, 0), (0, 0)]]
     assert shifts == [(0, 0), (0, 0)] and (its == [[12, 15]] * 4).all()
+
+
+class FakeFormCtx:
+    """Per precision form: step time (ms) and whether its steps fail on the device."""
+
+    def __init__(self, ms, failing=()):
+        self.ms, self.failing = ms, set(failing)
+        self.prec = None
+        self.state = "initial"
+        self.saved = None
+        self.profiling = False
+        self.steps_profiled = 0
+        self.total = 0
+        self.failed = False
+
+    def vip_checkpoint(self, save, buf=None):
+        if save:
+            return ("ckpt", self.state)
+        self.state = buf[1]
+        self.failed = False
+        return buf
+
+    def vip_set_solver(self, prec, rtol, max_iters, identity):
+        self.prec = prec
+
+    def vip_step(self, n):
+        self.state = ("stepped", self.prec)
+        self.total += 10 * n
+        if self.prec in self.failing:
+            self.failed = True
+        if self.profiling:
+            self.steps_profiled += n
+
+    def vip_get_stats(self):
+        if self.failed:
+            raise vip.VipError(vip.VIP_ERR_NONFINITE, "device reported status 6")
+        return FakeStats(self.total)
+
+    def vip_set_profiling(self, on):
+        self.profiling = bool(on)
+        if on:
+            self.steps_profiled = 0
+
+    def vip_get_profile(self):
+        n = self.steps_profiled
+        return {"rhs": 0.0, "poisson": self.ms[self.prec] * n}, n
+
+
+def test_choose_precision_picks_fastest_form_and_restores_state():
+    ctx = FakeFormCtx({vip.VIP_PREC_MIXED: 20.0, vip.VIP_PREC_FP64: 29.0, vip.VIP_PREC_MG32: 23.0})
+    best, table = vip.choose_precision(ctx, candidates=(vip.VIP_PREC_FP64, vip.VIP_PREC_MIXED,
+                                                        vip.VIP_PREC_MG32), steps=3)
+    assert best == vip.VIP_PREC_MIXED and ctx.prec == vip.VIP_PREC_MIXED
+    assert ctx.state == "initial"  # the caller continues from where it was
+    assert [r["ms"] for r in table] == [29.0, 20.0, 23.0]
+
+
+def test_choose_precision_skips_a_failing_form():
+    ctx = FakeFormCtx({vip.VIP_PREC_MIXED: 90.0, vip.VIP_PREC_FP64: 74.0, vip.VIP_PREC_MG32: 10.0},
+                      failing={vip.VIP_PREC_MG32})
+    best, table = vip.choose_precision(ctx, candidates=(vip.VIP_PREC_MG32, vip.VIP_PREC_MIXED,
+                                                        vip.VIP_PREC_FP64))
+    assert best == vip.VIP_PREC_FP64
+    assert table[0]["ms"] is None and "NONFINITE" in table[0]["error"]
+    assert not ctx.profiling and ctx.state == "initial"
+
+
+def test_choose_precision_raises_when_every_form_fails():
+    ctx = FakeFormCtx({vip.VIP_PREC_MIXED: 1.0, vip.VIP_PREC_FP64: 1.0},
+                      failing={vip.VIP_PREC_MIXED, vip.VIP_PREC_FP64})
+    try:
+        vip.choose_precision(ctx)
+    except vip.VipError as e:
+        assert e.status == vip.VIP_ERR_NOT_CONVERGED
+    else:
+        raise AssertionError("expected VipError")
+    assert ctx.state == "initial"
