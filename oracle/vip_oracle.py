@@ -14,7 +14,9 @@ garbled the reading used is stated at the function (the readings are listed in
 one place in the design notes of the repository).
 
 Pins (tests/test_oracle_*.py, all CPU):
-  * weight functions: values, continuity and support (Sec. 3);
+  * weight functions: values, continuity and support; the printed weight's
+    expansion at both ends of its support, Phi(1 - s) = s^12 (1 + 2s + ...) and
+    (1 - Phi(r)) / r -> 4 (Sec. 3);
   * neighbour search: brute force on small node sets, periodic and not;
   * MLS weights: exact reproduction of the six quadratic monomials and their
     derivatives, and agreement with a brute-force weighted least-squares fit by
@@ -27,6 +29,11 @@ Pins (tests/test_oracle_*.py, all CPU):
   * full step: observed second order in space and time on the decaying
     vortices (Sec. 5.1) and the divergence of the projected velocity at the
     Poisson tolerance in the composite-operator reading (Eqs. 13-14);
+  * the alternative readings: pressure="kim_moin" gives the time-centred
+    pressure of the decaying vortices (closed form at t - dt/2) and the
+    incremental reading's pressure (Eq. 15); identity="mls" agrees with the exact
+    identity on quadratics and keeps second order (Eq. 12, Eq. vip:1); mistakes
+    planted in these pins are caught (test_planted_mistakes_are_caught);
   * normal points (flag probes="inside", tests/test_paper_values.py): inside
     the exact edges of the 28-degree wedge cavity, unchanged on the square
     cavity, and the wedge's steps stable with them and unstable without.

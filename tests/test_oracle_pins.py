@@ -46,6 +46,25 @@ def test_paper_weight_values():
     assert f(0.5) == pytest.approx((1 - 0.5 ** 0.25) ** 4, rel=1e-14)
 
 
+def paper_weight_asymptotics_hold(f):
+    for s in (1e-2, 1e-3):
+        ratio = float(f(1.0 - s)) / s ** 12
+        if not abs(ratio - (1.0 + 2.0 * s)) <= 4.0 * s * s:
+            return False
+    r = 1e-6
+    return abs((1.0 - float(f(r))) / r - 4.0) <= 2e-4
+
+
+def test_paper_weight_asymptotics_at_both_ends():
+    """The printed weight's behaviour at the ends of its support, from its expansion
+    rather than from the formula itself.  With r = 1 - s, r^((1-r)^2) = exp(s^2 ln(1-s))
+    = 1 - s^3 - s^4/2 + O(s^5), so Phi(1 - s) = s^12 (1 + 2s + O(s^2)): the power 12
+    comes from the squared exponent (s^3) and the fourth power together, so an exponent
+    (1 - r) (s^8) or a square in place of the fourth power (s^6) fails.  Near the centre
+    r^((1-r)^2) = r^(1 - 2r + r^2) = r (1 - 2 r ln r + ...), so (1 - Phi(r)) / r -> 4."""
+    assert paper_weight_asymptotics_hold(vo.weight_paper)
+
+
 # ---------------------------------------------------------------------------
 # Sec. 3: neighbourhoods against brute force
 # ---------------------------------------------------------------------------
@@ -374,3 +393,105 @@ def test_closed_domain_poisson_is_solvable():
     r = fs.b_last - (L @ fs.phi) - fs.mu * inner
     assert np.max(np.abs(r[inner])) <= 1e-9 * max(1.0, np.max(np.abs(fs.b_last)))
     assert st["res_p"] <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2, Eq. (15) and Eq. (12): the alternative readings of the fractional step
+# ---------------------------------------------------------------------------
+
+def kim_moin_errors(fs_class=vo.FractionalStep):
+    """(error of the kim_moin pressure against the closed form at t - dt/2, its
+    difference from the incremental reading's pressure, its largest value) on the
+    decaying vortices, Re = 1, 48 x 48, dt = 0.02, ten steps."""
+    ns = w.periodic_box(48, Re=1.0, dt=0.02)
+    ops = vo.Operators(ns)
+    km = fs_class(ops, rtol=1e-12, pressure="kim_moin")
+    inc = vo.FractionalStep(ops, rtol=1e-12, pressure="incremental")
+    for _ in range(10):
+        km.step()
+        inc.step()
+    _, _, pe = w.taylor_green(ns.x, ns.y, 10 * 0.02 - 0.01, 1.0)
+    rel = lambda a, b: np.linalg.norm((a - a.mean()) - (b - b.mean())) / np.linalg.norm(b - b.mean())  # noqa: E731
+    return rel(km.p, pe), rel(km.p, inc.p), float(np.max(np.abs(km.p)))
+
+
+def kim_moin_holds(fs_class=vo.FractionalStep):
+    e_half, e_inc, pmax = kim_moin_errors(fs_class)
+    return e_half <= 3e-3 and e_inc <= 1e-4 and pmax < 1.0
+
+
+def test_kim_moin_pressure_is_time_centred():
+    """pressure='kim_moin' (r^n as printed, without G p^n, and p^{n+1} = phi -
+    (dt/2Re) L phi).  With the Crank-Nicolson step of Eq. (12) that pressure is the
+    one centred between the time levels: on the decaying vortices (Sec. 5.1; Re = 1,
+    48 x 48, dt = 0.02, ten steps) it matches the closed form at t - dt/2 to 3e-3
+    relative L2 (mean removed), where flipping the sign of the (dt/2Re) L phi term
+    misses by 7.6e-2 and dropping it by 3.7e-2.  The incremental reading (r^n with
+    -G p^n, p^{n+1} = p^n + phi - (dt/2Re) L phi) gives the same pressure: the two
+    differ only through the approximate projection (L is not D_vip G_vip), by ~1e-5.
+    The pressure is not accumulated in this reading, so it stays O(1)."""
+    assert kim_moin_holds()
+
+
+def mls_identity_quadratics_hold(ops, identity_op=None):
+    """Both readings' Helmholtz and right-hand-side operators agree on quadratics at
+    interior rows (identity_op replaces D^[0,0] for planted mistakes)."""
+    if identity_op is not None:
+        ops.D = dict(ops.D)
+        ops.D[(0, 0)] = identity_op
+    a = vo.FractionalStep(ops, rtol=1e-12, identity="mls")
+    b = vo.FractionalStep(ops, rtol=1e-12, identity="exact")
+    x, y = ops.ns.x, ops.ns.y
+    for q in (np.ones_like(x), x, y, x * x, x * y, y * y):
+        for A, B in ((a.Hu, b.Hu), (a.Hv, b.Hv), (a.Rm, b.Rm)):
+            d = (A @ q - B @ q)[a.inner]
+            scale = np.max(np.abs(B @ q)) + np.max(np.abs(q))
+            if not np.max(np.abs(d)) <= 1e-11 * scale:
+                return False
+    return True
+
+
+def test_mls_identity_reading():
+    """identity='mls' (I = D^[0,0] wherever Eq. 12 writes I, Eq. vip:1).  (a) D^[0,0]
+    reproduces quadratics, so on a cavity node set both readings' Helmholtz operators
+    and right-hand-side operator agree on every quadratic field at interior rows (to
+    rounding); an operator other than D^[0,0] in place of I fails there.  (b) The
+    scheme stays second order in space on the decaying vortices (observed order >= 1.8
+    from 16 to 64 nodes per side, as with the exact identity)."""
+    assert mls_identity_quadratics_hold(vo.Operators(w.cavity(12, Re=100.0)))
+    e = [tg_error(n, 0.05, 1e-3, identity="mls")[1] for n in (16, 32, 64)]
+    orders = [math.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert min(orders) >= 1.8, orders
+
+
+def test_planted_mistakes_are_caught():
+    """Mistakes planted in the oracle (on the CPU) fail the pins written for them:
+    the printed weight with exponent (1 - r) or a square in place of the fourth power;
+    the kim_moin pressure with the sign of its (dt/2Re) L phi term flipped, with the
+    term dropped, or accumulated onto p^n; D^[1,0] in place of D^[0,0] as the identity."""
+    assert not paper_weight_asymptotics_hold(lambda r: np.where(np.asarray(r) < 1, (1 - np.power(r, 1 - np.asarray(r))) ** 4, 0.0))
+    assert not paper_weight_asymptotics_hold(lambda r: np.where(np.asarray(r) < 1, (1 - np.power(r, (1 - np.asarray(r)) ** 2)) ** 2, 0.0))
+
+    class Flipped(vo.FractionalStep):
+        def step(self):
+            st = super().step()
+            self.p = self.phi + self.alpha * (self.ops.L @ self.phi)
+            return st
+
+    class Dropped(vo.FractionalStep):
+        def step(self):
+            st = super().step()
+            self.p = self.phi.copy()
+            return st
+
+    class Accumulated(vo.FractionalStep):
+        def step(self):
+            p0 = self.p.copy()
+            st = super().step()
+            self.p = p0 + self.p
+            return st
+
+    for planted in (Flipped, Dropped, Accumulated):
+        assert not kim_moin_holds(planted), planted.__name__
+    ops = vo.Operators(w.cavity(12, Re=100.0))
+    assert not mls_identity_quadratics_hold(ops, identity_op=ops.D[(1, 0)])
