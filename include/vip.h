@@ -367,6 +367,14 @@ vip_status vip_ws_params(vip_ctx* ctx, int direction, float* buf, int64_t* count
 vip_status vip_ws_eval(vip_ctx* ctx, int32_t H, int32_t W, const float* x, float* y, float* grads,
                        const float* target, const float* mask, double* loss);
 
+/* One Adam update of the network parameters (the optimiser of vip_ws_train:
+ * beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, FP32) with step size lr > 0,
+ * applied to the gradients of the last vip_ws_eval call that computed gradients
+ * (or of the last training sample); the step count runs from the last load of the
+ * parameters by vip_ws_params (direction 1), which also zeroes the moments.
+ * Synchronous.  With vip_ws_eval it lets a caller train on samples of its own. */
+vip_status vip_ws_adam(vip_ctx* ctx, double lr);
+
 /* ---- BiCGSTAB without device allocation -----------------------------------
  * An addition of this library; the paper has no counterpart.  For callers that
  * must not allocate device memory while they run: a process whose device memory
@@ -389,13 +397,19 @@ vip_status vip_ws_eval(vip_ctx* ctx, int32_t H, int32_t W, const float* x, float
  * Workspace: file-scope static device memory, at most VIP_STATIC_MAX_ROWS rows;
  * larger n returns VIP_ERR_ARG before any device work.  Each call clears the
  * barrier words and result record it uses (on cuda_stream); nothing needs to be
- * zero beforehand.  The first call on a device looks up the workspace's device
- * address (and loads the module there): make it before any stream capture on
- * that device.  All calls on one device share the one workspace, so calls that
- * overlap in time on that device (other streams, other host threads) race and
- * must be serialised by the caller.  Errors: VIP_ERR_ARG (bad size, tolerance,
- * NULL or host pointer), VIP_ERR_CUDA, VIP_ERR_BREAKDOWN, VIP_ERR_NOT_CONVERGED,
- * VIP_ERR_TIMEOUT (a grid-barrier wait ran out; the result is not valid). */
+ * zero beforehand.  The call is synchronous (it waits for cuda_stream and reads
+ * its result back), so it cannot be recorded into a CUDA graph: on a stream that
+ * is capturing it returns VIP_ERR_ARG before any work, leaving the capture
+ * intact.  The first call on a device looks up the workspace's device address
+ * (and loads the module there) and keeps it for the life of the process; after
+ * a cudaDeviceReset of that device the kept address is stale, so a process that
+ * resets a device must not call this entry point on it again.  All calls on one
+ * device share the one workspace, so calls that overlap in time on that device
+ * (other streams, other host threads) race and must be serialised by the caller.
+ * Errors: VIP_ERR_ARG (bad size or tolerance; a NULL pointer, a host pointer or
+ * memory of another device; a capturing stream), VIP_ERR_CUDA,
+ * VIP_ERR_BREAKDOWN, VIP_ERR_NOT_CONVERGED, VIP_ERR_TIMEOUT (a grid-barrier wait
+ * ran out; the result is not valid). */
 #define VIP_STATIC_MAX_ROWS 131072
 vip_status vip_bicgstab_static(int device, void* cuda_stream, int64_t n, const int64_t* row_ptr,
                                const int32_t* col, const double* val, const double* b, double* x,

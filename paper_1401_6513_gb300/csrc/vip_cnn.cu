@@ -665,6 +665,17 @@ vip_status vip_ws_train(vip_ctx* c, vip_train_cfg* cfg) {
     return VIP_OK;
 }
 
+vip_status vip_ws_adam(vip_ctx* c, double lr) {
+    if (!c) return VIP_ERR_ARG;
+    if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_adam before vip_build");
+    if (!(lr > 0)) return fail(c, VIP_ERR_ARG, "vip_ws_adam: lr must be > 0");
+    Cnn& N = *cnn_of(c);
+    vip_status st = adam(c, N, lr, c->stream);
+    if (st != VIP_OK) return st;
+    VIP_CUDA(cudaStreamSynchronize(c->stream));
+    return VIP_OK;
+}
+
 vip_status vip_ws_params(vip_ctx* c, int direction, float* buf, int64_t* count) {
     if (!c) return VIP_ERR_ARG;
     if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_params before vip_build");

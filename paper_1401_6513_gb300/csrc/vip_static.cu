@@ -266,13 +266,15 @@ vip_status setup(int device, double** ws, unsigned int** bar) {
     return VIP_OK;
 }
 
-bool on_device(const void* q) {
+// q is managed memory, or device memory of `device` (memory of another GPU would be
+// read as a peer address, which faults without peer access)
+bool on_device(const void* q, int device) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == device);
 }
 
 }  // namespace
@@ -285,13 +287,19 @@ extern "C" vip_status vip_bicgstab_static(int device, void* cuda_stream, int64_t
     if (device < 0 || device >= MAX_DEVICES) return VIP_ERR_ARG;
     DeviceGuard guard(device);
     if (!guard.ok) return VIP_ERR_CUDA;
-    if (!on_device(row_ptr) || !on_device(col) || !on_device(val) || !on_device(b) || !on_device(x))
+    if (!on_device(row_ptr, device) || !on_device(col, device) || !on_device(val, device) ||
+        !on_device(b, device) || !on_device(x, device))
         return VIP_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    {   // the call synchronises its stream and reads results back: it cannot be captured
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return VIP_ERR_CUDA;
+        if (cs != cudaStreamCaptureStatusNone) return VIP_ERR_ARG;
+    }
     double* ws = nullptr;
     unsigned int* bar = nullptr;
     vip_status st0 = setup(device, &ws, &bar);
     if (st0 != VIP_OK) return st0;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     int nsm = 0, occ = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return VIP_ERR_CUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bicgstab_static, THREADS, 0) != cudaSuccess)

@@ -36,7 +36,7 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static",
            "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout",
            "vip_multigrid_info", "vip_set_mg_shift", "vip_set_refinement", "vip_checkpoint_size",
-           "vip_checkpoint"]
+           "vip_checkpoint", "vip_ws_adam"]
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -96,6 +96,7 @@ def lib(path: str | Path | None = None):
         "vip_set_refinement": ([vp, dbl], C.c_int),
         "vip_checkpoint_size": ([vp, C.POINTER(i64)], C.c_int),
         "vip_checkpoint": ([vp, C.c_int, vp], C.c_int),
+        "vip_ws_adam": ([vp, dbl], C.c_int),
         "vip_build": ([vp], C.c_int),
         "vip_set_state": ([vp, vp, vp, vp], C.c_int),
         "vip_step": ([vp, i32], C.c_int),
@@ -274,6 +275,9 @@ class Context:
         cfg = TrainCfg(epochs=int(epochs), lr=float(lr), seed=int(seed))
         self._check(self.L.vip_ws_train(self.h, C.byref(cfg)))
         return cfg
+
+    def vip_ws_adam(self, lr=1e-3):
+        self._check(self.L.vip_ws_adam(self.h, float(lr)))
 
     def vip_ws_params(self, params=None):
         """Return the FP32 parameters; with `params`, load them instead."""

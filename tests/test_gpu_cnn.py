@@ -153,6 +153,35 @@ def test_gradients_match_reference(ctx):
             assert ew < 5e-2 and eb < 5e-2, (k, ci, cout, ew, eb)
 
 
+def test_adam_matches_oracle(ctx):
+    """Three Adam updates on the GPU (vip_ws_adam after vip_ws_eval on three different
+    images) against the oracle's adam_step (oracle/cnn_oracle.py) fed the same
+    gradients, from the same parameters and zero moments, element by element.  The
+    GPU keeps parameters, moments and the update in FP32 (bias corrections by powf):
+    after each update |p_gpu - p_oracle| <= 2^-22 |p| (two FP32 roundings of p)
+    + 1e-5 lr (FP32 arithmetic in the update)."""
+    lr = 1e-3
+    flat = random_params(ctx, 5)  # loading the parameters zeroes the moments and the step count
+    rng = np.random.default_rng(6)
+    H, W = 4, 96
+    p = flat.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for t in (1, 2, 3):
+        x = np.zeros((H, W, 16), np.float32)
+        x[..., :6] = rng.standard_normal((H, W, 6))
+        x = bf16(x)
+        tgt = rng.standard_normal((H, W)).astype(np.float32)
+        msk = (rng.random((H, W)) > 0.3).astype(np.float32)
+        _, g, _ = eval_gpu(ctx, x, tgt, msk, flat.size)
+        ctx.vip_ws_adam(lr)
+        got = ctx.vip_ws_params().astype(np.float64)
+        p, m, v = co.adam_step(p, g.astype(np.float64), m, v, t, lr=lr)
+        bar = 2.0 ** -22 * np.abs(p) + 1e-5 * lr
+        assert np.all(np.abs(got - p) <= bar), (t, np.max(np.abs(got - p) - bar))
+        p = got  # continue from the GPU's FP32 parameters, as the GPU does
+
+
 def test_untrained_network_reproduces_previous_increment_guess(vip):
     """With the untrained (zero last layer) network the warm start equals the plain
     previous-increment guess, so the state matches the run without it."""

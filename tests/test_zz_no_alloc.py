@@ -106,3 +106,27 @@ def test_rejects_bad_arguments(vip):
     # the identity system still solves after the refusals
     st, it, rr = vip.vip_bicgstab_static(0, None, n, dptr, dcol, dval, db, x)
     assert st == vip.VIP_OK and np.allclose(x.cpu().numpy(), 1.0)
+
+
+def test_refuses_a_capturing_stream(vip):
+    """The call synchronises its stream and reads its result back, so on a stream that
+    is being captured into a CUDA graph it returns VIP_ERR_ARG before any work and the
+    capture stays valid."""
+    import torch
+    n = 8
+    dptr = torch.arange(n + 1, dtype=torch.int64, device="cuda")
+    dcol = torch.arange(n, dtype=torch.int32, device="cuda")
+    dval = torch.ones(n, dtype=torch.float64, device="cuda")
+    db = torch.ones(n, dtype=torch.float64, device="cuda")
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        x.add_(0.0)
+        st, _, _ = vip.vip_bicgstab_static(0, s.cuda_stream, n, dptr, dcol, dval, db, x)
+    assert st == vip.VIP_ERR_ARG
+    g.replay()
+    torch.cuda.synchronize()
+    st, it, rr = vip.vip_bicgstab_static(0, None, n, dptr, dcol, dval, db, x)
+    assert st == vip.VIP_OK and np.allclose(x.cpu().numpy(), 1.0)
