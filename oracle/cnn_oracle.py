@@ -11,9 +11,15 @@ benchmark may import it; the GPU path never does.
 Tensor layout: activations [H, W, C] (channels last); weights [3, 3, Cin, Cout]
 indexed [dy+1, dx+1, ci, co]; biases [Cout].
 
+Two losses: the mean squared error of the prediction, and a residual proxy, the
+squared 5-point lattice Laplacian of the error (what the Poisson residual of the
+resulting initial guess measures) plus a small multiple of the squared error.
+
 Pins (tests/test_cnn_oracle.py): the convolution equals an independent direct
-sum over taps; the gradients equal central finite differences; one Adam step
-equals the update written from its definition.
+sum over taps; the lattice Laplacian equals a loop over points and vanishes on
+linear fields away from the image edge; the gradients of both losses equal
+central finite differences; one Adam step equals the update written from its
+definition.
 """
 from __future__ import annotations
 
@@ -74,6 +80,48 @@ def loss_and_grads(params, x, target, mask):
     L = float((d * d).sum() / cnt)
     gy = np.zeros_like(y)
     gy[..., 0] = 2.0 * d / cnt
+    grads = [None] * len(params)
+    for k in range(len(params) - 1, -1, -1):
+        w, b = params[k]
+        gx, gw, gb = conv3x3_backward(acts[k], w, gy)
+        grads[k] = (gw, gb)
+        if k > 0:
+            gy = gx * (acts[k] > 0)
+    return L, grads
+
+
+def lap5(e):
+    """5-point lattice Laplacian in lattice units with zero values outside the image:
+    (Delta e)[i, j] = e[i+1, j] + e[i-1, j] + e[i, j+1] + e[i, j-1] - 4 e[i, j]."""
+    ep = np.pad(e, 1)
+    return ep[2:, 1:-1] + ep[:-2, 1:-1] + ep[1:-1, 2:] + ep[1:-1, :-2] - 4.0 * e
+
+
+def residual_loss(params, x, target, mask, lam):
+    """Residual proxy of an initial guess.  With e = mask (output[..., 0] - target), the
+    error the guess leaves at the active points, the solve starts from the residual
+    L e (L the Poisson operator, ~ Delta / h^2 on the lattice), so the loss is the
+    squared lattice Laplacian of that error plus a small error term:
+        (sum over active points of (Delta e)^2 + lam e^2) / (number of active points)."""
+    y, _ = forward(params, x)
+    m = (mask != 0).astype(np.float64)
+    cnt = max(m.sum(), 1.0)
+    e = m * (y[..., 0] - target)
+    q = m * lap5(e)
+    return float(((q * q).sum() + lam * (e * e).sum()) / cnt)
+
+
+def residual_loss_and_grads(params, x, target, mask, lam):
+    """residual_loss and its parameter gradients by the chain rule: with q = m Delta e,
+    dL/dy = (2 / cnt) m (Delta q + lam e) (Delta is symmetric on zero-padded images)."""
+    y, acts = forward(params, x)
+    m = (mask != 0).astype(np.float64)
+    cnt = max(m.sum(), 1.0)
+    e = m * (y[..., 0] - target)
+    q = m * lap5(e)
+    L = float(((q * q).sum() + lam * (e * e).sum()) / cnt)
+    gy = np.zeros_like(y)
+    gy[..., 0] = 2.0 * m * (lap5(q) + lam * e) / cnt
     grads = [None] * len(params)
     for k in range(len(params) - 1, -1, -1):
         w, b = params[k]
