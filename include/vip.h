@@ -204,12 +204,13 @@ vip_status vip_get_state(vip_ctx* ctx, double* u, double* v, double* p, double* 
  * A checkpoint holds everything the next fractional step depends on: u^n, v^n,
  * p^n, the last pressure increment phi (the Poisson solve's initial guess), the
  * convection term N^{n-1} of the Adams-Bashforth extrapolation (Eq. 12), the held
- * Dirichlet values and the step counter (which selects the first step's Euler
- * start).  Restoring it makes the following vip_step calls repeat, bit for bit,
+ * Dirichlet values, the learned warm start's history (the increment before phi)
+ * and the step counter (which selects the first step's Euler start).  The
+ * network's parameters and the extrapolation coefficient are not part of it.  Restoring it makes the following vip_step calls repeat, bit for bit,
  * the steps that followed the save (the kernels' reductions are deterministic).
  * Statistics counters (vip_get_stats totals, vip_get_geometry_iters) are not part
  * of it.  Layout: a 64-byte header (magic, node/row/geometry counts, host step
- * count, checksum = the sum modulo 2^64 of the body's 64-bit words), then eight
+ * count, checksum = the sum modulo 2^64 of the body's 64-bit words), then nine
  * arrays of R doubles in the padded row space, then the step counter; R is an
  * internal size, so buffers are sized by vip_checkpoint_size.
  *
@@ -328,18 +329,27 @@ vip_status vip_autotune(vip_ctx* ctx, const float* omegas, int32_t nomega, const
                         int32_t ncorr, vip_tune_result* out);
 
 /* ---- learned warm start of the pressure-increment solve ------------------
- * Not part of the paper's method: a 6-layer 3x3 convolutional network (BF16
- * tensor-core kernels, FP32 accumulation) on each geometry's regular background
- * lattice predicts phi^{n+1} - phi^n from u*, v*, the divergence right-hand
- * side, phi^n and node masks.  The Poisson solve then starts from
- * phi^n + S * prediction and runs to the same tolerance (Eq. 13 unchanged).
- * The untrained network predicts 0, i.e. the previous-increment guess. */
+ * Not part of the paper's method: the Poisson solve of Eq. (13) starts from
+ *   phi^n + a (phi^n - phi^{n-1}) + S * prediction
+ * and runs to the same tolerance (Eq. 13 unchanged).  a is a temporal
+ * extrapolation coefficient fitted by least squares on the collected solves;
+ * the prediction is a 6-layer 3x3 convolutional network (BF16 tensor-core
+ * kernels, FP32 accumulation) on each geometry's regular background lattice,
+ * from u*, v*, the divergence right-hand side, phi^n, phi^n - phi^{n-1} and node
+ * masks, trained on what the extrapolation leaves of phi^{n+1} - phi^n, in units
+ * of S D: S the RMS of phi^n and D the RMS of (phi^n - phi^{n-1}) / S, per
+ * geometry.  Untrained (a = 0, last layer zero) the guess is phi^n, the
+ * previous-increment guess. */
 typedef struct {
     int32_t epochs;     /* passes over the collected samples */
     double lr;          /* Adam step size */
     uint64_t seed;      /* sample order */
     double first_loss;  /* out: mean loss of the first epoch */
-    double final_loss;  /* out: mean loss of the last epoch */
+    double final_loss;  /* out: mean loss of the trained network over the samples */
+    double extrap;      /* out: the fitted extrapolation coefficient a */
+    double base_loss;   /* out: mean loss of the extrapolation alone (output zero) */
+    int32_t net_kept;   /* out: 1 if final_loss < base_loss; 0: the network's last
+                           layer was zeroed, the guess is the extrapolation alone */
 } vip_train_cfg;
 
 /* enable != 0: from the next step on, store (network input, solved increment
@@ -347,11 +357,18 @@ typedef struct {
  * steps run without the CUDA graph while collecting.  0 stops collecting. */
 vip_status vip_ws_collect(vip_ctx* ctx, int enable, int32_t max_samples);
 
-/* Train the network on the collected samples (Adam, one sample per update,
- * mean squared error over interior lattice nodes).  Synchronous. */
+/* Fit the extrapolation coefficient a on the collected samples (least squares
+ * over interior lattice nodes, clamped to [-1, 2]), then train the network on
+ * what a (phi^n - phi^{n-1}) leaves of phi^{n+1} - phi^n (Adam, one sample per
+ * update, the loss of vip_ws_set_loss over interior lattice nodes); the network is
+ * kept only if it lowers the mean loss over the samples below that of the
+ * extrapolation alone, else its last layer is zeroed.  Synchronous. */
 vip_status vip_ws_train(vip_ctx* ctx, vip_train_cfg* cfg);
 
-/* enable != 0: use the network's guess in vip_step. */
+/* The Poisson solve's initial guess in vip_step: enable 0: phi^n (the previous
+ * increment); 1: the learned guess, extrapolation plus network; 2: the fitted
+ * extrapolation alone, phi^n + a (phi^n - phi^{n-1}) (no network evaluation).
+ * Other values: VIP_ERR_ARG. */
 vip_status vip_ws_enable(vip_ctx* ctx, int enable);
 
 /* direction 0: copy the FP32 parameters out to buf; 1: load them from buf.
@@ -362,10 +379,26 @@ vip_status vip_ws_params(vip_ctx* ctx, int direction, float* buf, int64_t* count
 
 /* Evaluate the network on one H x W lattice image x[H][W][16] (FP32, converted
  * to BF16); y[H][W] (may be NULL) receives the output.  With target, mask and
- * grads non-NULL also the mean squared error over mask != 0 (*loss) and its
- * parameter gradients (grads, parameter layout).  Synchronous. */
+ * grads non-NULL also the loss set by vip_ws_set_loss over mask != 0 (*loss) and
+ * its parameter gradients (grads, parameter layout).  Synchronous. */
 vip_status vip_ws_eval(vip_ctx* ctx, int32_t H, int32_t W, const float* x, float* y, float* grads,
                        const float* target, const float* mask, double* loss);
+
+/* Loss of the network's training (vip_ws_train) and of vip_ws_eval, over the
+ * interior lattice nodes, with e = prediction - target:
+ *   kind 0: mean squared error, mean of e^2;
+ *   kind 1 (default): residual proxy, mean of (Delta e)^2 + lam e^2, Delta the
+ *           5-point lattice Laplacian (lattice units, zero outside the image):
+ *           the solve starts from the residual the guess leaves, the Poisson
+ *           operator applied to its error, so rough errors weigh more than smooth
+ *           ones.  lam >= 0 (default 0.01).
+ * VIP_ERR_ARG for another kind or a negative weight. */
+vip_status vip_ws_set_loss(vip_ctx* ctx, int kind, double lam);
+
+/* set != 0: set the extrapolation coefficient to *a (in [-1, 2], else
+ * VIP_ERR_ARG); 0: read it into *a.  With vip_ws_params it moves a trained warm
+ * start from one context to another. */
+vip_status vip_ws_extrapolation(vip_ctx* ctx, int set, double* a);
 
 /* One Adam update of the network parameters (the optimiser of vip_ws_train:
  * beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, FP32) with step size lr > 0,

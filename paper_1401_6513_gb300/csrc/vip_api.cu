@@ -48,16 +48,18 @@ __global__ void k_word_sum(const uint64_t* __restrict__ w, int64_t n, unsigned l
     atomicAdd(out, s);
 }
 
-// Checkpoint layout: this header, then the arrays of ckpt_arrays() in that order,
-// R doubles each (padded row space), then the step counter (int64).
+// Checkpoint layout: this header, then CKPT_ARRAYS arrays of R doubles each (padded
+// row space: u, v, p, phi, N_u^{n-1}, N_v^{n-1}, the two Dirichlet value arrays and
+// the warm start's phi^{n-1}), then the step counter (int64).
+constexpr int CKPT_ARRAYS = 9;
 struct CkptHeader {
-    uint64_t magic;      // "VIPCKPT1"
+    uint64_t magic;      // "VIPCKPT2"
     int64_t n_nodes, n_rows, n_geoms;
     int64_t host_steps;
     uint64_t checksum;   // k_word_sum of everything after the header
     uint64_t pad[2];
 };
-constexpr uint64_t CKPT_MAGIC = 0x3154504B43504956ull;
+constexpr uint64_t CKPT_MAGIC = 0x3254504B43504956ull;
 
 vip_status fail(vip_ctx* c, vip_status s, const char* msg) {
     if (c) c->err = msg;
@@ -475,6 +477,7 @@ vip_status vip_set_state(vip_ctx* c, const double* u, const double* v, const dou
     VIP_CUDA(cudaMemcpyAsync(c->ubc, c->u, c->R * 8, cudaMemcpyDeviceToDevice, st));
     VIP_CUDA(cudaMemcpyAsync(c->vbc, c->v, c->R * 8, cudaMemcpyDeviceToDevice, st));
     VIP_CUDA(cudaMemsetAsync(c->phi, 0, c->R * 8, st));
+    if ((s = cnn_reset_history(c)) != VIP_OK) return s;
     VIP_CUDA(cudaMemsetAsync(c->nu_prev, 0, c->R * 8, st));
     VIP_CUDA(cudaMemsetAsync(c->nv_prev, 0, c->R * 8, st));
     VIP_CUDA(cudaMemsetAsync(c->d_step, 0, 8, st));
@@ -575,7 +578,7 @@ vip_status vip_get_state(vip_ctx* c, double* u, double* v, double* p, double* ph
 vip_status vip_checkpoint_size(vip_ctx* c, int64_t* bytes) {
     if (!c || !bytes) return VIP_ERR_ARG;
     if (!c->built) return fail(c, VIP_ERR_ARG, "vip_checkpoint_size before vip_build");
-    *bytes = (int64_t)sizeof(CkptHeader) + 8 * c->R * 8 + 8;
+    *bytes = (int64_t)sizeof(CkptHeader) + CKPT_ARRAYS * c->R * 8 + 8;
     return VIP_OK;
 }
 
@@ -584,9 +587,11 @@ vip_status vip_checkpoint(vip_ctx* c, int save, void* buf) {
     if (!c->built) return fail(c, VIP_ERR_ARG, "vip_checkpoint before vip_build");
     VIP_CUDA(cudaSetDevice(c->device));
     cudaStream_t st = c->stream;
-    double* arrays[8] = {c->u, c->v, c->p, c->phi, c->nu_prev, c->nv_prev, c->ubc, c->vbc};
+    double* arrays[CKPT_ARRAYS] = {c->u, c->v, c->p, c->phi, c->nu_prev, c->nv_prev, c->ubc, c->vbc,
+                                   cnn_history(c)};
+    if (!arrays[CKPT_ARRAYS - 1]) return fail(c, VIP_ERR_ARG, "vip_checkpoint: no warm-start state");
     char* body = static_cast<char*>(buf) + sizeof(CkptHeader);
-    const int64_t nbody = 8 * c->R * 8 + 8;
+    const int64_t nbody = CKPT_ARRAYS * c->R * 8 + 8;
     // checksum of the body as it lies in buf (host or device): summed on the device
     auto checksum = [&](uint64_t* out) -> vip_status {
         DeviceScratch d_body, d_sum;
@@ -610,9 +615,9 @@ vip_status vip_checkpoint(vip_ctx* c, int save, void* buf) {
     };
     vip_status s;
     if (save) {
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < CKPT_ARRAYS; ++k)
             VIP_CUDA(cudaMemcpyAsync(body + (int64_t)k * c->R * 8, arrays[k], c->R * 8, cudaMemcpyDefault, st));
-        VIP_CUDA(cudaMemcpyAsync(body + 8 * c->R * 8, c->d_step, 8, cudaMemcpyDefault, st));
+        VIP_CUDA(cudaMemcpyAsync(body + CKPT_ARRAYS * c->R * 8, c->d_step, 8, cudaMemcpyDefault, st));
         VIP_CUDA(cudaStreamSynchronize(st));
         CkptHeader h{};
         h.magic = CKPT_MAGIC;
@@ -633,9 +638,9 @@ vip_status vip_checkpoint(vip_ctx* c, int save, void* buf) {
     uint64_t sum = 0;
     if ((s = checksum(&sum)) != VIP_OK) return s;
     if (sum != h.checksum) return fail(c, VIP_ERR_ARG, "vip_checkpoint: checksum mismatch");
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < CKPT_ARRAYS; ++k)
         VIP_CUDA(cudaMemcpyAsync(arrays[k], body + (int64_t)k * c->R * 8, c->R * 8, cudaMemcpyDefault, st));
-    VIP_CUDA(cudaMemcpyAsync(c->d_step, body + 8 * c->R * 8, 8, cudaMemcpyDefault, st));
+    VIP_CUDA(cudaMemcpyAsync(c->d_step, body + CKPT_ARRAYS * c->R * 8, 8, cudaMemcpyDefault, st));
     VIP_CUDA(cudaMemsetAsync(c->d_status, 0, 4, st));
     VIP_CUDA(cudaStreamSynchronize(st));
     c->host_steps = h.host_steps;

@@ -77,25 +77,36 @@ __global__ void k_pack_bias(const float* __restrict__ b, int creal, int cout, fl
 }
 
 // per-geometry scales (one block per geometry, fixed order)
+// Per geometry (one block each): s_b the RMS of b over interior nodes; S the RMS of
+// phi^n (s_b h^2 if phi^n = 0); D the RMS of (phi^n - phi^{n-1}) / S over interior
+// nodes (1 if zero): the network sees the history channel and predicts its
+// correction in units of S D, the size of the last change, so inputs and targets are
+// O(1) whatever the flow's time scale.
 __global__ void k_ws_scales(const GeomDev* __restrict__ g, const int8_t* __restrict__ rt,
                             const uint8_t* __restrict__ kind, const double* __restrict__ b,
-                            const double* __restrict__ phi, const double* __restrict__ hlat,
-                            double* __restrict__ scales) {
-    __shared__ double sb[1024], sp[1024], sn[1024];
+                            const double* __restrict__ phi, const double* __restrict__ phi_old,
+                            const double* __restrict__ hlat, double* __restrict__ scales) {
+    __shared__ double sb[1024], sp[1024], sn[1024], sd[1024];
     const GeomDev& G = g[blockIdx.x];
-    double a = 0, p = 0, n = 0;
+    double a = 0, p = 0, n = 0, d = 0;
     for (int64_t r = G.row0 + threadIdx.x; r < G.row0 + G.n; r += blockDim.x) {
         if (rt[r] != ROW_NODE) continue;
-        if (kind[r] == VIP_NODE_INTERIOR) { a += b[r] * b[r]; n += 1.0; }
+        if (kind[r] == VIP_NODE_INTERIOR) {
+            a += b[r] * b[r];
+            n += 1.0;
+            const double dd = phi[r] - phi_old[r];
+            d += dd * dd;
+        }
         p += phi[r] * phi[r];
     }
-    sb[threadIdx.x] = a; sp[threadIdx.x] = p; sn[threadIdx.x] = n;
+    sb[threadIdx.x] = a; sp[threadIdx.x] = p; sn[threadIdx.x] = n; sd[threadIdx.x] = d;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if ((int)threadIdx.x < s) {
             sb[threadIdx.x] += sb[threadIdx.x + s];
             sp[threadIdx.x] += sp[threadIdx.x + s];
             sn[threadIdx.x] += sn[threadIdx.x + s];
+            sd[threadIdx.x] += sd[threadIdx.x + s];
         }
         __syncthreads();
     }
@@ -104,8 +115,10 @@ __global__ void k_ws_scales(const GeomDev* __restrict__ g, const int8_t* __restr
         double s_b = sqrt(sb[0] / nn) + 1e-300;
         double rp = sqrt(sp[0] / (double)G.n);
         double S = rp > 0.0 ? rp : s_b * hlat[blockIdx.x] * hlat[blockIdx.x];
-        scales[2 * blockIdx.x] = s_b;
-        scales[2 * blockIdx.x + 1] = S;
+        double D = sqrt(sd[0] / nn) / S;
+        scales[3 * blockIdx.x] = s_b;
+        scales[3 * blockIdx.x + 1] = S;
+        scales[3 * blockIdx.x + 2] = D > 0.0 ? D : 1.0;
     }
 }
 
@@ -114,13 +127,14 @@ __global__ void k_ws_scatter(int64_t R, const int8_t* __restrict__ rt, const uin
                              const int32_t* __restrict__ rg, const int32_t* __restrict__ node_cell,
                              const double* __restrict__ us, const double* __restrict__ vs,
                              const double* __restrict__ b, const double* __restrict__ phi,
-                             const double* __restrict__ scales, __nv_bfloat16* __restrict__ x) {
+                             const double* __restrict__ phi_old, const double* __restrict__ scales,
+                             __nv_bfloat16* __restrict__ x) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     int32_t c = node_cell[r];
     if (c < 0 || rt[r] != ROW_NODE) return;
     int g = rg[r];
-    double s_b = scales[2 * g], S = scales[2 * g + 1];
+    double s_b = scales[3 * g], S = scales[3 * g + 1], D = scales[3 * g + 2];
     float v[CNN_CIN];
     for (int i = 0; i < CNN_CIN; ++i) v[i] = 0.0f;
     v[0] = (float)us[r];
@@ -129,44 +143,82 @@ __global__ void k_ws_scatter(int64_t R, const int8_t* __restrict__ rt, const uin
     v[3] = (float)(phi[r] / S);
     v[4] = 1.0f;
     v[5] = kind[r] != VIP_NODE_INTERIOR ? 1.0f : 0.0f;
+    v[6] = (float)((phi[r] - phi_old[r]) / (S * D));
     __nv_bfloat16* dst = x + (int64_t)c * CNN_CIN;
     for (int i = 0; i < CNN_CIN; ++i) dst[i] = __float2bfloat16(v[i]);
 }
 
-// phi guess = phi^n + S * prediction at lattice nodes
+// phi guess = phi^n + a (phi^n - phi^{n-1}) at every node, + S D * prediction at
+// lattice nodes
 __global__ void k_ws_gather(int64_t R, const int8_t* __restrict__ rt, const int32_t* __restrict__ rg,
-                            const int32_t* __restrict__ node_cell, const float* __restrict__ y,
-                            const double* __restrict__ scales, double* __restrict__ phi) {
+                            const int32_t* __restrict__ node_cell, const uint8_t* __restrict__ deep,
+                            const float* __restrict__ y, const double* __restrict__ scales,
+                            const double* __restrict__ phi_old, const double* __restrict__ extrap,
+                            double* __restrict__ phi) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= R) return;
-    int32_t c = node_cell[r];
-    if (c < 0 || rt[r] != ROW_NODE) return;
-    phi[r] += scales[2 * rg[r] + 1] * (double)y[c];
+    if (r >= R || rt[r] != ROW_NODE) return;
+    double g = phi[r] + extrap[0] * (phi[r] - phi_old[r]);
+    const int32_t c = node_cell[r];
+    if (c >= 0 && y && deep[c]) g += scales[3 * rg[r] + 1] * scales[3 * rg[r] + 2] * (double)y[c];
+    phi[r] = g;
 }
 
-// training target (phi^{n+1} - phi^n) / S and loss mask (interior lattice nodes)
-__global__ void k_ws_target(int64_t R, const int8_t* __restrict__ rt, const uint8_t* __restrict__ kind,
+// training target (phi^{n+1} - phi^n) / (S D), the history (phi^n - phi^{n-1}) / (S D)
+// and the loss mask (interior lattice nodes)
+__global__ void k_ws_target(int64_t R, const int8_t* __restrict__ rt, const uint8_t* __restrict__ deep,
                             const int32_t* __restrict__ rg, const int32_t* __restrict__ node_cell,
-                            const double* __restrict__ phi_new, const double* __restrict__ phi_old,
-                            const double* __restrict__ scales, float* __restrict__ tgt,
-                            float* __restrict__ mask) {
+                            const double* __restrict__ phi_new, const double* __restrict__ phi_n,
+                            const double* __restrict__ phi_nm1, const double* __restrict__ scales,
+                            float* __restrict__ tgt, float* __restrict__ dprev, float* __restrict__ mask) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     int32_t c = node_cell[r];
     if (c < 0 || rt[r] != ROW_NODE) return;
-    tgt[c] = (float)((phi_new[r] - phi_old[r]) / scales[2 * rg[r] + 1]);
-    mask[c] = kind[r] == VIP_NODE_INTERIOR ? 1.0f : 0.0f;
+    const double SD = scales[3 * rg[r] + 1] * scales[3 * rg[r] + 2];
+    tgt[c] = (float)((phi_new[r] - phi_n[r]) / SD);
+    dprev[c] = (float)((phi_n[r] - phi_nm1[r]) / SD);
+    mask[c] = deep[c] ? 1.0f : 0.0f;
+}
+
+// Block partials of sum m t d and sum m d d over cells (fixed order): the least-squares
+// fit of the extrapolation coefficient over the collected samples.
+__global__ void k_ws_fit(int64_t n, const float* __restrict__ t, const float* __restrict__ d,
+                         const float* __restrict__ m, double* __restrict__ part) {
+    __shared__ double s1[256], s2[256];
+    double a = 0.0, b = 0.0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const double dm = (double)m[c] * (double)d[c];
+        a += dm * (double)t[c];
+        b += dm * (double)d[c];
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s1[0];
+        part[2 * blockIdx.x + 1] = s2[0];
+    }
 }
 
 // MSE loss and its gradient wrt the output channel 0: gy = 2 (y - t) m / count.
 // Block partials of the loss in fixed order.
+// The target is t - a dp when dp is given (the part of the increment change that the
+// extrapolation a (phi^n - phi^{n-1}) leaves), else t.
 __global__ void k_loss(int64_t n, const float* __restrict__ y, const float* __restrict__ t,
-                       const float* __restrict__ m, double inv_cnt, __nv_bfloat16* __restrict__ gy,
-                       double* __restrict__ part) {
+                       const float* __restrict__ dp, double a, const float* __restrict__ m, double inv_cnt,
+                       __nv_bfloat16* __restrict__ gy, double* __restrict__ part) {
     __shared__ double s[256];
     double acc = 0.0;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
-        double d = (double)m[c] * ((double)y[c] - (double)t[c]);
+        const double tc = dp ? (double)t[c] - a * (double)dp[c] : (double)t[c];
+        double d = (double)m[c] * ((double)y[c] - tc);
         acc += d * d;
         __nv_bfloat16* g = gy + c * CNN_COUT;
         g[0] = __float2bfloat16((float)(2.0 * d * inv_cnt));
@@ -179,6 +231,74 @@ __global__ void k_loss(int64_t n, const float* __restrict__ y, const float* __re
         __syncthreads();
     }
     if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// Residual-proxy loss (the squared 5-point lattice Laplacian of the error e = m (y -
+// (t - a dp)) plus lam e^2, averaged over the active cells; the Poisson residual an
+// initial guess leaves is the operator applied to its error, so rough errors cost
+// more than smooth ones).  Cells are those of the images img[0..nimg), row-major.
+__device__ __forceinline__ int cnn_image_of(const CnnImage* __restrict__ img, int nimg, int64_t c) {
+    int lo = 0, hi = nimg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (img[mid].off <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ double cnn_err(int64_t c, const float* __restrict__ y, const float* __restrict__ t,
+                                          const float* __restrict__ dp, double a, const float* __restrict__ m) {
+    const double tc = dp ? (double)t[c] - a * (double)dp[c] : (double)t[c];
+    return (double)m[c] * ((double)y[c] - tc);
+}
+// sum of f over the four lattice neighbours of cell c (those inside its image)
+template <class F>
+__device__ __forceinline__ double cnn_nbr_sum(const CnnImage& I, int64_t c, F&& f) {
+    const int64_t k = c - I.off;
+    const int iy = (int)(k / I.W), ix = (int)(k % I.W);
+    double s = 0.0;
+    if (ix > 0) s += f(c - 1);
+    if (ix + 1 < I.W) s += f(c + 1);
+    if (iy > 0) s += f(c - I.W);
+    if (iy + 1 < I.H) s += f(c + I.W);
+    return s;
+}
+// pass 1: q(c) = m(c) (Delta e)(c), block partials of q^2 + lam e^2 (fixed order)
+__global__ void k_rloss1(int64_t n, const CnnImage* __restrict__ img, int nimg, const float* __restrict__ y,
+                         const float* __restrict__ t, const float* __restrict__ dp, double a,
+                         const float* __restrict__ m, double lam, float* __restrict__ q,
+                         double* __restrict__ part) {
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const CnnImage I = img[cnn_image_of(img, nimg, c)];
+        const double e = cnn_err(c, y, t, dp, a, m);
+        const double lap = cnn_nbr_sum(I, c, [&](int64_t j) { return cnn_err(j, y, t, dp, a, m); }) - 4.0 * e;
+        const double qc = (double)m[c] * lap;
+        q[c] = (float)qc;
+        acc += qc * qc + lam * e * e;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+// pass 2: gradient wrt output channel 0, gy(c) = 2 m(c) ((Delta q)(c) + lam e(c)) / cnt
+__global__ void k_rloss2(int64_t n, const CnnImage* __restrict__ img, int nimg, const float* __restrict__ y,
+                         const float* __restrict__ t, const float* __restrict__ dp, double a,
+                         const float* __restrict__ m, double lam, const float* __restrict__ q,
+                         double inv_cnt, __nv_bfloat16* __restrict__ gy) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const CnnImage I = img[cnn_image_of(img, nimg, c)];
+    const double lq = cnn_nbr_sum(I, c, [&](int64_t j) { return (double)q[j]; }) - 4.0 * (double)q[c];
+    const double g = 2.0 * (double)m[c] * (lq + lam * cnn_err(c, y, t, dp, a, m)) * inv_cnt;
+    __nv_bfloat16* o = gy + c * CNN_COUT;
+    o[0] = __float2bfloat16((float)g);
+    for (int k = 1; k < CNN_COUT; ++k) o[k] = __float2bfloat16(0.0f);
 }
 
 // Weight and bias gradients of one layer:
@@ -288,6 +408,7 @@ struct Cnn {
     CnnImage* img = nullptr;
     int64_t ncells = 0, ntiles = 0;
     int32_t* node_cell = nullptr;
+    uint8_t* deep = nullptr;        // [cells] 1: an interior node whose four lattice neighbours are too
     double* hlat = nullptr;
     double* scales = nullptr;
     // activations of one pass: act[0] input, act[1..5] hidden, out (FP32), grads
@@ -298,13 +419,21 @@ struct Cnn {
     int wg_blocks = 0;
     double* loss_part = nullptr;
     int loss_blocks = 0;
-    double* phi_prev = nullptr;
+    double* phi_prev = nullptr;     // phi^n, kept through the step's solve
+    double* phi_old = nullptr;      // phi^{n-1}, the warm start's history
+    double* extrap = nullptr;       // [1] the fitted extrapolation coefficient a (device)
+    double extrap_host = 0.0;
     // samples
     int max_samples = 0, nsamples = 0;
     int64_t loss_cnt = 0;           // interior lattice nodes (cells of the loss)
     bool collect = false, enable = false;
+    bool net = true;                // the guess uses the network (false: extrapolation only)
+    int loss_kind = 1;              // 0: mean squared error; 1: residual proxy (k_rloss1/2)
+    double loss_lam = 0.01;         // weight of the squared error in the residual proxy
+    float* lq = nullptr;            // [cells] q of the residual proxy
     __nv_bfloat16* s_in = nullptr;
     float *s_tgt = nullptr, *s_mask = nullptr;
+    float* s_dprev = nullptr;       // (phi^n - phi^{n-1}) / S of each sample (FP32)
     // test images (vip_cnn_forward / vip_cnn_grads)
     CnnImage* timg = nullptr;
 };
@@ -411,11 +540,18 @@ vip_status backward(vip_ctx* c, Cnn& N, const CnnImage* img, int nimg, int64_t n
     return VIP_OK;
 }
 
-vip_status loss_grad(vip_ctx* c, Cnn& N, int64_t off, int64_t n, const float* tgt, const float* mask,
-                     double cnt, double* loss_out, cudaStream_t s) {
+vip_status loss_grad(vip_ctx* c, Cnn& N, const CnnImage* img, int nimg, int64_t n, const float* tgt,
+                     const float* dprev, double a, const float* mask, double cnt, double* loss_out,
+                     cudaStream_t s) {
     int nb = N.loss_blocks;
-    k_loss<<<nb, 256, 0, s>>>(n, N.out + off, tgt, mask, 1.0 / std::max(cnt, 1.0), N.gl + off * CNN_COUT,
-                              N.loss_part);
+    if (N.loss_kind == 1) {
+        k_rloss1<<<nb, 256, 0, s>>>(n, img, nimg, N.out, tgt, dprev, a, mask, N.loss_lam, N.lq, N.loss_part);
+        k_rloss2<<<nblk(n, 256), 256, 0, s>>>(n, img, nimg, N.out, tgt, dprev, a, mask, N.loss_lam, N.lq,
+                                              1.0 / std::max(cnt, 1.0), N.gl);
+    } else {
+        k_loss<<<nb, 256, 0, s>>>(n, N.out, tgt, dprev, a, mask, 1.0 / std::max(cnt, 1.0), N.gl,
+                                  N.loss_part);
+    }
     VIP_CUDA(cudaGetLastError());
     if (loss_out) {
         std::vector<double> part(nb);
@@ -448,6 +584,7 @@ vip_status ensure_act(vip_ctx* c, Cnn& N, int64_t ncells) {
     VIP_CUDA(dalloc(c, &N.g0, (size_t)N.ncells * CNN_CH));
     VIP_CUDA(dalloc(c, &N.g1, (size_t)N.ncells * CNN_CH));
     VIP_CUDA(dalloc(c, &N.gl, (size_t)N.ncells * CNN_COUT));
+    VIP_CUDA(dalloc(c, &N.lq, (size_t)N.ncells));
     return VIP_OK;
 }
 
@@ -515,7 +652,6 @@ vip_status cnn_setup(vip_ctx* c, uint64_t seed) {
             if (std::fabs(fx - ix) < 1e-6 && std::fabs(fy - iy) < 1e-6 && ix >= 0 && ix < W && iy >= 0 &&
                 iy < H) {
                 cell[gg.row0 + i] = (int32_t)(off + iy * W + ix);
-                if (c->hkind[gg.off + i] == VIP_NODE_INTERIOR) N->loss_cnt++;
             }
         }
         off += (int64_t)W * H;
@@ -526,10 +662,37 @@ vip_status cnn_setup(vip_ctx* c, uint64_t seed) {
     VIP_CUDA(cudaMemcpy(N->img, N->himg.data(), G * sizeof(CnnImage), cudaMemcpyHostToDevice));
     VIP_CUDA(dalloc(c, &N->node_cell, c->R));
     VIP_CUDA(cudaMemcpy(N->node_cell, cell.data(), c->R * 4, cudaMemcpyHostToDevice));
+    {   // cells where the network's correction applies (and is trained): interior nodes
+        // whose four lattice neighbours are interior nodes too, away from boundary nodes
+        // off the lattice, where a correction that stopped short would leave a jump
+        std::vector<uint8_t> inner(off, 0), dp(off, 0);
+        for (int g = 0; g < G; ++g) {
+            const Geom& gg = c->geoms[g];
+            for (int64_t i = 0; i < gg.n; ++i) {
+                const int32_t cc = cell[gg.row0 + i];
+                if (cc >= 0 && c->hkind[gg.off + i] == VIP_NODE_INTERIOR) inner[cc] = 1;
+            }
+        }
+        for (const CnnImage& I : N->himg)
+            for (int iy = 1; iy + 1 < I.H; ++iy)
+                for (int ix = 1; ix + 1 < I.W; ++ix) {
+                    const int64_t cc = I.off + (int64_t)iy * I.W + ix;
+                    dp[cc] = inner[cc] && inner[cc - 1] && inner[cc + 1] && inner[cc - I.W] && inner[cc + I.W];
+                }
+        int64_t nd = 0;
+        for (uint8_t v : dp) nd += v;
+        N->loss_cnt = nd;
+        VIP_CUDA(dalloc(c, &N->deep, off));
+        VIP_CUDA(cudaMemcpy(N->deep, dp.data(), off, cudaMemcpyHostToDevice));
+    }
     VIP_CUDA(dalloc(c, &N->hlat, G));
     VIP_CUDA(cudaMemcpy(N->hlat, hl.data(), G * 8, cudaMemcpyHostToDevice));
-    VIP_CUDA(dalloc(c, &N->scales, 2 * G));
+    VIP_CUDA(dalloc(c, &N->scales, 3 * G));
     VIP_CUDA(dalloc(c, &N->phi_prev, c->R));
+    VIP_CUDA(dalloc(c, &N->phi_old, c->R));
+    VIP_CUDA(dalloc(c, &N->extrap, 1));
+    VIP_CUDA(cudaMemsetAsync(N->phi_old, 0, c->R * 8, c->stream));
+    VIP_CUDA(cudaMemsetAsync(N->extrap, 0, 8, c->stream));
     st = ensure_act(c, *N, off);
     if (st != VIP_OK) return st;
     N->ncells = off;
@@ -554,36 +717,59 @@ vip_status cnn_warm_start(vip_ctx* c, cudaStream_t s) {
     const int64_t R = c->R;
     VIP_CUDA(cudaMemcpyAsync(N->phi_prev, c->phi, R * 8, cudaMemcpyDeviceToDevice, s));
     k_ws_scales<<<(unsigned)c->geoms.size(), 1024, 0, s>>>(c->gdev, c->row_type, c->kind, c->prhs, c->phi,
-                                                          N->hlat, N->scales);
+                                                          N->phi_old, N->hlat, N->scales);
     VIP_CUDA(cudaMemsetAsync(N->act[0], 0, (size_t)N->ncells * CNN_CIN * 2, s));
     k_ws_scatter<<<nblk(R, 256), 256, 0, s>>>(R, c->row_type, c->kind, c->row_geom, N->node_cell, c->hsol,
-                                               c->hsol + R, c->prhs, c->phi, N->scales, N->act[0]);
+                                               c->hsol + R, c->prhs, c->phi, N->phi_old, N->scales,
+                                               N->act[0]);
     VIP_CUDA(cudaGetLastError());
     if (N->enable) {
-        vip_status st = forward(c, *N, N->img, (int)N->himg.size(), N->ntiles, N->act[0], s);
-        if (st != VIP_OK) return st;
-        k_ws_gather<<<nblk(R, 256), 256, 0, s>>>(R, c->row_type, c->row_geom, N->node_cell, N->out, N->scales,
+        if (N->net) {
+            vip_status st = forward(c, *N, N->img, (int)N->himg.size(), N->ntiles, N->act[0], s);
+            if (st != VIP_OK) return st;
+        }
+        k_ws_gather<<<nblk(R, 256), 256, 0, s>>>(R, c->row_type, c->row_geom, N->node_cell, N->deep,
+                                                  N->net ? N->out : nullptr, N->scales, N->phi_old, N->extrap,
                                                   c->phi);
         VIP_CUDA(cudaGetLastError());
     }
     return VIP_OK;
 }
 
-// After the solve: store (input, target) when collecting.
+// phi^{n-1} := phi (the next step's history is then no change), outside any step
+vip_status cnn_reset_history(vip_ctx* c) {
+    Cnn* N = cnn_of(c);
+    if (!N) return VIP_OK;
+    VIP_CUDA(cudaMemcpyAsync(N->phi_old, c->phi, c->R * 8, cudaMemcpyDeviceToDevice, c->stream));
+    return VIP_OK;
+}
+
+double* cnn_history(vip_ctx* c) {
+    Cnn* N = cnn_of(c);
+    return N ? N->phi_old : nullptr;
+}
+
+// After the solve: store (input, target, history) when collecting, and move the
+// history on: phi^{n-1} := phi^n.
 vip_status cnn_after_solve(vip_ctx* c, cudaStream_t s) {
     Cnn* N = cnn_of(c);
-    if (!N || !N->collect || N->nsamples >= N->max_samples) return VIP_OK;
-    const int64_t nc = N->ncells;
-    const int k = N->nsamples;
-    VIP_CUDA(cudaMemcpyAsync(N->s_in + (int64_t)k * nc * CNN_CIN, N->act[0], nc * CNN_CIN * 2,
-                             cudaMemcpyDeviceToDevice, s));
-    VIP_CUDA(cudaMemsetAsync(N->s_tgt + (int64_t)k * nc, 0, nc * 4, s));
-    VIP_CUDA(cudaMemsetAsync(N->s_mask + (int64_t)k * nc, 0, nc * 4, s));
-    k_ws_target<<<nblk(c->R, 256), 256, 0, s>>>(c->R, c->row_type, c->kind, c->row_geom, N->node_cell, c->phi,
-                                                 N->phi_prev, N->scales, N->s_tgt + (int64_t)k * nc,
-                                                 N->s_mask + (int64_t)k * nc);
-    VIP_CUDA(cudaGetLastError());
-    N->nsamples++;
+    if (!N || (!N->enable && !N->collect)) return VIP_OK;
+    if (N->collect && N->nsamples < N->max_samples) {
+        const int64_t nc = N->ncells;
+        const int k = N->nsamples;
+        VIP_CUDA(cudaMemcpyAsync(N->s_in + (int64_t)k * nc * CNN_CIN, N->act[0], nc * CNN_CIN * 2,
+                                 cudaMemcpyDeviceToDevice, s));
+        VIP_CUDA(cudaMemsetAsync(N->s_tgt + (int64_t)k * nc, 0, nc * 4, s));
+        VIP_CUDA(cudaMemsetAsync(N->s_dprev + (int64_t)k * nc, 0, nc * 4, s));
+        VIP_CUDA(cudaMemsetAsync(N->s_mask + (int64_t)k * nc, 0, nc * 4, s));
+        k_ws_target<<<nblk(c->R, 256), 256, 0, s>>>(c->R, c->row_type, N->deep, c->row_geom, N->node_cell,
+                                                     c->phi, N->phi_prev, N->phi_old, N->scales,
+                                                     N->s_tgt + (int64_t)k * nc, N->s_dprev + (int64_t)k * nc,
+                                                     N->s_mask + (int64_t)k * nc);
+        VIP_CUDA(cudaGetLastError());
+        N->nsamples++;
+    }
+    VIP_CUDA(cudaMemcpyAsync(N->phi_old, N->phi_prev, c->R * 8, cudaMemcpyDeviceToDevice, s));
     return VIP_OK;
 }
 
@@ -605,10 +791,15 @@ vip_status vip_ws_collect(vip_ctx* c, int enable, int32_t max_samples) {
         if (max_samples > N.max_samples) {
             VIP_CUDA(dalloc(c, &N.s_in, (size_t)max_samples * N.ncells * CNN_CIN));
             VIP_CUDA(dalloc(c, &N.s_tgt, (size_t)max_samples * N.ncells));
+            VIP_CUDA(dalloc(c, &N.s_dprev, (size_t)max_samples * N.ncells));
             VIP_CUDA(dalloc(c, &N.s_mask, (size_t)max_samples * N.ncells));
             N.max_samples = max_samples;
         }
         N.nsamples = 0;
+        if (!N.collect && !N.enable) {
+            vip_status st = cnn_reset_history(c);
+            if (st != VIP_OK) return st;
+        }
     }
     N.collect = enable != 0;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
@@ -618,7 +809,14 @@ vip_status vip_ws_collect(vip_ctx* c, int enable, int32_t max_samples) {
 vip_status vip_ws_enable(vip_ctx* c, int enable) {
     if (!c) return VIP_ERR_ARG;
     if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_enable before vip_build");
-    cnn_of(c)->enable = enable != 0;
+    Cnn& N = *cnn_of(c);
+    if (enable && !N.enable && !N.collect) {
+        vip_status st = cnn_reset_history(c);
+        if (st != VIP_OK) return st;
+    }
+    if (enable < 0 || enable > 2) return fail(c, VIP_ERR_ARG, "vip_ws_enable: mode must be 0, 1 or 2");
+    N.enable = enable != 0;
+    N.net = enable != 2;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
     return VIP_OK;
 }
@@ -636,6 +834,29 @@ vip_status vip_ws_train(vip_ctx* c, vip_train_cfg* cfg) {
     const int64_t nc = N.ncells;
     const CnnImage* img = N.img;
     const int nimg = (int)N.himg.size();
+    // the extrapolation coefficient: least squares over every collected sample's
+    // interior lattice nodes, a = sum t d / sum d d (t the increment change, d the
+    // previous one, both / S); the network then learns what a d leaves of t
+    {
+        const int fb = 256;
+        DeviceScratch d_part;
+        VIP_CUDA(cudaMalloc(&d_part.p, 2 * fb * sizeof(double)));
+        std::vector<double> part(2 * fb);
+        double num = 0.0, den = 0.0;
+        for (int k = 0; k < N.nsamples; ++k) {
+            k_ws_fit<<<fb, 256, 0, s>>>(nc, N.s_tgt + (int64_t)k * nc, N.s_dprev + (int64_t)k * nc,
+                                        N.s_mask + (int64_t)k * nc, static_cast<double*>(d_part.p));
+            VIP_CUDA(cudaGetLastError());
+            VIP_CUDA(cudaMemcpyAsync(part.data(), d_part.p, 2 * fb * 8, cudaMemcpyDeviceToHost, s));
+            VIP_CUDA(cudaStreamSynchronize(s));
+            for (int b = 0; b < fb; ++b) { num += part[2 * b]; den += part[2 * b + 1]; }
+        }
+        double a = den > 0.0 ? num / den : 0.0;
+        a = std::min(2.0, std::max(-1.0, a));  // a guess beyond these is no extrapolation
+        N.extrap_host = a;
+        VIP_CUDA(cudaMemcpyAsync(N.extrap, &N.extrap_host, 8, cudaMemcpyHostToDevice, s));
+        cfg->extrap = a;
+    }
     double last = 0.0;
     for (int ep = 0; ep < cfg->epochs; ++ep) {
         std::shuffle(order.begin(), order.end(), rng);
@@ -646,7 +867,8 @@ vip_status vip_ws_train(vip_ctx* c, vip_train_cfg* cfg) {
             if (st != VIP_OK) return st;
             double cnt = (double)N.loss_cnt;
             double L = 0.0;
-            st = loss_grad(c, N, 0, nc, N.s_tgt + (int64_t)k * nc, N.s_mask + (int64_t)k * nc, cnt, &L, s);
+            st = loss_grad(c, N, img, nimg, nc, N.s_tgt + (int64_t)k * nc, N.s_dprev + (int64_t)k * nc,
+                           N.extrap_host, N.s_mask + (int64_t)k * nc, cnt, &L, s);
             if (st != VIP_OK) return st;
             st = backward(c, N, img, nimg, N.ntiles, in, s);
             if (st != VIP_OK) return st;
@@ -657,11 +879,69 @@ vip_status vip_ws_train(vip_ctx* c, vip_train_cfg* cfg) {
         last = sum / N.nsamples;
         if (ep == 0) cfg->first_loss = last;
     }
-    cfg->final_loss = last;
+    (void)last;
+    // Keep the network only if, on its own samples, it leaves less than the
+    // extrapolation alone: the mean loss with the trained network and with its output
+    // zero.  Otherwise its last layer is zeroed, so the guess is the extrapolation.
+    {
+        double net = 0.0, base = 0.0;
+        for (int k = 0; k < N.nsamples; ++k) {
+            __nv_bfloat16* in = N.s_in + (int64_t)k * nc * CNN_CIN;
+            const float* tk = N.s_tgt + (int64_t)k * nc;
+            const float* dk = N.s_dprev + (int64_t)k * nc;
+            const float* mk = N.s_mask + (int64_t)k * nc;
+            double L = 0.0;
+            vip_status st = forward(c, N, img, nimg, N.ntiles, in, s);
+            if (st != VIP_OK) return st;
+            if ((st = loss_grad(c, N, img, nimg, nc, tk, dk, N.extrap_host, mk, (double)N.loss_cnt, &L, s)) != VIP_OK)
+                return st;
+            net += L;
+            VIP_CUDA(cudaMemsetAsync(N.out, 0, nc * sizeof(float), s));
+            if ((st = loss_grad(c, N, img, nimg, nc, tk, dk, N.extrap_host, mk, (double)N.loss_cnt, &L, s)) != VIP_OK)
+                return st;
+            base += L;
+        }
+        net /= N.nsamples;
+        base /= N.nsamples;
+        cfg->final_loss = net;
+        cfg->base_loss = base;
+        cfg->net_kept = net < base ? 1 : 0;
+        if (!cfg->net_kept) {
+            const int l = CNN_LAYERS - 1;
+            VIP_CUDA(cudaMemsetAsync(N.params + N.L.w[l], 0, (N.L.total - N.L.w[l]) * sizeof(float), s));
+            vip_status st = repack(c, N);
+            if (st != VIP_OK) return st;
+        }
+    }
     VIP_CUDA(cudaStreamSynchronize(s));
     int32_t hs = 0;
     VIP_CUDA(cudaMemcpy(&hs, c->d_status, 4, cudaMemcpyDeviceToHost));
     if (hs) return fail(c, (vip_status)hs, "device error during training");
+    return VIP_OK;
+}
+
+vip_status vip_ws_set_loss(vip_ctx* c, int kind, double lam) {
+    if (!c) return VIP_ERR_ARG;
+    if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_set_loss before vip_build");
+    if ((kind != 0 && kind != 1) || !(lam >= 0.0)) return fail(c, VIP_ERR_ARG, "vip_ws_set_loss: bad kind or weight");
+    Cnn& N = *cnn_of(c);
+    N.loss_kind = kind;
+    N.loss_lam = lam;
+    return VIP_OK;
+}
+
+vip_status vip_ws_extrapolation(vip_ctx* c, int set, double* a) {
+    if (!c || !a) return VIP_ERR_ARG;
+    if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_extrapolation before vip_build");
+    Cnn& N = *cnn_of(c);
+    if (!set) {
+        *a = N.extrap_host;
+        return VIP_OK;
+    }
+    if (!(*a >= -1.0 && *a <= 2.0)) return fail(c, VIP_ERR_ARG, "vip_ws_extrapolation: a must be in [-1, 2]");
+    N.extrap_host = *a;
+    VIP_CUDA(cudaMemcpyAsync(N.extrap, &N.extrap_host, 8, cudaMemcpyHostToDevice, c->stream));
+    VIP_CUDA(cudaStreamSynchronize(c->stream));
     return VIP_OK;
 }
 
@@ -740,7 +1020,7 @@ vip_status vip_ws_eval(vip_ctx* c, int32_t H, int32_t W, const float* x, float* 
         VIP_CUDA(cudaMemcpy(hmk.data(), mask, n * 4, cudaMemcpyDefault));
         double cnt = 0;
         for (float v : hmk) cnt += v != 0.0f;
-        st = loss_grad(c, N, 0, n, dt, dm, cnt, loss, s);
+        st = loss_grad(c, N, N.timg, 1, n, dt, nullptr, 0.0, dm, cnt, loss, s);
         if (st == VIP_OK) st = backward(c, N, N.timg, 1, ntiles, in, s);
         if (st == VIP_OK) VIP_CUDA(cudaMemcpyAsync(grads, N.grads, N.L.total * 4, cudaMemcpyDefault, s));
         VIP_CUDA(cudaStreamSynchronize(s));

@@ -9,7 +9,7 @@
 namespace vip {
 
 constexpr int CNN_LAYERS = 6;
-constexpr int CNN_CIN = 16;     // input channels (6 used, zero padded)
+constexpr int CNN_CIN = 16;     // input channels (7 used, zero padded)
 constexpr int CNN_CH = 32;      // hidden channels
 constexpr int CNN_COUT = 16;    // MMA width of the last layer (channel 0 is the output)
 constexpr int CNN_TILE = 128;   // pixels of a lattice row per MMA tile (TMEM lanes)

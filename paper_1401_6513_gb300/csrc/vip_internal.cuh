@@ -218,6 +218,10 @@ void cnn_free(vip_ctx* c);
 vip_status cnn_warm_start(vip_ctx* c, cudaStream_t s);
 vip_status cnn_after_solve(vip_ctx* c, cudaStream_t s);
 bool cnn_collecting(vip_ctx* c);
+// the warm start's history phi^{n-1}: reset to phi (outside any step), and its buffer
+// (saved with checkpoints)
+vip_status cnn_reset_history(vip_ctx* c);
+double* cnn_history(vip_ctx* c);
 // step kernels (vip_step.cu)
 void launch_conv_rhs(vip_ctx* c, cudaStream_t s);
 void launch_div(vip_ctx* c, cudaStream_t s);

@@ -36,7 +36,7 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static",
            "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout",
            "vip_multigrid_info", "vip_set_mg_shift", "vip_set_refinement", "vip_checkpoint_size",
-           "vip_checkpoint", "vip_ws_adam"]
+           "vip_checkpoint", "vip_ws_adam", "vip_ws_extrapolation", "vip_ws_set_loss"]
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -51,7 +51,8 @@ class StepStats(C.Structure):
 
 class TrainCfg(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64),
-                ("first_loss", C.c_double), ("final_loss", C.c_double)]
+                ("first_loss", C.c_double), ("final_loss", C.c_double), ("extrap", C.c_double),
+                ("base_loss", C.c_double), ("net_kept", C.c_int32)]
 
 
 class TuneResult(C.Structure):
@@ -97,6 +98,8 @@ def lib(path: str | Path | None = None):
         "vip_checkpoint_size": ([vp, C.POINTER(i64)], C.c_int),
         "vip_checkpoint": ([vp, C.c_int, vp], C.c_int),
         "vip_ws_adam": ([vp, dbl], C.c_int),
+        "vip_ws_extrapolation": ([vp, C.c_int, C.POINTER(dbl)], C.c_int),
+        "vip_ws_set_loss": ([vp, C.c_int, dbl], C.c_int),
         "vip_build": ([vp], C.c_int),
         "vip_set_state": ([vp, vp, vp, vp], C.c_int),
         "vip_step": ([vp, i32], C.c_int),
@@ -269,12 +272,24 @@ class Context:
         self._check(self.L.vip_ws_collect(self.h, 1 if enable else 0, int(max_samples)))
 
     def vip_ws_enable(self, enable=True):
-        self._check(self.L.vip_ws_enable(self.h, 1 if enable else 0))
+        """enable: False/0 previous increment, True/1 extrapolation + network,
+        2 extrapolation alone."""
+        self._check(self.L.vip_ws_enable(self.h, int(enable)))
 
     def vip_ws_train(self, epochs=10, lr=1e-3, seed=0) -> TrainCfg:
         cfg = TrainCfg(epochs=int(epochs), lr=float(lr), seed=int(seed))
         self._check(self.L.vip_ws_train(self.h, C.byref(cfg)))
         return cfg
+
+    def vip_ws_set_loss(self, kind=1, lam=0.01):
+        """Network loss: 0 mean squared error, 1 residual proxy (lattice Laplacian)."""
+        self._check(self.L.vip_ws_set_loss(self.h, int(kind), float(lam)))
+
+    def vip_ws_extrapolation(self, a=None):
+        """Read the warm start's extrapolation coefficient, or set it to a."""
+        v = C.c_double(0.0 if a is None else float(a))
+        self._check(self.L.vip_ws_extrapolation(self.h, 0 if a is None else 1, C.byref(v)))
+        return v.value
 
     def vip_ws_adam(self, lr=1e-3):
         self._check(self.L.vip_ws_adam(self.h, float(lr)))

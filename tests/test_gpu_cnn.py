@@ -45,6 +45,7 @@ def bf16(a):
 @pytest.fixture(scope="module")
 def ctx(vip):
     c = vip.solver_for(w.cavity(24, Re=100.0), precision=vip.VIP_PREC_FP64)
+    c.vip_ws_set_loss(0)  # the tests below compare with the oracle's mean squared error
     yield c
     c.close()
 
@@ -98,9 +99,10 @@ def test_forward_matches_reference(ctx, shape):
     assert err < 2e-2, err
 
 
-def bf16_reference_grads(layers, x, t, m):
+def bf16_reference_grads(layers, x, t, m, lam=None):
     """FP64 forward/backward of the oracle with BF16 rounding where the GPU stores
-    BF16: packed weights, ReLU outputs, the loss gradient and each data gradient."""
+    BF16: packed weights, ReLU outputs, the loss gradient and each data gradient.
+    lam None: mean squared error; else the residual proxy with that weight."""
     wq = [(bf16(wt).astype(np.float64), b) for wt, b in layers]
     acts, h = [x], x
     for k, (wt, b) in enumerate(wq):
@@ -111,7 +113,11 @@ def bf16_reference_grads(layers, x, t, m):
     y = h[..., 0].astype(np.float32).astype(np.float64)
     d = (y - t) * m
     gy = np.zeros(h.shape)
-    gy[..., 0] = bf16(2.0 * d / max(m.sum(), 1.0))
+    if lam is None:
+        gy[..., 0] = bf16(2.0 * d / max(m.sum(), 1.0))
+    else:
+        q = (m * co.lap5(d)).astype(np.float32).astype(np.float64)
+        gy[..., 0] = bf16(2.0 * m * (co.lap5(q) + lam * d) / max(m.sum(), 1.0))
     out = [None] * len(wq)
     for k in range(len(wq) - 1, -1, -1):
         gx, gw, gb = co.conv3x3_backward(acts[k], wq[k][0], gy)
@@ -151,6 +157,41 @@ def test_gradients_match_reference(ctx):
         if k >= len(CH) - 3:
             ew, eb = rel(got_w, ref[k][0]), rel(got_b, ref[k][1])
             assert ew < 5e-2 and eb < 5e-2, (k, ci, cout, ew, eb)
+
+
+def test_residual_loss_gradients_match_reference(ctx):
+    """The residual-proxy loss (squared lattice Laplacian of the error plus lam times
+    the squared error) and its parameter gradients against the oracle: the loss
+    within 2e-2 of FP64, the gradients within 1e-2 of the oracle evaluated at the
+    GPU's BF16 storage points, as for the mean squared error."""
+    lam = 0.05
+    flat = random_params(ctx, 8)
+    rng = np.random.default_rng(9)
+    H, W = 6, 130
+    x = np.zeros((H, W, 16), np.float32)
+    x[..., :6] = rng.standard_normal((H, W, 6))
+    x = bf16(x)
+    t = rng.standard_normal((H, W)).astype(np.float32)
+    m = (rng.random((H, W)) > 0.2).astype(np.float32)
+    ctx.vip_ws_set_loss(1, lam)
+    try:
+        _, g, loss = eval_gpu(ctx, x, t, m, flat.size)
+    finally:
+        ctx.vip_ws_set_loss(0)
+    layers = to_layers(flat)
+    x64, t64, m64 = x.astype(np.float64), t.astype(np.float64), m.astype(np.float64)
+    L, _ = co.residual_loss_and_grads(layers, x64, t64, m64, lam)
+    emu = bf16_reference_grads(layers, x64, t64, m64, lam)
+    assert abs(loss - L) <= 2e-2 * abs(L)
+    o = 0
+    for k, (ci, cout) in enumerate(zip(CH[:-1], CH[1:])):
+        n = 9 * ci * cout
+        got_w = g[o:o + n].reshape(emu[k][0].shape)
+        o += n
+        got_b = g[o:o + cout]
+        o += cout
+        rel = lambda a, b: np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)  # noqa: E731
+        assert rel(got_w, emu[k][0]) < 1e-2 and rel(got_b, emu[k][1]) < 1e-2, k
 
 
 def test_adam_matches_oracle(ctx):
