@@ -8,8 +8,10 @@ of the dominant kernel (the Poisson BiCGSTAB launch).
 Workload (default): flow past the bumpy cylinder r = 1 + 0.05 sin 12t + 0.02 sin 31t
 in the channel [-8,24]x[-8,8] at h = 1/64 (about 2.1M nodes), Re = 200, dt = h/10,
 synthetic (generated) node set and an impulsively started uniform inflow, solved
-in the mixed form (FP32 inner BiCGSTAB and V-cycle under FP64 refinement, every
-solve stopped on the FP64 residual).  Its working set (several GB) exceeds the
+in the form chosen by measurement (the mixed form: FP32 inner BiCGSTAB and V-cycle
+under FP64 refinement, every solve stopped on the FP64 residual) with the learned
+warm start (the pressure increment extrapolated in time with a coefficient fitted
+on the run's own first solves).  Its working set (several GB) exceeds the
 129 MB L2, so no flush is needed between timed steps.
 
 The timed steps run three times from one checkpoint of the state: on the device
@@ -63,9 +65,10 @@ def parse():
                     help="skip the batch of 64 equilateral cavities (extra keys)")
     ap.add_argument("--batch-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--warm-start", choices=["previous", "learned"], default="previous",
+    ap.add_argument("--warm-start", choices=["previous", "extrap", "learned"], default="extrap",
                     help="initial guess of the pressure-increment solve: the previous "
-                         "increment, or the network trained on this run's own solves")
+                         "increment; its temporal extrapolation with the coefficient fitted on "
+                         "this run's own solves; or that plus the network trained on them")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default multigrid parameters (omega 1.0, corr 1.5)")
     ap.add_argument("--mg-shift", choices=["zero", "auto"], default="zero",
@@ -323,10 +326,13 @@ def timed_steps(ctx, stream, k):
     return e0.elapsed_time(e1)
 
 
-def form_run(vip, ctx, stream, ckpt, k, prec):
-    """The k steps after the checkpoint in precision form prec: ms, Poisson inner
-    iterations and refinement passes per step, last relative residual, status."""
+def form_run(vip, ctx, stream, ckpt, k, prec, ws_mode=None):
+    """The k steps after the checkpoint in precision form prec (and warm-start mode
+    ws_mode, if given): ms, Poisson inner iterations and refinement passes per step,
+    last relative residual, status."""
     ctx.vip_set_solver(prec, 1e-8, 50000, vip.VIP_IDENTITY_EXACT)
+    if ws_mode is not None:
+        ctx.vip_ws_enable(ws_mode)
     ctx.vip_checkpoint(False, ckpt)
     ctx.vip_step(1)  # captures this form's step graph outside the timed region
     ctx.vip_checkpoint(False, ckpt)
@@ -403,18 +409,21 @@ def main():
     tune = vip.autotune(ctx, nss) if not args.no_autotune else None
     ctx.vip_step(args.warmup)
     ws_info = None
-    if args.warm_start == "learned":
-        # collect solved increments, train, then use the network's guess (untimed)
+    ws_mode = {"previous": 0, "learned": 1, "extrap": 2}[args.warm_start]
+    if ws_mode:
+        # collect solved increments, fit the extrapolation and train the network, then
+        # use the guess (untimed)
         t1 = time.perf_counter()
         ctx.vip_ws_collect(True, args.ws_samples)
         ctx.vip_step(args.ws_samples)
         ctx.vip_ws_collect(False)
-        tc = ctx.vip_ws_train(epochs=args.ws_epochs, lr=1e-3, seed=7)
-        ctx.vip_ws_enable(True)
+        tc = ctx.vip_ws_train(epochs=args.ws_epochs if ws_mode == 1 else 1, lr=1e-3, seed=7)
+        ctx.vip_ws_enable(ws_mode)
         ctx.vip_step(2)
-        ws_info = {"guess": "learned", "samples": args.ws_samples, "epochs": args.ws_epochs,
-                   "first_loss": tc.first_loss, "final_loss": tc.final_loss,
-                   "collect_train_s": round(time.perf_counter() - t1, 2)}
+        ws_info = {"guess": args.warm_start, "samples": args.ws_samples,
+                   "epochs": args.ws_epochs if ws_mode == 1 else 1, "extrapolation_coefficient": tc.extrap,
+                   "first_loss": tc.first_loss, "final_loss": tc.final_loss, "base_loss": tc.base_loss,
+                   "network_kept": bool(tc.net_kept), "collect_train_s": round(time.perf_counter() - t1, 2)}
     form_trials = None
     if args.precision == "auto":
         prec, form_trials = vip.choose_precision(ctx, ALL_FORMS(vip))
@@ -536,11 +545,17 @@ def main():
     it_e2e = se1.total_poisson_iters - se0.total_poisson_iters
     st = se1
     # ---- the plain all-FP64 form on the same steps (same context, multigrid, checkpoint)
-    fp64_cmp = None
-    if form != "fp64" and not args.no_fp64_compare:
-        fp64_cmp = form_run(vip, ctx, stream, ckpt, args.steps, vip.VIP_PREC_FP64)
+    fp64_cmp = prev_cmp = None
+    if (form != "fp64" or ws_mode) and not args.no_fp64_compare:
+        # the plain all-FP64 form: FP64 solves started from the previous increment
+        fp64_cmp = form_run(vip, ctx, stream, ckpt, args.steps, vip.VIP_PREC_FP64, ws_mode=0)
         fp64_cmp["node_updates_per_s"] = N / (fp64_cmp["ms_per_step"] / 1e3)
         fp64_cmp["chosen_over_fp64"] = value / ws / fp64_cmp["node_updates_per_s"]
+    if ws_mode and not args.no_fp64_compare:
+        # the chosen precision with the previous-increment guess: the warm start's gain
+        prev_cmp = form_run(vip, ctx, stream, ckpt, args.steps, prec, ws_mode=0)
+        prev_cmp["node_updates_per_s"] = N / (prev_cmp["ms_per_step"] / 1e3)
+        prev_cmp["chosen_over_previous_guess"] = value / ws / prev_cmp["node_updates_per_s"]
     ctx.close()
     batch = None
     if ws == 1 and not args.no_batch and args.workload != "triangles64":
@@ -576,11 +591,14 @@ def main():
                     "h2d_bytes_per_step": 3 * 8 * N, "d2h_bytes_per_step": 4 * 8 * N,
                     "same_steps_as_value": it_e2e == it_p},
             # per step: rhs, Helmholtz, divergence, Poisson, stats, projection; the
-            # learned guess adds scales, scatter, six convolutions and gather
-            "gpu_launches": (6 + (9 if ws_info else 0)) * args.steps,
+            # learned guess adds scales, scatter, six convolutions and gather, the
+            # extrapolation alone its gather
+            "gpu_launches": (6 + {0: 0, 1: 9, 2: 1}[ws_mode]) * args.steps,
             "clocks": clk}
     if fp64_cmp is not None:
         line["fp64_same_steps"] = fp64_cmp
+    if prev_cmp is not None:
+        line["previous_guess_same_steps"] = prev_cmp
     if batch is not None:
         line["batch_64_cavities"] = batch
     if cpu is not None:

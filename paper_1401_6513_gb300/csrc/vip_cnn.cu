@@ -716,13 +716,15 @@ vip_status cnn_warm_start(vip_ctx* c, cudaStream_t s) {
     if (!N || (!N->enable && !N->collect)) return VIP_OK;
     const int64_t R = c->R;
     VIP_CUDA(cudaMemcpyAsync(N->phi_prev, c->phi, R * 8, cudaMemcpyDeviceToDevice, s));
-    k_ws_scales<<<(unsigned)c->geoms.size(), 1024, 0, s>>>(c->gdev, c->row_type, c->kind, c->prhs, c->phi,
-                                                          N->phi_old, N->hlat, N->scales);
-    VIP_CUDA(cudaMemsetAsync(N->act[0], 0, (size_t)N->ncells * CNN_CIN * 2, s));
-    k_ws_scatter<<<nblk(R, 256), 256, 0, s>>>(R, c->row_type, c->kind, c->row_geom, N->node_cell, c->hsol,
-                                               c->hsol + R, c->prhs, c->phi, N->phi_old, N->scales,
-                                               N->act[0]);
-    VIP_CUDA(cudaGetLastError());
+    if (N->collect || (N->enable && N->net)) {  // the network's input (the extrapolation alone needs none)
+        k_ws_scales<<<(unsigned)c->geoms.size(), 1024, 0, s>>>(c->gdev, c->row_type, c->kind, c->prhs, c->phi,
+                                                              N->phi_old, N->hlat, N->scales);
+        VIP_CUDA(cudaMemsetAsync(N->act[0], 0, (size_t)N->ncells * CNN_CIN * 2, s));
+        k_ws_scatter<<<nblk(R, 256), 256, 0, s>>>(R, c->row_type, c->kind, c->row_geom, N->node_cell, c->hsol,
+                                                   c->hsol + R, c->prhs, c->phi, N->phi_old, N->scales,
+                                                   N->act[0]);
+        VIP_CUDA(cudaGetLastError());
+    }
     if (N->enable) {
         if (N->net) {
             vip_status st = forward(c, *N, N->img, (int)N->himg.size(), N->ntiles, N->act[0], s);
