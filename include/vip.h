@@ -85,6 +85,22 @@ enum { VIP_PREC_FP64 = 0, VIP_PREC_MIXED = 1, VIP_PREC_MG32 = 2 };
  *   EXACT  the identity; MLS  the MLS approximant D^[0,0] (Eq. vip:1). */
 enum { VIP_IDENTITY_EXACT = 0, VIP_IDENTITY_MLS = 1 };
 
+/* Pressure of Eqs. (12) and (15) (the paper prints r^n of Eq. 12 without a
+ * pressure term but Eq. 15 with p^n; these forms are readings of the pair):
+ *   INCREMENTAL           r^n carries -G p^n, so phi is the pressure increment,
+ *                         and p^{n+1} = p^n + phi - (dt/2Re) L phi at every node;
+ *   KIM_MOIN              r^n as printed (no pressure term), so phi is the whole
+ *                         pseudo-pressure of Kim and Moin, and
+ *                         p^{n+1} = phi - (dt/2Re) L phi (Eq. 15 without p^n); the
+ *                         steady state carries a splitting error of order dt;
+ *   INCREMENTAL_INTERIOR  INCREMENTAL with the term -(dt/2Re) L phi of Eq. 15 at
+ *                         interior nodes only (boundary nodes: p^n + phi).  At a
+ *                         boundary node L is a one-sided MLS fit; on the 28.072
+ *                         degree wedge of Sec. 5 the term there feeds a growing
+ *                         wall-pressure mode (an eigenvalue of the linearised
+ *                         step above 1), which this form does not have. */
+enum { VIP_PRESSURE_INCREMENTAL = 0, VIP_PRESSURE_KIM_MOIN = 1, VIP_PRESSURE_INCREMENTAL_INTERIOR = 2 };
+
 /* Tables and operators that can be exported (vip_get_stencil) or applied
  * (vip_apply).  Rows are global nodes; columns are global nodes, except the
  * column index N (total node count) of the POISSON operator, which is the
@@ -141,7 +157,8 @@ const char* vip_last_error(const vip_ctx* ctx);
  * n nodes; x, y coordinates; kind per node (VIP_NODE_*); nx, ny unit outward
  * normal of the fluid domain at boundary nodes (ignored at interior nodes);
  * h_local > 0, the local node spacing (rho = support * h_local, VIPs at
- * +-h_local/2, normal auxiliary points at h_local and 2 h_local); Lx, Ly > 0
+ * +-h_local/2, normal auxiliary points at h_local and 2 h_local, see
+ * vip_set_probes); Lx, Ly > 0
  * make the geometry periodic with that period (0 = not periodic).  All arrays
  * are copied.  *geom_out receives the geometry index (0, 1, ...).
  * Must precede vip_build. */
@@ -154,6 +171,28 @@ vip_status vip_add_nodes(vip_ctx* ctx, int64_t n, const double* x, const double*
  * 2, VIP_W_CUBIC_SPLINE, 2.2.  Must precede vip_build. */
 vip_status vip_set_mls(vip_ctx* ctx, int basis_order, int weight, double support);
 
+/* Placement of the two auxiliary points on the inward normal of a boundary node
+ * (the zero-normal-derivative rows of the pressure increment, q_i - 4/3 q(x_b1)
+ * + 1/3 q(x_b2) = 0; the paper states no boundary condition for phi, so these
+ * rows are a reading of Sec. 2 and 4):
+ *   NORMAL  x_b1 = x_i - h_local n_i, x_b2 = x_i - 2 h_local n_i;
+ *   INSIDE  the same with h_local replaced by a step s_i that starts at h_local
+ *           and is multiplied by 0.7 (at most 12 times) while x_b2 lies less
+ *           than 0.05 h_j inside the tangent at the boundary node j nearest to
+ *           x_b2, i.e. while (x_b2 - x_j) . n_j > -0.05 h_j.  Where two walls
+ *           meet at a narrow angle (the 28.072 degree apex of the triangular
+ *           cavity of Sec. 5) the plain points pass through the opposite wall.
+ * Nearest: smallest Euclidean distance (periodic minimum image) among the
+ * geometry's non-interior nodes.  INSIDE needs a support ratio above 2 (the
+ * search radius is the support radius of the boundary node, which contains
+ * x_b2); vip_build returns VIP_ERR_ARG otherwise. */
+enum { VIP_PROBES_NORMAL = 0, VIP_PROBES_INSIDE = 1 };
+
+/* Normal-point placement VIP_PROBES_* of geometry `geom` (-1 = every
+ * geometry); default NORMAL.  Must precede vip_build.  VIP_ERR_ARG for a bad
+ * mode or geometry index, or after vip_build. */
+vip_status vip_set_probes(vip_ctx* ctx, int32_t geom, int mode);
+
 /* Flow parameters of geometry `geom` (-1 = every geometry): Reynolds number
  * and time step of Sec. 2.  Must precede vip_build (the operators depend on
  * dt/Re). */
@@ -165,6 +204,11 @@ vip_status vip_set_flow(vip_ctx* ctx, int32_t geom, double Re, double dt);
  * The identity mode must be set before vip_build. */
 vip_status vip_set_solver(vip_ctx* ctx, int precision, double rtol, int32_t max_iters,
                           int identity);
+
+/* Pressure form VIP_PRESSURE_* of the fractional step (default INCREMENTAL).
+ * May be called at any time; the next step uses it.  VIP_ERR_ARG for a bad
+ * form. */
+vip_status vip_set_pressure(vip_ctx* ctx, int form);
 
 /* Inner tolerance of the MIXED form's refinement loop (not in the paper; the
  * solves of Eqs. 12-13 stop at the same FP64 residual whatever it is): each FP32

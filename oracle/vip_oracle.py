@@ -36,7 +36,12 @@ Pins (tests/test_oracle_*.py, all CPU):
     planted in these pins are caught (test_planted_mistakes_are_caught);
   * normal points (flag probes="inside", tests/test_paper_values.py): inside
     the exact edges of the 28-degree wedge cavity, unchanged on the square
-    cavity, and the wedge's steps stable with them and unstable without.
+    cavity, and the wedge's steps stable with them and unstable without;
+  * pressure="incremental_interior" (tests/test_oracle_pins.py): identical to the
+    incremental reading, bit for bit, where there are no boundary nodes (the
+    periodic box), and on the wedge (normal points inside) the step linearised
+    about rest has no eigenvalue above 1, where the incremental reading has one
+    (1 + 8.7e-4); planted mistakes in it are caught.
 """
 from __future__ import annotations
 
@@ -405,7 +410,10 @@ class FractionalStep:
                 projected divergence equals dt times the Poisson residual.
       pressure  'incremental': r^n carries -G p^n so that phi is the pressure
                 increment of Eq. (15), p^{n+1} = p^n + phi - (dt/2Re) L phi;
-                'kim_moin': r^n as printed, p^{n+1} = phi - (dt/2Re) L phi.
+                'kim_moin': r^n as printed, p^{n+1} = phi - (dt/2Re) L phi;
+                'incremental_interior': 'incremental' with the term
+                -(dt/2Re) L phi of Eq. (15) at interior nodes only (at a boundary
+                node L is a one-sided fit; the paper gives no boundary rule).
     Boundary rows: velocity Dirichlet rows hold the node's initial value; zero
     normal derivatives are imposed through the two MLS points on the inward normal
     (Operators.Nb); pressure-increment Dirichlet rows (outlet) set phi = 0.
@@ -423,6 +431,8 @@ class FractionalStep:
         self.maxit = maxit
         self.identity = identity
         self.poisson = poisson
+        if pressure not in ("incremental", "kim_moin", "incremental_interior"):
+            raise ValueError(f"unknown pressure reading {pressure!r}")
         self.pressure = pressure
         N = ops.N
         k = ns.kind
@@ -512,8 +522,9 @@ class FractionalStep:
         Nv_ab = 1.5 * Nv - 0.5 * self.N_prev[1]
         self.N_prev = (Nu, Nv)
         # Eq. (12) times dt: (I - al L) u* = (I + al L) u^n - dt [N^{n+1/2} + G p^n]
-        gpx = ops.Gx @ p if self.pressure == "incremental" else 0.0
-        gpy = ops.Gy @ p if self.pressure == "incremental" else 0.0
+        incremental = self.pressure != "kim_moin"
+        gpx = ops.Gx @ p if incremental else 0.0
+        gpy = ops.Gy @ p if incremental else 0.0
         ru = np.where(inner, self.Rm @ u - dt * (Nu_ab + gpx), 0.0)
         rv = np.where(inner, self.Rm @ v - dt * (Nv_ab + gpy), 0.0)
         ru = np.where(self.u_dir, self.u_bc, ru)
@@ -537,8 +548,7 @@ class FractionalStep:
         self.u = np.where(inner, us - dt * (ops.Gx @ phi), us)
         self.v = np.where(inner, vs - dt * (ops.Gy @ phi), vs)
         # Eq. (15)
-        base = p if self.pressure == "incremental" else 0.0
-        self.p = base + phi - al * (ops.L @ phi)
+        self.p = self.pressure_update(p, phi)
         self.phi = phi
         self.nstep += 1
         st = {"it_u": itu, "it_v": itv, "it_p": itp, "res_u": resu, "res_v": resv,
@@ -547,6 +557,14 @@ class FractionalStep:
         self.stats.append({k: v for k, v in st.items() if k != "poisson_residual"})
         self.last = st
         return st
+
+    def pressure_update(self, p, phi):
+        """Eq. (15) under the pressure reading: p^{n+1} from p^n and phi^{n+1}."""
+        base = p if self.pressure != "kim_moin" else 0.0
+        rot = self.ops.L @ phi
+        if self.pressure == "incremental_interior":
+            rot = np.where(self.inner, rot, 0.0)
+        return base + phi - self.alpha * rot
 
     def divergence(self, u=None, v=None):
         """div_vip of a velocity field at interior nodes (Sec. 4.1, item 2)."""

@@ -226,6 +226,17 @@ vip_status vip_set_flow(vip_ctx* c, int32_t geom, double Re, double dt) {
     return VIP_OK;
 }
 
+vip_status vip_set_probes(vip_ctx* c, int32_t geom, int mode) {
+    if (!c) return VIP_ERR_ARG;
+    if (c->built) return fail(c, VIP_ERR_ARG, "vip_set_probes after vip_build");
+    if (geom < -1 || geom >= (int32_t)c->geoms.size()) return fail(c, VIP_ERR_ARG, "bad geometry index");
+    if (mode != VIP_PROBES_NORMAL && mode != VIP_PROBES_INSIDE)
+        return fail(c, VIP_ERR_ARG, "vip_set_probes: mode must be VIP_PROBES_NORMAL or VIP_PROBES_INSIDE");
+    for (int32_t g = 0; g < (int32_t)c->geoms.size(); ++g)
+        if (geom == -1 || geom == g) c->geoms[g].probes = mode;
+    return VIP_OK;
+}
+
 vip_status vip_set_mg_shift(vip_ctx* c, int32_t geom, int32_t shift_x, int32_t shift_y) {
     if (!c) return VIP_ERR_ARG;
     if (c->built) return fail(c, VIP_ERR_ARG, "vip_set_mg_shift after vip_build");
@@ -345,6 +356,19 @@ vip_status vip_set_solver(vip_ctx* c, int precision, double rtol, int32_t max_it
     return VIP_OK;
 }
 
+vip_status vip_set_pressure(vip_ctx* c, int form) {
+    if (!c) return VIP_ERR_ARG;
+    if (form != VIP_PRESSURE_INCREMENTAL && form != VIP_PRESSURE_KIM_MOIN &&
+        form != VIP_PRESSURE_INCREMENTAL_INTERIOR)
+        return fail(c, VIP_ERR_ARG, "vip_set_pressure: bad form");
+    if (form != c->pressure && c->graph) {  // the step graph holds the launch arguments
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    c->pressure = form;
+    return VIP_OK;
+}
+
 vip_status vip_set_refinement(vip_ctx* c, double inner_rtol) {
     if (!c) return VIP_ERR_ARG;
     if (!(inner_rtol > 0.0) || !(inner_rtol < 1.0)) return fail(c, VIP_ERR_ARG, "inner_rtol must be in (0, 1)");
@@ -397,7 +421,9 @@ vip_status vip_build(vip_ctx* c) {
             if (pin < 0) return fail(c, VIP_ERR_ARG, "a closed geometry needs an interior node");
         }
         gd[gi] = GeomDev{g.row0, g.nrows, g.n, g.Lx, g.Ly, g.Re, g.dt, g.dt / (2.0 * g.Re),
-                         g.bordered ? 1 : 0, pin};
+                         g.bordered ? 1 : 0, pin, g.probes};
+        if (g.probes == VIP_PROBES_INSIDE && !(c->support > 2.0))
+            return fail(c, VIP_ERR_ARG, "VIP_PROBES_INSIDE needs a support ratio above 2");
     }
     cudaStream_t st = c->stream;
     VIP_CUDA(dalloc(c, &c->x, R)); VIP_CUDA(dalloc(c, &c->y, R)); VIP_CUDA(dalloc(c, &c->nx, R));

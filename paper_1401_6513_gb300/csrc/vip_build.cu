@@ -105,6 +105,8 @@ struct BuildArgs {
     const double* csy;
     const int64_t* cell_ptr;    // [C+1]
     const int32_t* cell_rows;   // [N]
+    // normal-point step of every row (VIP_PROBES_INSIDE), or null: h_local
+    const double* pstep;
 };
 
 // Coordinates and support radius of point p; returns false for an inactive slot.
@@ -126,12 +128,14 @@ __device__ __forceinline__ bool point_of(const BuildArgs& a, int64_t p, double& 
         case PT_W: qx = __dsub_rn(x, hh); qy = y; return k == VIP_NODE_INTERIOR;
         case PT_N: qx = x; qy = __dadd_rn(y, hh); return k == VIP_NODE_INTERIOR;
         case PT_S: qx = x; qy = __dsub_rn(y, hh); return k == VIP_NODE_INTERIOR;
-        case PT_B1:
-            qx = __dsub_rn(x, __dmul_rn(h, a.nx[r]));
-            qy = __dsub_rn(y, __dmul_rn(h, a.ny[r]));
+        case PT_B1: {
+            double sb = a.pstep ? a.pstep[r] : h;
+            qx = __dsub_rn(x, __dmul_rn(sb, a.nx[r]));
+            qy = __dsub_rn(y, __dmul_rn(sb, a.ny[r]));
             return k != VIP_NODE_INTERIOR;
+        }
         case PT_B2: {
-            double h2 = __dmul_rn(2.0, h);
+            double h2 = __dmul_rn(2.0, a.pstep ? a.pstep[r] : h);
             qx = __dsub_rn(x, __dmul_rn(h2, a.nx[r]));
             qy = __dsub_rn(y, __dmul_rn(h2, a.ny[r]));
             return k != VIP_NODE_INTERIOR;
@@ -194,6 +198,45 @@ __device__ __forceinline__ void for_each_neighbour(const BuildArgs& a, int gi, d
             }
         }
     }
+}
+
+// Normal-point step of every row (VIP_PROBES_INSIDE placement): a boundary node of
+// an INSIDE geometry starts from h_local and shrinks its step by 0.7, at most 12
+// times, while its second normal point x_b2 = x_i - 2 s n_i lies less than 5 % of
+// h_j inside the tangent at the boundary node j nearest to x_b2.  The nearest
+// node is searched within the support radius of node i, which contains x_b2 (at
+// 2 s <= 2 h_local < rho for a support ratio above 2) and hence node i itself.
+// Other rows keep h_local.  Explicitly rounded operations, as in point_of.
+__global__ void k_probe_steps(BuildArgs a, double* __restrict__ pstep) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.R) return;
+    double h = a.h[r];
+    double s = h;
+    if (a.row_type[r] == ROW_NODE && a.kind[r] != VIP_NODE_INTERIOR) {
+        int gi = a.row_geom[r];
+        if (a.g[gi].probes == VIP_PROBES_INSIDE) {
+            double x = a.x[r], y = a.y[r], nx = a.nx[r], ny = a.ny[r];
+            double rho = __dmul_rn(a.support, h);
+            for (int it = 0; it < 12; ++it) {
+                double s2 = __dmul_rn(2.0, s);
+                double qx = __dsub_rn(x, __dmul_rn(s2, nx));
+                double qy = __dsub_rn(y, __dmul_rn(s2, ny));
+                int best = -1;
+                double bx = 0.0, by = 0.0, bd2 = 0.0;
+                for_each_neighbour(a, gi, qx, qy, rho, [&](int j, double ddx, double ddy) {
+                    if (a.kind[j] == VIP_NODE_INTERIOR) return;
+                    double d2 = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));
+                    if (best < 0 || d2 < bd2) { best = j; bd2 = d2; bx = ddx; by = ddy; }
+                });
+                if (best < 0) break;
+                // (x_b2 - x_j) . n_j, with x_j - x_b2 = (bx, by) in the minimum image
+                double side = __dadd_rn(__dmul_rn(-bx, a.nx[best]), __dmul_rn(-by, a.ny[best]));
+                if (!(side > __dmul_rn(-0.05, a.h[best]))) break;
+                s = __dmul_rn(0.7, s);
+            }
+        }
+    }
+    pstep[r] = s;
 }
 
 __global__ void k_cell_count(BuildArgs a, int32_t* __restrict__ cell_cnt, int32_t* __restrict__ node_cell) {
@@ -853,6 +896,7 @@ vip_status build_all(vip_ctx* c) {
     a.support = c->support; a.weight = c->weight;
     a.cell_base = d_cell_base; a.ncx = d_ncx; a.ncy = d_ncy; a.cx0 = d_cx0; a.cy0 = d_cy0;
     a.csx = d_csx; a.csy = d_csy;
+    a.pstep = nullptr;
 
     int32_t *cell_cnt = nullptr, *node_cell = nullptr, *cursor = nullptr;
     int64_t* cell_ptr = nullptr;
@@ -872,6 +916,14 @@ vip_status build_all(vip_ctx* c) {
     VIP_CUDA(cudaGetLastError());
     a.cell_ptr = cell_ptr;
     a.cell_rows = cell_rows;
+    bool inside = false;
+    for (const Geom& gg : c->geoms) inside = inside || gg.probes == VIP_PROBES_INSIDE;
+    if (inside) {
+        VIP_CUDA(dalloc(c, &c->pstep, R));
+        k_probe_steps<<<(unsigned)((R + TB - 1) / TB), TB, 0, st>>>(a, c->pstep);
+        VIP_CUDA(cudaGetLastError());
+        a.pstep = c->pstep;
+    }
 
     int32_t* bad = nullptr;
     VIP_CUDA(dalloc(c, &bad, 1));

@@ -71,6 +71,7 @@ struct Geom {
     // parity of the multigrid's first 2h x 2h cell grid: 1 moves the cell boundaries
     // by one lattice spacing along that axis (non-periodic axes only)
     int32_t mg_shift_x = 0, mg_shift_y = 0;
+    int32_t probes = VIP_PROBES_NORMAL;  // normal-point placement (vip_set_probes)
 };
 
 // Per-geometry constants visible to kernels.
@@ -79,6 +80,7 @@ struct GeomDev {
     double Lx, Ly, Re, dt, alpha;
     int32_t bordered;
     int64_t pin;       // bordered: padded row of the reference node k (first interior node)
+    int32_t probes;    // VIP_PROBES_*
 };
 
 // Work split of a persistent Krylov launch over a batch of systems.
@@ -149,6 +151,7 @@ struct vip_ctx {
     double rtol = 1e-8;
     int32_t max_iters = 20000;
     int identity = VIP_IDENTITY_EXACT;
+    int pressure = VIP_PRESSURE_INCREMENTAL;  // VIP_PRESSURE_* (vip_set_pressure)
     double inner_rtol = 1e-4;     // FP32 inner solve target relative to the FP64 residual
     bool built = false;
     bool use_graph = true;
@@ -163,6 +166,7 @@ struct vip_ctx {
     int8_t* row_type = nullptr;    // [R] ROW_PAD / ROW_NODE / ROW_BORDER
     double* inv_ew = nullptr;      // [R] 1/|x_e - x_w|
     double* inv_ns = nullptr;      // [R] 1/|x_n - x_s|
+    double* pstep = nullptr;       // [R] normal-point step of boundary rows (INSIDE geometries only)
     vip::GeomDev* gdev = nullptr;  // [G]
     int32_t* first_row = nullptr;  // [G]
     vip::Tables T;

@@ -20,6 +20,8 @@ struct StepArgs {
     const double* inv_ns;
     Sell ve, vw, vn, vs, gx, gy, lap, d00;
     int identity;
+    int incremental;   // 1: r^n carries -G p^n and p^{n+1} adds p^n (not VIP_PRESSURE_KIM_MOIN)
+    int rot_interior;  // 1: the term -(dt/2Re) L phi of Eq. 15 at interior nodes only
     const int64_t* step;
 };
 
@@ -88,13 +90,14 @@ __global__ void k_conv_rhs(StepArgs a, const double* __restrict__ u, const doubl
             if (*a.step > 0) { Nu0 = nu_prev[r]; Nv0 = nv_prev[r]; }
             nu_prev[r] = Nu;
             nv_prev[r] = Nv;
-            double gpx = gather(a.gx, r, p), gpy = gather(a.gy, r, p);
+            double gpx = 0.0, gpy = 0.0;
+            if (a.incremental) { gpx = gather(a.gx, r, p); gpy = gather(a.gy, r, p); }
             double lu, lv;
             gather2(a.lap, r, u, v, lu, lv);
             double iu, iv;
             if (a.identity == VIP_IDENTITY_MLS) gather2(a.d00, r, u, v, iu, iv);
             else { iu = u[r]; iv = v[r]; }
-            // (I + al L) u^n - dt [ (3 N^n - N^{n-1}) / 2 + G p^n ]
+            // (I + al L) u^n - dt [ (3 N^n - N^{n-1}) / 2 + G p^n ]  (no G p^n: KIM_MOIN)
             ru = iu + G.alpha * lu - G.dt * ((1.5 * Nu - 0.5 * Nu0) + gpx);
             rv = iv + G.alpha * lv - G.dt * ((1.5 * Nv - 0.5 * Nv0) + gpy);
         } else {
@@ -137,8 +140,11 @@ __global__ void k_project(StepArgs a, const double* __restrict__ hsol, const dou
     }
     u[r] = us;
     v[r] = vs;
-    // Eq. (15): p^{n+1} = p^n + phi - (dt / 2Re) L phi
-    p[r] = p[r] + phi[r] - G.alpha * gather(a.lap, r, phi);
+    // Eq. (15): p^{n+1} = p^n + phi - (dt / 2Re) L phi (KIM_MOIN: without p^n;
+    // INCREMENTAL_INTERIOR: without the L phi term at boundary nodes)
+    double base = a.incremental ? p[r] : 0.0;
+    double rot = (a.rot_interior && a.kind[r] != VIP_NODE_INTERIOR) ? 0.0 : G.alpha * gather(a.lap, r, phi);
+    p[r] = base + phi[r] - rot;
 }
 
 __global__ void k_spmv(Sell A, const double* __restrict__ x, double* __restrict__ y) {
@@ -164,6 +170,8 @@ static StepArgs step_args(vip_ctx* c) {
     a.ve = c->T.ve; a.vw = c->T.vw; a.vn = c->T.vn; a.vs = c->T.vs;
     a.gx = c->T.gx; a.gy = c->T.gy; a.lap = c->T.lap; a.d00 = c->T.d00;
     a.identity = c->identity;
+    a.incremental = c->pressure != VIP_PRESSURE_KIM_MOIN ? 1 : 0;
+    a.rot_interior = c->pressure == VIP_PRESSURE_INCREMENTAL_INTERIOR ? 1 : 0;
     a.step = c->d_step;
     return a;
 }

@@ -23,6 +23,8 @@ VIP_NODE_INTERIOR, VIP_NODE_WALL, VIP_NODE_SLIP, VIP_NODE_OUTLET = 0, 1, 2, 3
 VIP_W_CUBIC_SPLINE, VIP_W_PAPER = 0, 1
 VIP_PREC_FP64, VIP_PREC_MIXED, VIP_PREC_MG32 = 0, 1, 2
 VIP_IDENTITY_EXACT, VIP_IDENTITY_MLS = 0, 1
+VIP_PROBES_NORMAL, VIP_PROBES_INSIDE = 0, 1
+VIP_PRESSURE_INCREMENTAL, VIP_PRESSURE_KIM_MOIN, VIP_PRESSURE_INCREMENTAL_INTERIOR = 0, 1, 2
 OPS = ["NBR", "D00", "D10", "D01", "D20", "D11", "D02", "LAPLACE", "VIP_E", "VIP_W", "VIP_N",
        "VIP_S", "GX", "GY", "HELM_U", "HELM_V", "POISSON"]
 OP = {name: i for i, name in enumerate(OPS)}
@@ -36,7 +38,8 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_ws_enable", "vip_ws_params", "vip_ws_eval", "vip_bicgstab_static",
            "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout",
            "vip_multigrid_info", "vip_set_mg_shift", "vip_set_refinement", "vip_checkpoint_size",
-           "vip_checkpoint", "vip_ws_adam", "vip_ws_extrapolation", "vip_ws_set_loss"]
+           "vip_checkpoint", "vip_ws_adam", "vip_ws_extrapolation", "vip_ws_set_loss",
+           "vip_set_probes", "vip_set_pressure"]
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -124,6 +127,8 @@ def lib(path: str | Path | None = None):
                                  C.POINTER(dbl)], C.c_int),
         "vip_set_multigrid": ([vp, C.c_float, C.c_float], C.c_int),
         "vip_set_mg_shift": ([vp, i32, i32, i32], C.c_int),
+        "vip_set_probes": ([vp, i32, C.c_int], C.c_int),
+        "vip_set_pressure": ([vp, C.c_int], C.c_int),
         "vip_get_geometry_iters": ([vp, vp], C.c_int),
         "vip_operator_layout": ([vp, C.c_int, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64),
                                  C.POINTER(i64)], C.c_int),
@@ -253,11 +258,25 @@ class Context:
         self._check(self.L.vip_set_mg_shift(self.h, int(geom), int(shift_x), int(shift_y)))
         self.__dict__.setdefault("_mg_shift_calls", []).append((int(geom), int(shift_x), int(shift_y)))
 
+    def vip_set_probes(self, geom, mode):
+        """Normal-point placement VIP_PROBES_NORMAL / VIP_PROBES_INSIDE of geometry geom
+        (-1: every geometry); before vip_build."""
+        self._check(self.L.vip_set_probes(self.h, int(geom), int(mode)))
+        self.__dict__.setdefault("_probe_calls", []).append((int(geom), int(mode)))
+
+    def vip_set_pressure(self, form):
+        """Pressure form VIP_PRESSURE_INCREMENTAL / _KIM_MOIN / _INCREMENTAL_INTERIOR."""
+        self._check(self.L.vip_set_pressure(self.h, int(form)))
+
     def mg_shift_key(self):
-        """The vip_set_mg_shift calls made on this context, as a suffix of the
-        autotuning cache key ("" when the parity is the default everywhere)."""
+        """The vip_set_mg_shift (and vip_set_probes) calls made on this context, as a
+        suffix of the autotuning cache key ("" when both are the defaults everywhere)."""
         calls = self.__dict__.get("_mg_shift_calls", [])
-        return "|mg:" + ",".join(f"{g}:{x}{y}" for g, x, y in calls) if calls else ""
+        key = "|mg:" + ",".join(f"{g}:{x}{y}" for g, x, y in calls) if calls else ""
+        probes = self.__dict__.get("_probe_calls", [])
+        if any(m != VIP_PROBES_NORMAL for _, m in probes):
+            key += "|probes:" + ",".join(f"{g}:{m}" for g, m in probes)
+        return key
 
     def vip_autotune(self, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.6, 1.7, 1.8, 1.9, 2.1)) -> TuneResult:
         """Time the last step's pressure-increment solve for every (omega, corr) pair
@@ -561,9 +580,13 @@ def autotune(ctx, nodesets, cache=None, omegas=(0.9, 1.0), corrs=(1.3, 1.5, 1.6,
 
 def solver_for(nodesets, precision=VIP_PREC_FP64, rtol=1e-8, max_iters=20000,
                identity=VIP_IDENTITY_EXACT, weight=VIP_W_CUBIC_SPLINE, support=2.2,
-               device=0, stream=None, set_state=True, mg_shifts=None) -> Context:
+               device=0, stream=None, set_state=True, mg_shifts=None, probes="normal",
+               pressure="incremental") -> Context:
     """Create a context for one node set or a list of them, build it and set u0, v0, p0.
-    mg_shifts: one (shift_x, shift_y) per node set for vip_set_mg_shift (default 0, 0)."""
+    mg_shifts: one (shift_x, shift_y) per node set for vip_set_mg_shift (default 0, 0).
+    probes: "normal" or "inside", the normal-point placement of every node set
+    (vip_set_probes).  pressure: "incremental", "kim_moin" or "incremental_interior"
+    (vip_set_pressure)."""
     if not isinstance(nodesets, (list, tuple)):
         nodesets = [nodesets]
     ctx = Context(device, stream)
@@ -574,6 +597,17 @@ def solver_for(nodesets, precision=VIP_PREC_FP64, rtol=1e-8, max_iters=20000,
             raise ValueError("one (shift_x, shift_y) per node set")
         for g, (sx, sy) in enumerate(mg_shifts):
             ctx.vip_set_mg_shift(g, sx, sy)
+    modes = {"normal": VIP_PROBES_NORMAL, "inside": VIP_PROBES_INSIDE}
+    if probes not in modes:
+        raise ValueError(f"probes must be 'normal' or 'inside', not {probes!r}")
+    if probes != "normal":
+        ctx.vip_set_probes(-1, modes[probes])
+    forms = {"incremental": VIP_PRESSURE_INCREMENTAL, "kim_moin": VIP_PRESSURE_KIM_MOIN,
+             "incremental_interior": VIP_PRESSURE_INCREMENTAL_INTERIOR}
+    if pressure not in forms:
+        raise ValueError(f"pressure must be one of {sorted(forms)}, not {pressure!r}")
+    if pressure != "incremental":
+        ctx.vip_set_pressure(forms[pressure])
     ctx.vip_set_mls(2, weight, support)
     ctx.vip_set_solver(precision, rtol, max_iters, identity)
     ctx.vip_build()

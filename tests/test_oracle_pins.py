@@ -433,6 +433,76 @@ def test_kim_moin_pressure_is_time_centred():
     assert kim_moin_holds()
 
 
+def stokes_step_spectral_radius(fs, k=6):
+    """Largest |eigenvalue| of the fractional step linearised about rest: no
+    convection, homogeneous boundary values, direct solves, the map (u, v, p) ->
+    (u', v', p') of Eqs. (12)-(15) under fs's pressure reading (fs.pressure_update),
+    with the free constant of p (a closed domain) removed."""
+    N = fs.ops.N
+    inner, dt = fs.inner, fs.dt
+    Gx, Gy = fs.ops.Gx, fs.ops.Gy
+    Hu, Hv, P = (spl.splu(A.tocsc()) for A in (fs.Hu, fs.Hv, fs.P))
+    incremental = fs.pressure != "kim_moin"
+
+    def step(s):
+        u, v, p = s[:N], s[N:2 * N], s[2 * N:]
+        ru, rv = fs.Rm @ u, fs.Rm @ v
+        if incremental:
+            ru, rv = ru - dt * (Gx @ p), rv - dt * (Gy @ p)
+        us = Hu.solve(np.where(inner, ru, 0.0))
+        vs = Hv.solve(np.where(inner, rv, 0.0))
+        b = np.where(inner, (Gx @ us + Gy @ vs) / dt, 0.0)
+        if fs.bordered:
+            b = np.append(b, b[fs.pin])
+            b[fs.pin] = 0.0
+        phi = P.solve(b)[:N]
+        p2 = fs.pressure_update(p, phi)
+        if fs.bordered:
+            p2 = p2 - p2[fs.pin]
+        return np.concatenate([np.where(inner, us - dt * (Gx @ phi), us),
+                               np.where(inner, vs - dt * (Gy @ phi), vs), p2])
+
+    op = spl.LinearOperator((3 * N, 3 * N), matvec=step, dtype=np.float64)
+    vals = spl.eigs(op, k=k, which="LM", tol=1e-10, maxiter=20000, return_eigenvectors=False)
+    return float(np.max(np.abs(vals)))
+
+
+def wedge_fs(fs_class, pressure):
+    ns = w.wedge_cavity(33, Re=1.0, dt=1.6 / 32 ** 2)   # alpha / h^2 = 0.8
+    return fs_class(vo.Operators(ns, probes="inside"), pressure=pressure)
+
+
+def interior_reading_holds(fs_class=vo.FractionalStep):
+    """pressure='incremental_interior' (the (dt/2Re) L phi term of Eq. 15 at interior
+    nodes only): (a) with no boundary nodes (the periodic box) it is the incremental
+    reading, bit for bit, over five steps; (b) on the 28.072 degree wedge of Sec. 5
+    (n_base = 33, Re = 1, alpha/h^2 = 0.8, normal points inside) the step linearised
+    about rest has no eigenvalue above 1 + 1e-9."""
+    ops = vo.Operators(w.periodic_box(16, Re=100.0, dt=1e-3))
+    a = fs_class(ops, rtol=1e-12, pressure="incremental_interior")
+    b = vo.FractionalStep(ops, rtol=1e-12, pressure="incremental")
+    for _ in range(5):
+        a.step()
+        b.step()
+    if not all(np.array_equal(x, y) for x, y in ((a.u, b.u), (a.v, b.v), (a.p, b.p))):
+        return False
+    return stokes_step_spectral_radius(wedge_fs(fs_class, "incremental_interior")) <= 1.0 + 1e-9
+
+
+def test_interior_pressure_reading_is_stable_on_the_wedge():
+    """The wall-pressure mode of the incremental reading on the wedge, and the
+    reading without it.  Linearised about rest, the incremental step (the (dt/2Re)
+    L phi term of Eq. 15 at every node, with the one-sided MLS Laplacian at the wall
+    nodes) has an eigenvalue above 1 (1 + 8.7e-4 measured: a mode that lives in the
+    wall pressures about 38 lattice spacings from the apex, and grows on the GPU at
+    n_base = 129 and 257); with the term at interior nodes only every eigenvalue
+    lies within 1 + 1e-9 (the largest are the neutral modes of p: its constant and
+    the null space of G), and the printed (Kim-Moin) form is stable too."""
+    assert stokes_step_spectral_radius(wedge_fs(vo.FractionalStep, "incremental")) > 1.0 + 5e-4
+    assert interior_reading_holds()
+    assert stokes_step_spectral_radius(wedge_fs(vo.FractionalStep, "kim_moin")) < 1.0
+
+
 def mls_identity_quadratics_hold(ops, identity_op=None):
     """Both readings' Helmholtz and right-hand-side operators agree on quadratics at
     interior rows (identity_op replaces D^[0,0] for planted mistakes)."""
@@ -468,7 +538,9 @@ def test_planted_mistakes_are_caught():
     """Mistakes planted in the oracle (on the CPU) fail the pins written for them:
     the printed weight with exponent (1 - r) or a square in place of the fourth power;
     the kim_moin pressure with the sign of its (dt/2Re) L phi term flipped, with the
-    term dropped, or accumulated onto p^n; D^[1,0] in place of D^[0,0] as the identity."""
+    term dropped, or accumulated onto p^n; the incremental_interior pressure with its
+    L phi term dropped, applied at boundary nodes only, or at every node; D^[1,0] in
+    place of D^[0,0] as the identity."""
     assert not paper_weight_asymptotics_hold(lambda r: np.where(np.asarray(r) < 1, (1 - np.power(r, 1 - np.asarray(r))) ** 4, 0.0))
     assert not paper_weight_asymptotics_hold(lambda r: np.where(np.asarray(r) < 1, (1 - np.power(r, (1 - np.asarray(r)) ** 2)) ** 2, 0.0))
 
@@ -493,5 +565,20 @@ def test_planted_mistakes_are_caught():
 
     for planted in (Flipped, Dropped, Accumulated):
         assert not kim_moin_holds(planted), planted.__name__
+
+    class NoRotation(vo.FractionalStep):      # the L phi term dropped everywhere
+        def pressure_update(self, p, phi):
+            return p + phi
+
+    class BoundaryOnly(vo.FractionalStep):    # the mask inverted
+        def pressure_update(self, p, phi):
+            return p + phi - self.alpha * np.where(self.inner, 0.0, self.ops.L @ phi)
+
+    class EveryNode(vo.FractionalStep):       # the mask ignored
+        def pressure_update(self, p, phi):
+            return p + phi - self.alpha * (self.ops.L @ phi)
+
+    for planted in (NoRotation, BoundaryOnly, EveryNode):
+        assert not interior_reading_holds(planted), planted.__name__
     ops = vo.Operators(w.cavity(12, Re=100.0))
     assert not mls_identity_quadratics_hold(ops, identity_op=ops.D[(1, 0)])
