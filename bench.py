@@ -258,7 +258,14 @@ def run_reference(args, rank, ws):
 # launch divided by its inner iterations; profiles/): every iteration streams the same
 # operator and vectors, so a launch's traffic scales with its iterations.  Keyed by
 # workload and form; a form whose kernel changed since its capture has no entry.
-TRAFFIC_PER_ITER = {}
+TRAFFIC_PER_ITER = {
+    # 12.172 GB read + 4.557 GB written by the timed step's launch, 40 iterations
+    ("bumpy_h64", "mixed"): 16.729e9 / 40,
+    # 25.232 GB + 9.361 GB, 38 iterations
+    ("bumpy_h64", "fp64"): 34.592e9 / 38,
+    # 129.4 MB + 14.3 MB, 23 iterations (the working set fits in L2)
+    ("cylinder_h32", "mixed"): 143.6e6 / 23,
+}
 
 # FP64 operations per clock per SM of GB300 (two FP64 FMAs), for the ALU roofline;
 # 152 SMs at 2070 MHz give 1.26 TFLOP/s, the part's nominal FP64 rate.
