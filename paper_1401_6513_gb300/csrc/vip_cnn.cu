@@ -76,20 +76,22 @@ __global__ void k_pack_bias(const float* __restrict__ b, int creal, int cout, fl
     if (i < cout) out[i] = i < creal ? b[i] : 0.0f;
 }
 
-// per-geometry scales (one block per geometry, fixed order)
-// Per geometry (one block each): s_b the RMS of b over interior nodes; S the RMS of
-// phi^n (s_b h^2 if phi^n = 0); D the RMS of (phi^n - phi^{n-1}) / S over interior
-// nodes (1 if zero): the network sees the history channel and predicts its
-// correction in units of S D, the size of the last change, so inputs and targets are
-// O(1) whatever the flow's time scale.
-__global__ void k_ws_scales(const GeomDev* __restrict__ g, const int8_t* __restrict__ rt,
-                            const uint8_t* __restrict__ kind, const double* __restrict__ b,
-                            const double* __restrict__ phi, const double* __restrict__ phi_old,
-                            const double* __restrict__ hlat, double* __restrict__ scales) {
-    __shared__ double sb[1024], sp[1024], sn[1024], sd[1024];
-    const GeomDev& G = g[blockIdx.x];
+// Per-geometry scales of the network's input, in two fixed-order passes (so the
+// same state always gives the same scales).  Pass 1: block (chunk k, geometry g)
+// sums, over its share of g's rows, b^2 and 1 at interior nodes, phi^2 at all
+// nodes, and (phi - phi_old)^2 at interior nodes; tree sum in shared memory.
+constexpr int WS_CHUNKS = 128;   // blocks per geometry in pass 1
+__global__ void k_ws_scales_part(const GeomDev* __restrict__ g, const int8_t* __restrict__ rt,
+                                 const uint8_t* __restrict__ kind, const double* __restrict__ b,
+                                 const double* __restrict__ phi, const double* __restrict__ phi_old,
+                                 double* __restrict__ part) {
+    __shared__ double sq[4][256];
+    const GeomDev& G = g[blockIdx.y];
+    const int64_t len = (G.n + WS_CHUNKS - 1) / WS_CHUNKS;
+    const int64_t r0 = G.row0 + (int64_t)blockIdx.x * len;
+    const int64_t r1 = min(r0 + len, G.row0 + G.n);
     double a = 0, p = 0, n = 0, d = 0;
-    for (int64_t r = G.row0 + threadIdx.x; r < G.row0 + G.n; r += blockDim.x) {
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
         if (rt[r] != ROW_NODE) continue;
         if (kind[r] == VIP_NODE_INTERIOR) {
             a += b[r] * b[r];
@@ -99,23 +101,37 @@ __global__ void k_ws_scales(const GeomDev* __restrict__ g, const int8_t* __restr
         }
         p += phi[r] * phi[r];
     }
-    sb[threadIdx.x] = a; sp[threadIdx.x] = p; sn[threadIdx.x] = n; sd[threadIdx.x] = d;
+    sq[0][threadIdx.x] = a; sq[1][threadIdx.x] = p; sq[2][threadIdx.x] = n; sq[3][threadIdx.x] = d;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) {
-            sb[threadIdx.x] += sb[threadIdx.x + s];
-            sp[threadIdx.x] += sp[threadIdx.x + s];
-            sn[threadIdx.x] += sn[threadIdx.x + s];
-            sd[threadIdx.x] += sd[threadIdx.x + s];
-        }
+        if ((int)threadIdx.x < s)
+            for (int q = 0; q < 4; ++q) sq[q][threadIdx.x] += sq[q][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[((int64_t)blockIdx.y * WS_CHUNKS + blockIdx.x) * 4 + threadIdx.x] = sq[threadIdx.x][0];
+}
+
+// Pass 2: one block per geometry sums its chunks' partials (tree sum) and forms
+// s_b (RMS of b over interior nodes), S (RMS of phi, or s_b h^2 when phi = 0) and
+// D (RMS of (phi - phi_old) / S over interior nodes, 1 when zero).
+__global__ void k_ws_scales(const GeomDev* __restrict__ g, const double* __restrict__ part,
+                            const double* __restrict__ hlat, double* __restrict__ scales) {
+    __shared__ double sq[4][WS_CHUNKS];
+    const GeomDev& G = g[blockIdx.x];
+    for (int q = 0; q < 4; ++q)
+        sq[q][threadIdx.x] = part[((int64_t)blockIdx.x * WS_CHUNKS + threadIdx.x) * 4 + q];
+    __syncthreads();
+    for (int s = WS_CHUNKS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int q = 0; q < 4; ++q) sq[q][threadIdx.x] += sq[q][threadIdx.x + s];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double nn = fmax(sn[0], 1.0);
-        double s_b = sqrt(sb[0] / nn) + 1e-300;
-        double rp = sqrt(sp[0] / (double)G.n);
+        double nn = fmax(sq[2][0], 1.0);
+        double s_b = sqrt(sq[0][0] / nn) + 1e-300;
+        double rp = sqrt(sq[1][0] / (double)G.n);
         double S = rp > 0.0 ? rp : s_b * hlat[blockIdx.x] * hlat[blockIdx.x];
-        double D = sqrt(sd[0] / nn) / S;
+        double D = sqrt(sq[3][0] / nn) / S;
         scales[3 * blockIdx.x] = s_b;
         scales[3 * blockIdx.x + 1] = S;
         scales[3 * blockIdx.x + 2] = D > 0.0 ? D : 1.0;
@@ -411,6 +427,7 @@ struct Cnn {
     uint8_t* deep = nullptr;        // [cells] 1: an interior node whose four lattice neighbours are too
     double* hlat = nullptr;
     double* scales = nullptr;
+    double* scale_part = nullptr;   // [G][WS_CHUNKS][4] partial sums of the scales
     // activations of one pass: act[0] input, act[1..5] hidden, out (FP32), grads
     __nv_bfloat16* act[CNN_LAYERS] = {};
     float* out = nullptr;
@@ -688,6 +705,7 @@ vip_status cnn_setup(vip_ctx* c, uint64_t seed) {
     VIP_CUDA(dalloc(c, &N->hlat, G));
     VIP_CUDA(cudaMemcpy(N->hlat, hl.data(), G * 8, cudaMemcpyHostToDevice));
     VIP_CUDA(dalloc(c, &N->scales, 3 * G));
+    VIP_CUDA(dalloc(c, &N->scale_part, (size_t)G * WS_CHUNKS * 4));
     VIP_CUDA(dalloc(c, &N->phi_prev, c->R));
     VIP_CUDA(dalloc(c, &N->phi_old, c->R));
     VIP_CUDA(dalloc(c, &N->extrap, 1));
@@ -717,8 +735,10 @@ vip_status cnn_warm_start(vip_ctx* c, cudaStream_t s) {
     const int64_t R = c->R;
     VIP_CUDA(cudaMemcpyAsync(N->phi_prev, c->phi, R * 8, cudaMemcpyDeviceToDevice, s));
     if (N->collect || (N->enable && N->net)) {  // the network's input (the extrapolation alone needs none)
-        k_ws_scales<<<(unsigned)c->geoms.size(), 1024, 0, s>>>(c->gdev, c->row_type, c->kind, c->prhs, c->phi,
-                                                              N->phi_old, N->hlat, N->scales);
+        k_ws_scales_part<<<dim3(WS_CHUNKS, (unsigned)c->geoms.size()), 256, 0, s>>>(
+            c->gdev, c->row_type, c->kind, c->prhs, c->phi, N->phi_old, N->scale_part);
+        k_ws_scales<<<(unsigned)c->geoms.size(), WS_CHUNKS, 0, s>>>(c->gdev, N->scale_part, N->hlat,
+                                                                    N->scales);
         VIP_CUDA(cudaMemsetAsync(N->act[0], 0, (size_t)N->ncells * CNN_CIN * 2, s));
         k_ws_scatter<<<nblk(R, 256), 256, 0, s>>>(R, c->row_type, c->kind, c->row_geom, N->node_cell, c->hsol,
                                                    c->hsol + R, c->prhs, c->phi, N->phi_old, N->scales,

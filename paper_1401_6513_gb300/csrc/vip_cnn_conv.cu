@@ -1,18 +1,24 @@
 // 3x3 convolution of the warm-start network as an implicit GEMM on the 5th-generation
 // tensor cores (tcgen05, kind::f16: BF16 x BF16 -> FP32 accumulators in TMEM).
 //
-// A CTA owns one TMEM accumulator of 128 lanes x Cout columns and loops over tiles
-// of 128 consecutive pixels of one lattice row (persistent grid).  Per tile it
-// stages the 3 x 130 halo of the input in shared memory, channel-chunk planar:
-// plane[c][row][col] holds channels 8c..8c+7 (16 bytes) of one pixel.  In that
-// layout the 8-pixel x 8-channel core matrices of the MMA operand A are 128
-// contiguous bytes, so every one of the nine taps is the same operand seen from a
-// shifted start address -- no im2col copy.  The weights sit in shared memory for the
-// whole launch in the same core-matrix layout ([tap][chunk][cout][8 ci]).  One
-// thread issues 9 * Cin/16 MMAs (K = 16 each) and commits them to an mbarrier; the
-// four warps then read their 32 TMEM lanes with tcgen05.ld and run the epilogue.
-// Four CTAs share an SM, so one CTA's staging overlaps another's MMAs and epilogue.
-// Every mbarrier wait is bounded (2 s, then VIP_ERR_TIMEOUT); TMEM is always freed.
+// A CTA loops over tiles of 128 consecutive pixels of one lattice row (persistent
+// grid).  Per tile it stages the 3 x 130 halo of the input in shared memory,
+// channel-chunk planar: plane[c][row][col] holds channels 8c..8c+7 (16 bytes) of one
+// pixel.  In that layout the 8-pixel x 8-channel core matrices of the MMA operand A
+// are 128 contiguous bytes, so every one of the nine taps is the same operand seen
+// from a shifted start address -- no im2col copy.  The weights sit in shared memory
+// for the whole launch in the same core-matrix layout ([tap][chunk][cout][8 ci]).
+// One thread issues 9 * Cin/16 MMAs (K = 16 each) and commits them to an mbarrier;
+// the four warps then read their 32 TMEM lanes with tcgen05.ld and run the epilogue.
+//
+// Pipeline: two halo buffers and two TMEM accumulators.  The halo of a tile is
+// fetched with cp.async (16-byte copies, zero-filled outside the image), so all of a
+// thread's copies are in flight at once, and the tile after next is fetched while
+// the current tile's MMAs run and the previous tile's epilogue drains its
+// accumulator: in iteration k the CTA waits for the MMAs of tile k, issues those of
+// tile k+1 (whose halo landed during iteration k-1), starts the copies of tile k+2
+// into the buffer tile k has released, and then runs tile k's epilogue.  Every
+// mbarrier wait is bounded (2 s, then VIP_ERR_TIMEOUT); TMEM is always freed.
 #include <algorithm>
 #include <cstdio>
 
@@ -25,10 +31,10 @@ constexpr int PLANE_BYTES = 3 * PLANE_COLS * 16;       // 6240
 constexpr int MAX_CHUNKS = CNN_CH / 8;                 // 4
 constexpr int SMEM_IN = MAX_CHUNKS * PLANE_BYTES;      // 24960
 constexpr int SMEM_W = 9 * MAX_CHUNKS * CNN_CH * 16;   // 18432
-// Operands, the mbarrier, the TMEM address word and the failure flag: small enough
-// for four CTAs (4 x 32 TMEM columns) per SM, so one CTA's staging overlaps another's
-// MMAs and epilogue.
-constexpr int SMEM_CONV = SMEM_IN + SMEM_W + 32;
+// Two halo buffers, the weights, two mbarriers, the TMEM address word and the
+// failure flag: three CTAs (3 x 64 TMEM columns) per SM.
+constexpr int SMEM_CONV = 2 * SMEM_IN + SMEM_W + 64;
+constexpr int CONV_CTAS_PER_SM = 3;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -138,22 +144,82 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16-byte asynchronous copy global -> shared; src_bytes 0 writes zeros (the source
+// address is then not read, but is still a valid one).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// Where tile t lies: its image, lattice row and first column.
+struct ConvTile {
+    CnnImage I;
+    int y, x0;
+};
+__device__ __forceinline__ ConvTile conv_tile(const CnnConvArgs& a, int64_t tile) {
+    int im = 0;
+    while (im + 1 < a.nimg && a.img[im + 1].tile0 <= tile) ++im;
+    ConvTile t;
+    t.I = a.img[im];
+    const int64_t tloc = tile - t.I.tile0;
+    const int tpr = (t.I.W + CNN_TILE - 1) / CNN_TILE;  // tiles per row
+    t.y = (int)(tloc / tpr);
+    t.x0 = (int)(tloc % tpr) * CNN_TILE;
+    return t;
+}
+
+// Start the copies of a tile's halo into the planes at buf: [chunk][3][130] x 16
+// bytes, zero outside the image.  One commit group per call.
+__device__ __forceinline__ void conv_stage(const CnnConvArgs& a, const ConvTile& t, uint32_t buf,
+                                           int nch, int tid) {
+    const int nitem = nch * 3 * PLANE_COLS;
+    for (int i = tid; i < nitem; i += blockDim.x) {
+        const int c = i / (3 * PLANE_COLS);
+        const int rem = i - c * 3 * PLANE_COLS;
+        const int r = rem / PLANE_COLS;
+        const int col = rem - r * PLANE_COLS;
+        const int yy = t.y - 1 + r, xx = t.x0 - 1 + col;
+        const bool in = yy >= 0 && yy < t.I.H && xx >= 0 && xx < t.I.W;
+        const __nv_bfloat16* src = a.x;
+        if (in) src = a.x + (t.I.off + (int64_t)yy * t.I.W + xx) * a.cin + c * 8;
+        cp_async16(buf + c * PLANE_BYTES + (r * PLANE_COLS + col) * 16, src, in ? 16u : 0u);
+    }
+    cp_async_commit();
+}
+
+// The 9 * Cin/16 MMAs of one tile: halo planes at in_addr, accumulator at tmem_d.
+__device__ __forceinline__ void conv_mma(uint32_t in_addr, uint32_t w_base, uint32_t tmem_d,
+                                         uint32_t idesc, int nch, int cout) {
+    uint32_t acc = 0;
+    for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;  // 0..2 = offset + 1
+        for (int kc = 0; kc < nch / 2; ++kc) {
+            const uint32_t aaddr = in_addr + (2 * kc) * PLANE_BYTES + (dy * PLANE_COLS + dx) * 16;
+            const uint32_t baddr = w_base + (tap * nch + 2 * kc) * cout * 16;
+            umma_bf16(tmem_d, umma_desc(aaddr, PLANE_BYTES, 128), umma_desc(baddr, cout * 16, 128),
+                      idesc, acc);
+            acc = 1;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128) k_conv_tc(CnnConvArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* s_in = smem;
-    uint8_t* s_w = smem + SMEM_IN;
-    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + SMEM_IN + SMEM_W);
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + SMEM_IN + SMEM_W + 8);
-    int* s_fail = reinterpret_cast<int*>(smem + SMEM_IN + SMEM_W + 16);
+    uint8_t* s_w = smem + 2 * SMEM_IN;
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + 2 * SMEM_IN + SMEM_W);  // [2]
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + 2 * SMEM_IN + SMEM_W + 16);
+    int* s_fail = reinterpret_cast<int*>(smem + 2 * SMEM_IN + SMEM_W + 20);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cin = a.cin, cout = a.cout;
     const int nch = cin / 8;
-    const int ncol = 32;  // TMEM columns (power of two >= cout)
+    const int ncol = 64;  // TMEM columns: two accumulators of 32 (>= cout) columns
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -162,80 +228,72 @@ __global__ void __launch_bounds__(128) k_conv_tc(CnnConvArgs a) {
     }
     if (tid == 0) {
         mbar_init(s_bar, 1);
+        mbar_init(s_bar + 1, 1);
         *s_fail = 0;
     }
     // weights, already in [tap][chunk][cout][8] order: one 16-byte copy per thread step
     const int wbytes = 9 * nch * cout * 16;
     for (int i = tid; i < wbytes / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(s_w)[i] = reinterpret_cast<const uint4*>(a.wpack)[i];
+    // this CTA's tiles: blockIdx.x + k gridDim.x, k < nt
+    const int64_t nt = blockIdx.x < a.ntiles ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint32_t in_base = smem_u32(smem);
+    if (nt > 0) conv_stage(a, conv_tile(a, blockIdx.x), in_base, nch, tid);
+    if (nt > 1) conv_stage(a, conv_tile(a, blockIdx.x + gridDim.x), in_base + SMEM_IN, nch, tid);
+    cp_async_wait_all();  // tile 0's halo (tile 1's may still be in flight with it; both wait)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
     const uint32_t idesc = umma_idesc(CNN_TILE, cout);
-    const uint32_t in_base = smem_u32(s_in);
     const uint32_t w_base = smem_u32(s_w);
-    uint32_t phase = 0;
+    uint32_t phase = 0u;  // bit b: parity of accumulator b's next completion
+    int issued = 0;       // bit b: a committed MMA group on accumulator b not yet waited for
+    if (nt > 0 && tid == 0) {
+        conv_mma(in_base, w_base, tmem, idesc, nch, cout);
+        umma_commit(s_bar);
+    }
+    if (nt > 0) issued = 1;
 
-    for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        int im = 0;
-        while (im + 1 < a.nimg && a.img[im + 1].tile0 <= tile) ++im;
-        const CnnImage I = a.img[im];
-        const int64_t tloc = tile - I.tile0;
-        const int tpr = (I.W + CNN_TILE - 1) / CNN_TILE;  // tiles per row
-        const int y = (int)(tloc / tpr);
-        const int x0 = (int)(tloc % tpr) * CNN_TILE;
-        // stage the halo: planes [chunk][3][130] x 16 bytes, zero outside the image
-        const int nitem = nch * 3 * PLANE_COLS;
-        for (int i = tid; i < nitem; i += blockDim.x) {
-            int c = i / (3 * PLANE_COLS);
-            int rem = i - c * 3 * PLANE_COLS;
-            int r = rem / PLANE_COLS;
-            int col = rem - r * PLANE_COLS;
-            int yy = y - 1 + r, xx = x0 - 1 + col;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (yy >= 0 && yy < I.H && xx >= 0 && xx < I.W) {
-                const int64_t cell = I.off + (int64_t)yy * I.W + xx;
-                v = *reinterpret_cast<const uint4*>(a.x + cell * cin + c * 8);
-            }
-            *reinterpret_cast<uint4*>(s_in + c * PLANE_BYTES + (r * PLANE_COLS + col) * 16) = v;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            uint32_t acc = 0;
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap % 3;  // 0..2 = offset + 1
-                for (int kc = 0; kc < nch / 2; ++kc) {
-                    uint32_t aaddr = in_base + (2 * kc) * PLANE_BYTES + (dy * PLANE_COLS + dx) * 16;
-                    uint32_t baddr = w_base + (tap * nch + 2 * kc) * cout * 16;
-                    uint64_t ad = umma_desc(aaddr, PLANE_BYTES, 128);
-                    uint64_t bd = umma_desc(baddr, cout * 16, 128);
-                    umma_bf16(tmem, ad, bd, idesc, acc);
-                    acc = 1;
-                }
-            }
-            umma_commit(s_bar);
-        }
-        bool ok = mbar_wait_bounded(s_bar, phase);
-        phase ^= 1u;
-        if (!ok) {
+    for (int64_t k = 0; k < nt; ++k) {
+        const int b = (int)(k & 1);
+        // the MMAs of tile k
+        const bool ok = mbar_wait_bounded(s_bar + b, (phase >> b) & 1u);
+        if (ok) {
+            phase ^= 1u << b;
+            issued &= ~(1 << b);
+        } else {  // still in flight: the cleanup below waits for it again
             set_status(a.status, VIP_ERR_TIMEOUT);
             *s_fail = 1;
         }
-        tc_fence_after();
+        // tile k+1's halo (started two iterations ago, or in the prologue)
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
         __syncthreads();
+        tc_fence_after();
         if (*s_fail) break;
-        // epilogue: warp w reads TMEM lanes 32w..32w+31 = pixels x0 + 32w + lane
+        if (k + 1 < nt) {
+            if (tid == 0) {
+                conv_mma(in_base + (1 - b) * SMEM_IN, w_base, tmem + (uint32_t)((1 - b) * 32), idesc,
+                         nch, cout);
+                umma_commit(s_bar + (1 - b));
+            }
+            issued |= 1 << (1 - b);
+        }
+        // tile k+2's halo into the buffer that tile k has released
+        if (k + 2 < nt)
+            conv_stage(a, conv_tile(a, blockIdx.x + (k + 2) * gridDim.x), in_base + b * SMEM_IN, nch, tid);
+        // epilogue of tile k: warp w reads TMEM lanes 32w..32w+31 = pixels x0 + 32w + lane
+        const ConvTile t = conv_tile(a, blockIdx.x + k * gridDim.x);
         float v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * 32);
         if (cout == 32) tmem_ld_x32(taddr, v);
         else tmem_ld_x16(taddr, v);
-        const int x = x0 + warp * 32 + lane;
-        if (x < I.W) {
-            const int64_t cell = I.off + (int64_t)y * I.W + x;
+        const int x = t.x0 + warp * 32 + lane;
+        if (x < t.I.W) {
+            const int64_t cell = t.I.off + (int64_t)t.y * t.I.W + x;
             if (a.epi == EPI_F32_CH0) {
                 a.y32[cell] = v[0] + (a.bias ? a.bias[0] : 0.0f);
             } else {
@@ -258,11 +316,16 @@ __global__ void __launch_bounds__(128) k_conv_tc(CnnConvArgs a) {
                                         packed[4 * q + 3]);
             }
         }
+        // accumulator b is read out before the MMAs of tile k+2 overwrite it
         tc_fence_before();
         __syncthreads();
     }
-    // a failed wait may leave MMAs in flight: wait once more (bounded) before freeing TMEM
-    if (*s_fail && tid == 0) mbar_wait_bounded(s_bar, phase ^ 1u);
+    // after a failed wait MMAs may still be in flight: wait for every committed group
+    // once more (bounded) before freeing TMEM; no copy is left in flight either
+    cp_async_wait_all();
+    if (tid == 0)
+        for (int bb = 0; bb < 2; ++bb)
+            if (issued & (1 << bb)) mbar_wait_bounded(s_bar + bb, (phase >> bb) & 1u);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -286,7 +349,7 @@ cudaError_t cnn_conv_fwd(const CnnConvArgs& a, int nsm, cudaStream_t s, const ch
         *why = "unsupported channel counts";
         return cudaErrorInvalidValue;
     }
-    const int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)std::max(nsm, 1) * 4);
+    const int grid = (int)std::min<int64_t>(a.ntiles, (int64_t)std::max(nsm, 1) * CONV_CTAS_PER_SM);
     k_conv_tc<<<grid, 128, SMEM_CONV, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) *why = "kernel launch";
