@@ -213,8 +213,14 @@ vip_status vip_set_pressure(vip_ctx* ctx, int form);
 /* Inner tolerance of the MIXED form's refinement loop (not in the paper; the
  * solves of Eqs. 12-13 stop at the same FP64 residual whatever it is): each FP32
  * BiCGSTAB pass stops when its recursive residual has fallen to inner_rtol times
- * the FP64 residual it started from (or to rtol ||b|| / 2).  inner_rtol in
- * (0, 1); default 1e-4.  VIP_ERR_ARG otherwise. */
+ * the FP64 residual it started from (or to rtol ||b|| / 2).  `which` =
+ * VIP_OP_POISSON (the pressure-increment solve; default 1e-4) or VIP_OP_HELM_U (both
+ * Helmholtz solves; default 1e-6: near the identity, their FP32 inner solve reaches
+ * the FP64 tolerance in one pass).  inner_rtol in (0, 1).  VIP_ERR_ARG otherwise.
+ * May be called at any time. */
+vip_status vip_set_inner_tolerance(vip_ctx* ctx, int which, double inner_rtol);
+
+/* vip_set_inner_tolerance for both solves at once. */
 vip_status vip_set_refinement(vip_ctx* ctx, double inner_rtol);
 
 /* Build everything that depends only on the geometry and flow parameters:

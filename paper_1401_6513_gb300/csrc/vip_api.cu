@@ -49,17 +49,18 @@ __global__ void k_word_sum(const uint64_t* __restrict__ w, int64_t n, unsigned l
 }
 
 // Checkpoint layout: this header, then CKPT_ARRAYS arrays of R doubles each (padded
-// row space: u, v, p, phi, N_u^{n-1}, N_v^{n-1}, the two Dirichlet value arrays and
+// row space: u, v, p, phi, N_u^{n-1}, N_v^{n-1}, the two Dirichlet value arrays, the
+// last Helmholtz solutions u*, v* and u^{n-1}, v^{n-1} (the next Helmholtz guess), and
 // the warm start's phi^{n-1}), then the step counter (int64).
-constexpr int CKPT_ARRAYS = 9;
+constexpr int CKPT_ARRAYS = 13;
 struct CkptHeader {
-    uint64_t magic;      // "VIPCKPT2"
+    uint64_t magic;      // "VIPCKPT3"
     int64_t n_nodes, n_rows, n_geoms;
     int64_t host_steps;
     uint64_t checksum;   // k_word_sum of everything after the header
     uint64_t pad[2];
 };
-constexpr uint64_t CKPT_MAGIC = 0x3254504B43504956ull;
+constexpr uint64_t CKPT_MAGIC = 0x3354504B43504956ull;
 
 vip_status fail(vip_ctx* c, vip_status s, const char* msg) {
     if (c) c->err = msg;
@@ -92,7 +93,7 @@ vip_status do_step(vip_ctx* c, cudaStream_t s) {
     VIP_CUDA(cudaGetLastError());
     VIP_CUDA(cudaEventRecord(c->ev[1], s));
     vip_status st = krylov_solve(c, c->plan_helm, c->T.helm, c->hrhs, c->hsol, c->precision, c->rtol,
-                                 c->max_iters, c->inner_rtol);
+                                 c->max_iters, c->helm_inner_rtol);
     if (st != VIP_OK) return st;
     VIP_CUDA(cudaEventRecord(c->ev[2], s));
     launch_div(c, s);
@@ -369,15 +370,24 @@ vip_status vip_set_pressure(vip_ctx* c, int form) {
     return VIP_OK;
 }
 
-vip_status vip_set_refinement(vip_ctx* c, double inner_rtol) {
+vip_status vip_set_inner_tolerance(vip_ctx* c, int which, double inner_rtol) {
     if (!c) return VIP_ERR_ARG;
+    if (which != VIP_OP_POISSON && which != VIP_OP_HELM_U)
+        return fail(c, VIP_ERR_ARG, "vip_set_inner_tolerance: which must be VIP_OP_POISSON or VIP_OP_HELM_U");
     if (!(inner_rtol > 0.0) || !(inner_rtol < 1.0)) return fail(c, VIP_ERR_ARG, "inner_rtol must be in (0, 1)");
-    if (inner_rtol != c->inner_rtol && c->graph) {  // the step graph holds the launch arguments
+    double& slot = which == VIP_OP_POISSON ? c->inner_rtol : c->helm_inner_rtol;
+    if (inner_rtol != slot && c->graph) {  // the step graph holds the launch arguments
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
     }
-    c->inner_rtol = inner_rtol;
+    slot = inner_rtol;
     return VIP_OK;
+}
+
+vip_status vip_set_refinement(vip_ctx* c, double inner_rtol) {
+    vip_status s = vip_set_inner_tolerance(c, VIP_OP_POISSON, inner_rtol);
+    if (s != VIP_OK) return s;
+    return vip_set_inner_tolerance(c, VIP_OP_HELM_U, inner_rtol);
 }
 
 vip_status vip_build(vip_ctx* c) {
@@ -480,6 +490,8 @@ vip_status vip_build(vip_ctx* c) {
     }
     VIP_CUDA(dalloc(c, &c->hsol, 2 * R));
     VIP_CUDA(dalloc(c, &c->hrhs, 2 * R));
+    VIP_CUDA(dalloc(c, &c->uv_prev, 2 * R));
+    VIP_CUDA(cudaMemsetAsync(c->uv_prev, 0, 2 * R * 8, st));
     VIP_CUDA(cudaMemsetAsync(c->hsol, 0, 2 * R * 8, st));
     VIP_CUDA(cudaMemsetAsync(c->hrhs, 0, 2 * R * 8, st));
     VIP_CUDA(cudaStreamSynchronize(st));
@@ -614,6 +626,7 @@ vip_status vip_checkpoint(vip_ctx* c, int save, void* buf) {
     VIP_CUDA(cudaSetDevice(c->device));
     cudaStream_t st = c->stream;
     double* arrays[CKPT_ARRAYS] = {c->u, c->v, c->p, c->phi, c->nu_prev, c->nv_prev, c->ubc, c->vbc,
+                                   c->hsol, c->hsol + c->R, c->uv_prev, c->uv_prev + c->R,
                                    cnn_history(c)};
     if (!arrays[CKPT_ARRAYS - 1]) return fail(c, VIP_ERR_ARG, "vip_checkpoint: no warm-start state");
     char* body = static_cast<char*>(buf) + sizeof(CkptHeader);

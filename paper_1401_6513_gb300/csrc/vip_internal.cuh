@@ -153,6 +153,7 @@ struct vip_ctx {
     int identity = VIP_IDENTITY_EXACT;
     int pressure = VIP_PRESSURE_INCREMENTAL;  // VIP_PRESSURE_* (vip_set_pressure)
     double inner_rtol = 1e-4;     // FP32 inner solve target relative to the FP64 residual
+    double helm_inner_rtol = 1e-6;   // the same for the Helmholtz solves (vip_set_inner_tolerance)
     bool built = false;
     bool use_graph = true;
     int64_t N = 0;                // nodes
@@ -172,6 +173,7 @@ struct vip_ctx {
     vip::Tables T;
     // state [R] (FP64)
     double *u = nullptr, *v = nullptr, *p = nullptr, *phi = nullptr;
+    double* uv_prev = nullptr;     // [2R] u^{n-1}, v^{n-1}: the Helmholtz guess u^n + (u*^n - u^{n-1})
     double *ubc = nullptr, *vbc = nullptr;
     double *nu_prev = nullptr, *nv_prev = nullptr;
     double *hsol = nullptr, *hrhs = nullptr;   // Helmholtz [2R]

@@ -73,12 +73,20 @@ __global__ void k_conv_rhs(StepArgs a, const double* __restrict__ u, const doubl
                            const double* __restrict__ p, const double* __restrict__ ubc,
                            const double* __restrict__ vbc, double* __restrict__ nu_prev,
                            double* __restrict__ nv_prev, double* __restrict__ hsol,
-                           double* __restrict__ hrhs) {
+                           double* __restrict__ hrhs, const double* __restrict__ uv_prev) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t R = a.R;
     if (r >= R) return;
-    hsol[r] = u[r];          // initial guess of the Helmholtz solve: u^n, v^n
-    hsol[R + r] = v[r];
+    // initial guess of the Helmholtz solve: u^n + (u*^n - u^{n-1}) once a step has been
+    // taken (hsol still holds the last solve's u*^n: the increment of the intermediate
+    // velocity one step later, an O(dt^2) guess), else u^n
+    if (*a.step > 0) {
+        hsol[r] = u[r] + (hsol[r] - uv_prev[r]);
+        hsol[R + r] = v[r] + (hsol[R + r] - uv_prev[R + r]);
+    } else {
+        hsol[r] = u[r];
+        hsol[R + r] = v[r];
+    }
     double ru = 0.0, rv = 0.0;
     if (a.row_type[r] == ROW_NODE) {
         uint8_t k = a.kind[r];
@@ -126,7 +134,7 @@ __global__ void k_div(StepArgs a, const double* __restrict__ hsol, double* __res
 
 __global__ void k_project(StepArgs a, const double* __restrict__ hsol, const double* __restrict__ phi,
                           double* __restrict__ u, double* __restrict__ v, double* __restrict__ p,
-                          int64_t* step) {
+                          int64_t* step, double* __restrict__ uv_prev) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t R = a.R;
     if (r == 0) atomicAdd((unsigned long long*)step, 1ull);
@@ -134,6 +142,8 @@ __global__ void k_project(StepArgs a, const double* __restrict__ hsol, const dou
     if (a.row_type[r] != ROW_NODE) return;
     const GeomDev& G = a.g[a.row_geom[r]];
     double us = hsol[r], vs = hsol[R + r];
+    uv_prev[r] = u[r];       // u^n, v^n: the next step's u^{n-1}, v^{n-1}
+    uv_prev[R + r] = v[r];
     if (a.kind[r] == VIP_NODE_INTERIOR) {
         us -= G.dt * gather(a.gx, r, phi);
         vs -= G.dt * gather(a.gy, r, phi);
@@ -180,14 +190,14 @@ static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / 
 
 void launch_conv_rhs(vip_ctx* c, cudaStream_t s) {
     k_conv_rhs<<<nblk(c->R, 256), 256, 0, s>>>(step_args(c), c->u, c->v, c->p, c->ubc, c->vbc,
-                                               c->nu_prev, c->nv_prev, c->hsol, c->hrhs);
+                                               c->nu_prev, c->nv_prev, c->hsol, c->hrhs, c->uv_prev);
 }
 void launch_div(vip_ctx* c, cudaStream_t s) {
     k_div<<<nblk(c->R, 256), 256, 0, s>>>(step_args(c), c->hsol, c->prhs);
 }
 void launch_project(vip_ctx* c, cudaStream_t s) {
     k_project<<<nblk(c->R, 256), 256, 0, s>>>(step_args(c), c->hsol, c->phi, c->u, c->v, c->p,
-                                              c->d_step);
+                                              c->d_step, c->uv_prev);
 }
 void launch_spmv(const Sell& A, const double* x, double* y, cudaStream_t s) {
     k_spmv<<<nblk(A.nrows, 256), 256, 0, s>>>(A, x, y);

@@ -39,7 +39,7 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout",
            "vip_multigrid_info", "vip_set_mg_shift", "vip_set_refinement", "vip_checkpoint_size",
            "vip_checkpoint", "vip_ws_adam", "vip_ws_extrapolation", "vip_ws_set_loss",
-           "vip_set_probes", "vip_set_pressure"]
+           "vip_set_probes", "vip_set_pressure", "vip_set_inner_tolerance"]
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -129,6 +129,7 @@ def lib(path: str | Path | None = None):
         "vip_set_mg_shift": ([vp, i32, i32, i32], C.c_int),
         "vip_set_probes": ([vp, i32, C.c_int], C.c_int),
         "vip_set_pressure": ([vp, C.c_int], C.c_int),
+        "vip_set_inner_tolerance": ([vp, C.c_int, C.c_double], C.c_int),
         "vip_get_geometry_iters": ([vp, vp], C.c_int),
         "vip_operator_layout": ([vp, C.c_int, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64),
                                  C.POINTER(i64)], C.c_int),
@@ -263,6 +264,12 @@ class Context:
         (-1: every geometry); before vip_build."""
         self._check(self.L.vip_set_probes(self.h, int(geom), int(mode)))
         self.__dict__.setdefault("_probe_calls", []).append((int(geom), int(mode)))
+
+    def vip_set_inner_tolerance(self, which, inner_rtol):
+        """Inner tolerance of the MIXED form's refinement for the solve `which`
+        ("POISSON" or "HELM_U", the latter for both Helmholtz systems)."""
+        self._check(self.L.vip_set_inner_tolerance(self.h, OP[which] if isinstance(which, str) else int(which),
+                                                   float(inner_rtol)))
 
     def vip_set_pressure(self, form):
         """Pressure form VIP_PRESSURE_INCREMENTAL / _KIM_MOIN / _INCREMENTAL_INTERIOR."""
