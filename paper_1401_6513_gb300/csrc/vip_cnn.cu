@@ -22,7 +22,6 @@
 
 namespace vip {
 
-constexpr int WG_THREADS = 256;
 
 // parameter offsets of layer l: weights [3][3][cin][cout_real] then bias [cout_real]
 struct ParamLayout {
@@ -317,66 +316,6 @@ __global__ void k_rloss2(int64_t n, const CnnImage* __restrict__ img, int nimg, 
     for (int k = 1; k < CNN_COUT; ++k) o[k] = __float2bfloat16(0.0f);
 }
 
-// Weight and bias gradients of one layer:
-//   dW[tap][ci][co] = sum_p x[p + off(tap)][ci] gy[p][co],  db[co] = sum_p gy[p][co].
-// Each block reduces its tiles into FP32 partials; k_wgrad_sum adds the partials.
-__global__ void __launch_bounds__(WG_THREADS) k_wgrad(const __nv_bfloat16* __restrict__ x,
-                                                      const __nv_bfloat16* __restrict__ gy,
-                                                      const CnnImage* __restrict__ img, int nimg,
-                                                      int64_t ntiles, int cin, int cout,
-                                                      float* __restrict__ part) {
-    __shared__ __nv_bfloat16 sx[3][CNN_TILE + 2][CNN_CH];
-    __shared__ __nv_bfloat16 sg[CNN_TILE][CNN_CH];
-    const int nent = 9 * cin * cout;
-    float acc[36];
-    float bacc = 0.0f;
-    for (int i = 0; i < 36; ++i) acc[i] = 0.0f;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        int im = 0;
-        while (im + 1 < nimg && img[im + 1].tile0 <= tile) ++im;
-        const CnnImage I = img[im];
-        const int64_t tl = tile - I.tile0;
-        const int tpr = (I.W + CNN_TILE - 1) / CNN_TILE;
-        const int y = (int)(tl / tpr), x0 = (int)(tl % tpr) * CNN_TILE;
-        __syncthreads();
-        for (int i = threadIdx.x; i < 3 * (CNN_TILE + 2) * cin; i += blockDim.x) {
-            int r = i / ((CNN_TILE + 2) * cin);
-            int rem = i - r * (CNN_TILE + 2) * cin;
-            int col = rem / cin, ci = rem % cin;
-            int yy = y - 1 + r, xx = x0 - 1 + col;
-            __nv_bfloat16 v = __float2bfloat16(0.0f);
-            if (yy >= 0 && yy < I.H && xx >= 0 && xx < I.W) v = x[(I.off + (int64_t)yy * I.W + xx) * cin + ci];
-            sx[r][col][ci] = v;
-        }
-        for (int i = threadIdx.x; i < CNN_TILE * cout; i += blockDim.x) {
-            int p = i / cout, co = i % cout;
-            int xx = x0 + p;
-            sg[p][co] = (xx < I.W) ? gy[(I.off + (int64_t)y * I.W + xx) * cout + co] : __float2bfloat16(0.0f);
-        }
-        __syncthreads();
-        for (int j = 0; j < 36; ++j) {
-            int e = threadIdx.x + j * WG_THREADS;
-            if (e >= nent) break;
-            int tap = e / (cin * cout);
-            int rem = e - tap * cin * cout;
-            int ci = rem / cout, co = rem % cout;
-            int dy = tap / 3, dx = tap % 3;
-            float s = 0.0f;
-            for (int p = 0; p < CNN_TILE; ++p)
-                s += __bfloat162float(sx[dy][p + dx][ci]) * __bfloat162float(sg[p][co]);
-            acc[j] += s;
-        }
-        if ((int)threadIdx.x < cout)
-            for (int p = 0; p < CNN_TILE; ++p) bacc += __bfloat162float(sg[p][threadIdx.x]);
-    }
-    float* dst = part + (int64_t)blockIdx.x * (nent + cout);
-    for (int j = 0; j < 36; ++j) {
-        int e = threadIdx.x + j * WG_THREADS;
-        if (e < nent) dst[e] = acc[j];
-    }
-    if ((int)threadIdx.x < cout) dst[nent + threadIdx.x] = bacc;
-}
-
 // sum block partials in block order into the gradient slots of the layer
 __global__ void k_wgrad_sum(const float* __restrict__ part, int nblocks, int cin, int cout, int creal,
                             float* __restrict__ gw, float* __restrict__ gb) {
@@ -526,7 +465,21 @@ vip_status backward(vip_ctx* c, Cnn& N, const CnnImage* img, int nimg, int64_t n
         const __nv_bfloat16* xin = (l == 0) ? in : N.act[l];
         int cin = N.L.cin[l], cout = N.L.cout[l];
         int nb = (int)std::min<int64_t>(ntiles, N.wg_blocks);
-        k_wgrad<<<nb, WG_THREADS, 0, s>>>(xin, gy, img, nimg, ntiles, cin, cout, N.wg_part);
+        {
+            CnnWgradArgs wa;
+            wa.x = xin;
+            wa.gy = gy;
+            wa.img = img;
+            wa.nimg = nimg;
+            wa.ntiles = ntiles;
+            wa.cin = cin;
+            wa.cout = cout;
+            wa.part = N.wg_part;
+            wa.status = c->d_status;
+            const char* why = "";
+            cudaError_t e = cnn_wgrad_tc(wa, nb, s, &why);
+            if (e != cudaSuccess) return fail(c, VIP_ERR_CUDA, why);
+        }
         k_wgrad_sum<<<64, 256, 0, s>>>(N.wg_part, nb, cin, cout, N.L.creal[l], N.grads + N.L.w[l],
                                        N.grads + N.L.b[l]);
         VIP_CUDA(cudaGetLastError());

@@ -47,7 +47,22 @@ struct CnnConvArgs {
     int32_t* status;
 };
 
+// Weight and bias gradients of one layer on the tensor cores (k_wgrad_tc): each block
+// accumulates its tiles into one FP32 partial of 9 cin cout + cout entries at
+// part + block (9 cin cout + cout), entry (tap cin + ci) cout + co, then the biases.
+struct CnnWgradArgs {
+    const __nv_bfloat16* x;      // [cells][cin] the layer's input
+    const __nv_bfloat16* gy;     // [cells][cout] the gradient wrt its output
+    const CnnImage* img;
+    int nimg;
+    int64_t ntiles;
+    int cin, cout;
+    float* part;
+    int32_t* status;
+};
+
 cudaError_t cnn_conv_init();
+cudaError_t cnn_wgrad_tc(const CnnWgradArgs& a, int nblocks, cudaStream_t s, const char** why);
 cudaError_t cnn_conv_fwd(const CnnConvArgs& a, int nsm, cudaStream_t s, const char** why);
 
 }  // namespace vip

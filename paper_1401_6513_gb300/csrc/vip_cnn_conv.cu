@@ -163,16 +163,19 @@ struct ConvTile {
     CnnImage I;
     int y, x0;
 };
-__device__ __forceinline__ ConvTile conv_tile(const CnnConvArgs& a, int64_t tile) {
+__device__ __forceinline__ ConvTile conv_tile_of(const CnnImage* img, int nimg, int64_t tile) {
     int im = 0;
-    while (im + 1 < a.nimg && a.img[im + 1].tile0 <= tile) ++im;
+    while (im + 1 < nimg && img[im + 1].tile0 <= tile) ++im;
     ConvTile t;
-    t.I = a.img[im];
+    t.I = img[im];
     const int64_t tloc = tile - t.I.tile0;
     const int tpr = (t.I.W + CNN_TILE - 1) / CNN_TILE;  // tiles per row
     t.y = (int)(tloc / tpr);
     t.x0 = (int)(tloc % tpr) * CNN_TILE;
     return t;
+}
+__device__ __forceinline__ ConvTile conv_tile(const CnnConvArgs& a, int64_t tile) {
+    return conv_tile_of(a.img, a.nimg, tile);
 }
 
 // Start the copies of a tile's halo into the planes at buf: [chunk][3][130] x 16
@@ -333,8 +336,166 @@ __global__ void __launch_bounds__(128) k_conv_tc(CnnConvArgs a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncol));
 }
 
+// Weight gradients dW[tap][ci][co] = sum_p x[p + off(tap)][ci] gy[p][co] as MMAs on the
+// tensor cores, K = pixels.  The halo is staged as for the convolution, channel-chunk
+// planar, here with four lattice rows: [row][chunk][col] x 16 bytes.  Read with the
+// pixel as K, an 8-pixel x 8-channel block (128 contiguous bytes) is a core matrix of
+// an MN-major operand, so A (M = 4 rows x 32 channels, the fourth row's products
+// discarded) and B (N = cout channels of gy, staged [chunk][pixel] x 16 bytes) need no
+// transpose, and the three column offsets of the taps are start addresses 16 bytes
+// apart.  Each block accumulates all its tiles in TMEM (three 32-column accumulators,
+// one per column offset) and writes one FP32 partial; the bias gradients are summed
+// on the side in pixel order.
+constexpr int WG_ROWS = 4;
+constexpr int WG_PLANE = PLANE_COLS * 16;                     // 2080: one row of one chunk
+constexpr int WG_SMEM_X = WG_ROWS * MAX_CHUNKS * WG_PLANE;    // 33280
+constexpr int WG_SMEM_G = MAX_CHUNKS * CNN_TILE * 16;         // 8192
+constexpr int SMEM_WGRAD = WG_SMEM_X + WG_SMEM_G + 64;
+// MN-major core matrices, no swizzle: the descriptor's leading-dimension offset is
+// the byte distance between core matrices adjacent along K (8 more pixels: 128 bytes
+// in both staged layouts), the stride-dimension offset the distance along M/N (8 more
+// channels: one plane row of the halo, one chunk plane of gy).  (Checked against the
+// FP64 reference of the gradients; the other assignment gives wrong sums.)
+constexpr uint32_t WG_K_STRIDE = 128;
+
+__host__ __device__ constexpr uint32_t umma_idesc_mn(int M, int N) {
+    return umma_idesc(M, N) | (1u << 15) | (1u << 16);  // A and B MN-major
+}
+
+__global__ void __launch_bounds__(128) k_wgrad_tc(CnnWgradArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* s_x = smem;
+    uint8_t* s_g = smem + WG_SMEM_X;
+    uint64_t* s_bar = reinterpret_cast<uint64_t*>(smem + WG_SMEM_X + WG_SMEM_G);
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + WG_SMEM_X + WG_SMEM_G + 8);
+    int* s_fail = reinterpret_cast<int*>(smem + WG_SMEM_X + WG_SMEM_G + 12);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int cin = a.cin, cout = a.cout;
+    const int nch = cin / 8, nchg = cout / 8;
+    const int ncol = 128;  // three accumulators of 32 columns
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(s_tmem)), "r"(ncol));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(s_bar, 1);
+        *s_fail = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+    const uint32_t idesc = umma_idesc_mn(128, cout);
+    const uint32_t xb = smem_u32(s_x), gb = smem_u32(s_g);
+    const uint32_t lbo = WG_K_STRIDE, sbo_a = WG_PLANE, sbo_b = CNN_TILE * 16;
+    uint32_t phase = 0u;
+    bool pending = false;
+    float bacc = 0.0f;
+    const int64_t nt = blockIdx.x < a.ntiles ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    for (int64_t k = 0; k < nt; ++k) {
+        const ConvTile t = conv_tile_of(a.img, a.nimg, blockIdx.x + k * gridDim.x);
+        // rows y-1 .. y+2 of the input, columns x0-1 .. x0+128, zero outside the image
+        const int nx_items = WG_ROWS * nch * PLANE_COLS;
+        for (int i = tid; i < nx_items; i += blockDim.x) {
+            const int r = i / (nch * PLANE_COLS);
+            const int rem = i - r * nch * PLANE_COLS;
+            const int c = rem / PLANE_COLS;
+            const int col = rem - c * PLANE_COLS;
+            const int yy = t.y - 1 + r, xx = t.x0 - 1 + col;
+            const bool in = yy >= 0 && yy < t.I.H && xx >= 0 && xx < t.I.W;
+            const __nv_bfloat16* src = a.x;
+            if (in) src = a.x + (t.I.off + (int64_t)yy * t.I.W + xx) * cin + c * 8;
+            cp_async16(xb + (r * MAX_CHUNKS + c) * WG_PLANE + col * 16, src, in ? 16u : 0u);
+        }
+        // gy of the tile's 128 pixels, zero beyond the row
+        for (int i = tid; i < nchg * CNN_TILE; i += blockDim.x) {
+            const int c = i / CNN_TILE, p = i - c * CNN_TILE;
+            const int xx = t.x0 + p;
+            const bool in = xx < t.I.W;
+            const __nv_bfloat16* src = a.gy;
+            if (in) src = a.gy + (t.I.off + (int64_t)t.y * t.I.W + xx) * cout + c * 8;
+            cp_async16(gb + (c * CNN_TILE + p) * 16, src, in ? 16u : 0u);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid < cout) {  // bias gradient, pixel order
+            const __nv_bfloat16* g = reinterpret_cast<const __nv_bfloat16*>(s_g) + (tid >> 3) * CNN_TILE * 8 + (tid & 7);
+            for (int p = 0; p < CNN_TILE; ++p) bacc += __bfloat162float(g[p * 8]);
+        }
+        if (tid == 0) {
+            for (int dx = 0; dx < 3; ++dx)
+                for (int kc = 0; kc < CNN_TILE / 16; ++kc) {
+                    const uint32_t aaddr = xb + dx * 16 + kc * 2 * WG_K_STRIDE;
+                    const uint32_t baddr = gb + kc * 2 * WG_K_STRIDE;
+                    umma_bf16(tmem + (uint32_t)(dx * 32), umma_desc(aaddr, lbo, sbo_a),
+                              umma_desc(baddr, lbo, sbo_b), idesc, (k > 0 || kc > 0) ? 1u : 0u);
+                }
+            umma_commit(s_bar);
+        }
+        pending = true;
+        const bool ok = mbar_wait_bounded(s_bar, phase);
+        if (ok) {
+            phase ^= 1u;
+            pending = false;
+        } else {
+            set_status(a.status, VIP_ERR_TIMEOUT);
+            *s_fail = 1;
+        }
+        tc_fence_before();
+        __syncthreads();  // the buffers are restaged by the next tile
+        tc_fence_after();
+        if (*s_fail) break;
+    }
+    const int nent = 9 * cin * cout;
+    float* dst = a.part + (int64_t)blockIdx.x * (nent + cout);
+    if (nt > 0 && !*s_fail) {
+        // warp w holds TMEM lanes 32w..32w+31 = row w of the halo (tap row dy = w), channel = lane
+        for (int dx = 0; dx < 3; ++dx) {
+            float v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dx * 32);
+            if (cout == 32) tmem_ld_x32(taddr, v);
+            else tmem_ld_x16(taddr, v);
+            if (warp < 3 && lane < cin) {
+                float* o = dst + ((int64_t)(warp * 3 + dx) * cin + lane) * cout;
+                for (int co = 0; co < cout; ++co) o[co] = v[co];
+            }
+        }
+    } else {
+        for (int e = tid; e < nent; e += blockDim.x) dst[e] = 0.0f;
+    }
+    if (tid < cout) dst[nent + tid] = bacc;
+    cp_async_wait_all();
+    if (tid == 0 && pending) mbar_wait_bounded(s_bar, phase);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncol));
+}
+
+cudaError_t cnn_wgrad_tc(const CnnWgradArgs& a, int nblocks, cudaStream_t s, const char** why) {
+    *why = "";
+    if (a.ntiles <= 0 || nblocks <= 0) return cudaSuccess;
+    if (a.cin % 16 || a.cin > CNN_CH || (a.cout != 16 && a.cout != 32)) {
+        *why = "unsupported channel counts";
+        return cudaErrorInvalidValue;
+    }
+    k_wgrad_tc<<<nblocks, 128, SMEM_WGRAD, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) *why = "weight-gradient launch";
+    return e;
+}
+
 cudaError_t cnn_conv_init() {
-    return cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CONV);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CONV);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_WGRAD);
 }
 
 cudaError_t cnn_conv_fwd(const CnnConvArgs& a, int nsm, cudaStream_t s, const char** why) {
