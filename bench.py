@@ -49,12 +49,13 @@ METRIC = "fractional-step node-updates/s at 1e-8 Poisson residual"
 UNIT = "node-updates/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 E2E_REPEATS = 3
+REF_STEPS = 6
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="bumpy_h64",
@@ -144,9 +145,13 @@ class Clocks:
         self.p = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200",
+                                       "--format=csv,noheader,nounits", "-lms", "50",
                                        "-i", str(gpu_id)],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            # the first sample comes after nvidia-smi's start-up; wait for it (it is taken
+            # before the timed region and not counted), so that the samples kept cover the
+            # timed steps
+            self.p.stdout.readline()
         except (OSError, FileNotFoundError):
             self.p = None
 
@@ -240,10 +245,13 @@ def run_reference(args, rank, ws):
     if rank != 0:
         return
     os.environ.setdefault("OMP_NUM_THREADS", "1")
-    ref = time_oracle(args.workload, max(1, args.steps), args.warmup)
+    # the oracle takes ~5 s per step on its sample: at most REF_STEPS timed steps after
+    # at most one warm-up step, so that the run ends within a minute or so
+    steps, warmup = max(1, min(args.steps, REF_STEPS)), min(args.warmup, 1)
+    ref = time_oracle(args.workload, steps, warmup)
     _, cfg = make_workload(args.workload)
     line = {"impl": "reference", "metric": METRIC, "value": ref["value"], "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": args.gpus, "steps": steps, "warmup": warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": ref["value"], "unit": UNIT, "cores": ref["cores"],
