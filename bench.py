@@ -36,6 +36,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import queue
 import statistics
 import subprocess
 import sys
@@ -221,8 +222,9 @@ def max_over_ranks(x, ws):
     return float(t.item())
 
 
-def time_oracle(name, steps, warmup=0):
-    """Time the CPU oracle, as it stands, on the bounded sample (node-updates/s)."""
+def time_oracle(name, steps, warmup=0, keep_state=False):
+    """Time the CPU oracle, as it stands, on the bounded sample (node-updates/s); with
+    keep_state the final (u, v, p, phi) come back under "_state" (not for the line)."""
     from oracle import vip_oracle as vo
     ns, desc = cpu_sample(name)
     t0 = time.perf_counter()
@@ -235,10 +237,56 @@ def time_oracle(name, steps, warmup=0):
         fs.step()
     sec = time.perf_counter() - t0
     iters = [s["it_p"] for s in fs.stats[warmup:]]
-    return {"value": ns.n * steps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} step(s) after {warmup} warm-up step(s) from the impulsive start, "
-                      f"{ns.n} nodes ({desc}); FP64 NumPy/SciPy, single thread; setup "
-                      f"{setup:.1f}s not timed; Poisson iterations {iters}"}
+    out = {"_state": (fs.u, fs.v, fs.p, fs.phi)} if keep_state else {}
+    return out | {"value": ns.n * steps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+                  "sample": f"{steps} step(s) after {warmup} warm-up step(s) from the impulsive "
+                            f"start, {ns.n} nodes ({desc}); FP64 NumPy/SciPy, single thread; setup "
+                            f"{setup:.1f}s not timed; Poisson iterations {iters}"}
+
+
+def _oracle_worker(name, steps, state, barrier, q):
+    """One oracle process of the all-cores CPU leg: the one-core leg's sample, continued
+    from that leg's final state; the timed steps of all processes start together."""
+    from oracle import vip_oracle as vo
+    ns, _ = cpu_sample(name)
+    fs = vo.FractionalStep(vo.Operators(ns), rtol=1e-8)
+    fs.set_state(*state)
+    barrier.wait(timeout=600)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fs.step()
+    q.put((ns.n * steps, t0, time.perf_counter()))
+
+
+def time_oracle_all_cores(name, steps, procs, state):
+    """The host's aggregate oracle throughput: `procs` independent single-threaded
+    oracle processes (spawned, so none inherits a CUDA context), each on the bounded
+    sample from the same state (u, v, p, phi); node updates of all of them / the span
+    from the first timed step's start to the last one's end."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(name, steps, state, barrier, q)) for _ in range(procs)]
+    for p in ps:
+        p.start()
+    res, deadline = [], time.perf_counter() + 900
+    while len(res) < procs:
+        try:
+            res.append(q.get(timeout=5))
+        except queue.Empty:
+            if any(p.exitcode not in (None, 0) for p in ps) or time.perf_counter() > deadline:
+                for p in ps:  # these processes only
+                    if p.is_alive():
+                        p.terminate()
+                raise RuntimeError("an oracle process of the all-cores leg failed")
+    for p in ps:
+        p.join(timeout=60)
+    upd = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    return {"value": upd / span, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} independent single-threaded oracle processes, each {steps} step(s) "
+                      f"on the one-core leg's sample from the state where that leg ended; node "
+                      f"updates of all / the span of their timed steps"}
 
 
 def run_reference(args, rank, ws):
@@ -585,10 +633,19 @@ def main():
         batch = batch_lines(vip, dev, stream, args.batch_steps, prec)
     if rank != 0:
         return
-    cpu = None
+    cpu = cpu_all = None
     if ws == 1 and not args.no_cpu_baseline:
+        # one BLAS thread per oracle process (inherited by the spawned ones)
         os.environ.setdefault("OMP_NUM_THREADS", "1")
-        cpu = time_oracle(args.workload, 2, 1)
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        cpu = time_oracle(args.workload, 2, 1, keep_state=True)
+        state = cpu.pop("_state")
+        ncores = min(os.cpu_count() or 1, 16)
+        if ncores > 1:
+            try:
+                cpu_all = time_oracle_all_cores(args.workload, 2, ncores, state)
+            except RuntimeError as e:
+                cpu_all = {"unavailable": str(e)}
     cfg.update({"global_batch": len(nss), "parallelism": f"replicas x{ws}", "precision": form,
                 "precision_choice": ({"by": "measurement (vip.choose_precision, 2 steps each)",
                                       "trials": form_trials} if form_trials else "fixed by --precision"),
@@ -628,6 +685,8 @@ def main():
         line["batch_64_cavities"] = batch
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if cpu_all is not None:
+        line["cpu_baseline_all_cores"] = cpu_all
     print(json.dumps(line), flush=True)
 
 
