@@ -159,21 +159,68 @@ def _radial_body(spec):
     raise ValueError(f"unknown body {spec!r}")
 
 
+def _stepwise_lattice(h, xlim, ylim, refine):
+    """Lattice nodes of a stepwise adaptive distribution: spacing h inside the first
+    box of `refine` (x0, x1, y0, y1), 2h between the first and the second, ..., and
+    h 2^K outside the last of the K boxes, all lattices sharing the origin
+    (xlim[0], ylim[0]).  A node of level k lies in box k (the channel for k = K) and
+    not in box k-1 (closed), whose edge nodes belong to the finer level.  Returns the
+    finest-lattice indices (ii, jj) of the nodes, their level and the lattice size."""
+    K = len(refine)
+    nxl = int(round((xlim[1] - xlim[0]) / h)) + 1
+    nyl = int(round((ylim[1] - ylim[0]) / h)) + 1
+    boxes = []
+    for k, (x0, x1, y0, y1) in enumerate(refine):
+        step = 2 ** (k + 1)   # the box edges lie on the lattice outside them
+        e = [(x0 - xlim[0]) / h, (x1 - xlim[0]) / h, (y0 - ylim[0]) / h, (y1 - ylim[0]) / h]
+        ei = [int(round(v)) for v in e]
+        if any(abs(a - b) > 1e-9 for a, b in zip(e, ei)) or any(v % step for v in ei):
+            raise ValueError(f"box {k} edges must lie on the lattice of spacing {step} h")
+        boxes.append(ei)
+    iis, jjs, levs = [], [], []
+    for k in range(K + 1):
+        st = 2 ** k
+        jj, ii = np.meshgrid(np.arange(0, nyl, st), np.arange(0, nxl, st), indexing="ij")
+        ii, jj = ii.ravel(), jj.ravel()
+        keep = np.ones(ii.size, bool)
+        if k < K:
+            a0, a1, b0, b1 = boxes[k]
+            keep &= (ii >= a0) & (ii <= a1) & (jj >= b0) & (jj <= b1)
+            # the box's edge carries only the coarser lattice's points
+            edge = (ii == a0) | (ii == a1) | (jj == b0) | (jj == b1)
+            keep &= ~(edge & ((ii % (2 * st) != 0) | (jj % (2 * st) != 0)))
+        if k > 0:
+            a0, a1, b0, b1 = boxes[k - 1]
+            keep &= ~((ii >= a0) & (ii <= a1) & (jj >= b0) & (jj <= b1))
+        iis.append(ii[keep])
+        jjs.append(jj[keep])
+        levs.append(np.full(int(keep.sum()), k, np.int64))
+    return np.concatenate(iis), np.concatenate(jjs), np.concatenate(levs), nxl, nyl
+
+
 def channel_body(h: float, body=("circle", 0.5), Re: float = 100.0, dt: float | None = None,
-                 xlim=(-8.0, 24.0), ylim=(-8.0, 8.0), name: str | None = None) -> NodeSet:
+                 xlim=(-8.0, 24.0), ylim=(-8.0, 8.0), name: str | None = None,
+                 refine=()) -> NodeSet:
     """Uniform inflow past a star-shaped body centred at the origin (Sec. 5.4-5.5).
 
     Background lattice of spacing h over the channel; lattice nodes inside the body
     or within CLEARANCE*h of its surface are removed; boundary nodes are placed on the
     surface at arc-length spacing close to h.  Inflow (x = xmin): u = 1, v = 0.
     Outflow (x = xmax): traction free.  Top/bottom: v = 0 with zero shear.
+
+    refine: the stepwise adaptive distribution of the paper's cylinder flows (Sec. 5.4,
+    used again in Sec. 5.5): nested boxes (x0, x1, y0, y1), innermost first, with
+    spacing h in the first and doubling outward (h 2^K outside the last); each box's
+    edges lie on the lattice outside it.  A node's h_local is its lattice's spacing,
+    except on a box's edge, which carries only the coarser lattice's points, with the
+    coarser spacing (reading: the paper gives no rule for the transition; with the
+    finer points and spacing on the edge the flow develops a growing mode at the box
+    corners, with the finer points at the coarser spacing a slower one).  The body
+    must lie in the first box.  The central VIP fluxes also need the cell Reynolds
+    number Re h 2^K of the coarsest region to stay moderate, as on a uniform lattice.
     """
     rfun, drfun, rmax = _radial_body(body)
-    nxl = int(round((xlim[1] - xlim[0]) / h)) + 1
-    nyl = int(round((ylim[1] - ylim[0]) / h)) + 1
-    jj, ii = np.meshgrid(np.arange(nyl), np.arange(nxl), indexing="ij")
-    ii = ii.ravel()
-    jj = jj.ravel()
+    ii, jj, lev, nxl, nyl = _stepwise_lattice(h, xlim, ylim, tuple(refine))
     x = xlim[0] + ii * h
     y = ylim[0] + jj * h
     # body surface, densely sampled for the clearance test
@@ -188,7 +235,7 @@ def channel_body(h: float, body=("circle", 0.5), Re: float = 100.0, dt: float | 
     inside = rad[idx] < rfun(th)
     d, _ = cKDTree(np.stack([cx, cy], 1)).query(np.stack([x[idx], y[idx]], 1))
     keep[idx[inside | (d < CLEARANCE * h)]] = False
-    x, y, ii, jj = x[keep], y[keep], ii[keep], jj[keep]
+    x, y, ii, jj, lev = x[keep], y[keep], ii[keep], jj[keep], lev[keep]
     N0 = x.size
     kind = np.zeros(N0, np.uint8)
     nx = np.zeros(N0)
@@ -232,9 +279,20 @@ def channel_body(h: float, body=("circle", 0.5), Re: float = 100.0, dt: float | 
     N = x.size
     if dt is None:
         dt = 0.25 * h
+    hl = h * 2.0 ** lev
+    for k, (x0, x1, y0, y1) in enumerate(refine):
+        # nodes of level k on the edge of box k: the spacing outside the box
+        xl, yl = x[:N0], y[:N0]
+        inb = (xl >= x0 - 1e-12) & (xl <= x1 + 1e-12) & (yl >= y0 - 1e-12) & (yl <= y1 + 1e-12)
+        onb = np.isclose(xl, x0) | np.isclose(xl, x1) | np.isclose(yl, y0) | np.isclose(yl, y1)
+        hl[(lev == k) & inb & onb] = h * 2.0 ** (k + 1)
+    hl = np.concatenate([hl, np.full(M, h)])
+    meta = {"h": h, "body": body, "surface_nodes": M, "lattice": (nxl, nyl)}
+    if refine:
+        meta["refine"] = tuple(tuple(b) for b in refine)
+        meta["level_nodes"] = [int((lev == k).sum()) for k in range(len(refine) + 1)]
     return _finish(name or f"channel_{body[0]}_h{int(round(1 / h))}", x, y, kind, nx, ny,
-                   np.full(N, h), 0.0, 0.0, u0, np.zeros(N), np.zeros(N), Re, dt, ylim[0],
-                   {"h": h, "body": body, "surface_nodes": M, "lattice": (nxl, nyl)})
+                   hl, 0.0, 0.0, u0, np.zeros(N), np.zeros(N), Re, dt, ylim[0], meta)
 
 
 def triangle_cavity(n_edge: int, Re: float = 100.0, dt: float | None = None,
