@@ -433,7 +433,7 @@ def test_kim_moin_pressure_is_time_centred():
     assert kim_moin_holds()
 
 
-def stokes_step_spectral_radius(fs, k=6):
+def stokes_step_spectral_radius(fs, k=6, tol=1e-10):
     """Largest |eigenvalue| of the fractional step linearised about rest: no
     convection, homogeneous boundary values, direct solves, the map (u, v, p) ->
     (u', v', p') of Eqs. (12)-(15) under fs's pressure reading (fs.pressure_update),
@@ -463,7 +463,7 @@ def stokes_step_spectral_radius(fs, k=6):
                                np.where(inner, vs - dt * (Gy @ phi), vs), p2])
 
     op = spl.LinearOperator((3 * N, 3 * N), matvec=step, dtype=np.float64)
-    vals = spl.eigs(op, k=k, which="LM", tol=1e-10, maxiter=20000, return_eigenvectors=False)
+    vals = spl.eigs(op, k=k, which="LM", tol=tol, maxiter=20000, return_eigenvectors=False)
     return float(np.max(np.abs(vals)))
 
 
@@ -501,6 +501,28 @@ def test_interior_pressure_reading_is_stable_on_the_wedge():
     assert stokes_step_spectral_radius(wedge_fs(vo.FractionalStep, "incremental")) > 1.0 + 5e-4
     assert interior_reading_holds()
     assert stokes_step_spectral_radius(wedge_fs(vo.FractionalStep, "kim_moin")) < 1.0
+
+
+def fine_circle_radius(n, pressure):
+    """Spectral radius of the step linearised about rest on the crop [-0.65, 0.65]^2
+    of a channel past the circle R = 0.55 (Re = 40, dt = 0.15 h, h = 1/n)."""
+    h = 1.0 / n
+    ns = w.channel_body(h, ("circle", 0.55), Re=40.0, dt=0.15 * h, xlim=(-0.65, 0.65), ylim=(-0.65, 0.65))
+    fs = vo.FractionalStep(vo.Operators(ns), pressure=pressure)
+    return stokes_step_spectral_radius(fs, k=2, tol=1e-6)
+
+
+def test_incremental_reading_has_a_wall_pressure_mode_on_the_fine_circle():
+    """The incremental reading's wall-pressure mode also appears on a circle, at one
+    lattice spacing and not at a coarser one: on a crop around the circle R = 0.55 the
+    step linearised about rest is neutral at h = 1/64 and has an eigenvalue 1 + 5e-3 at
+    h = 1/128 (1 + 8.8e-3 on the crop [-1, 1.5] x [-1, 1], whose eigenvector holds 56 %
+    of its pressure norm on the surface nodes, near theta = +-135 degrees, and whose
+    velocity is 5 % of its pressure; the h = 1/128 channel runs end non-finite in any
+    precision).  The Kim-Moin reading, whose step does not carry p, is stable there."""
+    assert fine_circle_radius(64, "incremental") <= 1.0 + 1e-5
+    assert fine_circle_radius(128, "incremental") >= 1.0 + 3e-3
+    assert fine_circle_radius(128, "kim_moin") < 1.0
 
 
 def mls_identity_quadratics_hold(ops, identity_op=None):
