@@ -1,0 +1,187 @@
+"""FP64 CPU oracle of the 3D extension of the VIP operator build.
+
+Park, Jo and Choe, "Virtual Interpolation Point Method for Viscous Flows in
+Complex Geometries" (arXiv:1401.6513).  The introduction and Sec. 3 state that the
+method extends to three dimensions with the quadratic basis of ten monomials; the
+paper shows no 3D flow.  This module states the 3D counterparts of the 2D oracle's
+neighbour search, MLS derivative weights (Sec. 3, Eq. fmlsrk:2) and operators
+(Eq. vip:1, Sec. 4.1), with the same readings: the cubic-spline weight, strict
+support |x_i - xbar| < rho with rho = support * h of the point's own node,
+"diffuse" derivatives of the local polynomial at its centre, VIPs at half the local
+spacing along each axis (six in 3D: east/west, north/south, top/bottom), VIP
+differences for the gradient, and at boundary nodes the zero-normal-derivative row
+q_i - (4/3) q(x_i - h n) + (1/3) q(x_i - 2h n) with MLS values at the two normal
+points.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests and the smoke check may import it; the
+product path never does.  It shares no code with the CUDA path (its inputs come
+from the seeded generators of ``workloads``).
+
+Pins (tests/test_oracle_3d.py, all CPU):
+  * neighbour lists equal a brute-force all-pairs test, periodic and not;
+  * the weights reproduce all ten quadratic monomials and their derivatives at
+    every node, VIP and normal point, and equal a weighted least-squares fit by
+    SVD (numpy.linalg.lstsq) on sampled points;
+  * L 1 = 0, L (x^2 + y^2 + z^2) = 6, Gx, Gy, Gz exact on quadratics at interior
+    nodes, the Neumann rows equal (2/3) h dq/dn on quadratics;
+  * L and G are second order on a smooth periodic field (observed order >= 1.8);
+  * planted mistakes (a dropped factorial, a swapped VIP pair) fail the pins.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+from scipy.spatial import cKDTree
+
+from .vip_oracle import KIND_INTERIOR, WEIGHTS, SingularStencil, min_image
+
+# The scaled quadratic basis in 3D, p = [1, xi, eta, zeta, xi^2, xi eta, xi zeta,
+# eta^2, eta zeta, zeta^2], and the derivative (a, b, c) each coefficient stands for.
+DERIVS3 = ((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0), (1, 0, 1),
+           (0, 2, 0), (0, 1, 1), (0, 0, 2))
+
+# The node derivative tables the 3D build exports.
+NODE_DERIVS3 = ((0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (0, 2, 0), (0, 0, 2))
+
+VIPS3 = ("e", "w", "n", "s", "t", "b")
+
+
+def basis3(xi, eta, zeta):
+    one = np.ones_like(xi)
+    return np.stack([one, xi, eta, zeta, xi * xi, xi * eta, xi * zeta, eta * eta,
+                     eta * zeta, zeta * zeta], axis=1)
+
+
+def neighbours3(q, rho, pts, L=(0.0, 0.0, 0.0)):
+    """Indices of the nodes strictly inside |x_i - q| < rho(q) for every query
+    point q (rows of q), ascending per point, as CSR (ptr, idx).  The test is
+    dx^2 + dy^2 + dz^2 < rho^2 with minimum-image differences in periodic
+    directions; a k-d tree only proposes candidates."""
+    q = np.asarray(q, np.float64)
+    rho = np.broadcast_to(np.asarray(rho, np.float64), (q.shape[0],))
+    if any(l > 0.0 for l in L):
+        if not all(l > 0.0 for l in L):
+            raise ValueError("periodic in every direction or in none")
+        tree = cKDTree(pts, boxsize=list(L))
+        qq = np.mod(q, np.asarray(L))
+        for k in range(3):
+            qq[qq[:, k] >= L[k], k] -= L[k]
+    else:
+        tree = cKDTree(pts)
+        qq = q
+    cand = tree.query_ball_point(qq, r=rho * (1.0 + 1e-9) + 1e-300)
+    ptr = np.zeros(q.shape[0] + 1, np.int64)
+    out = []
+    for p, c in enumerate(cand):
+        c = np.asarray(sorted(c), np.int64)
+        d = [min_image(pts[c, k] - q[p, k], L[k]) for k in range(3)]
+        keep = c[d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rho[p] * rho[p]]
+        out.append(keep)
+        ptr[p + 1] = ptr[p] + keep.size
+    idx = np.concatenate(out) if out else np.zeros(0, np.int64)
+    return ptr, idx
+
+
+def mls_weights3(q, rho, ptr, idx, pts, L=(0.0, 0.0, 0.0), weight="cubic_spline",
+                 derivs=NODE_DERIVS3, cond_max=1e13):
+    """Derivative weights of the 3D moving least-squares fit at each query point.
+
+    For a point xbar with neighbours x_i (Sec. 3, in three coordinates):
+    (xi, eta, zeta) = (x_i - xbar)/rho, p_i the ten monomials of basis3, Phi_i the
+    weight of |x_i - xbar|/rho, M = sum_i Phi_i p_i p_i^T; the fit's coefficient k
+    is (M^{-1} sum_i Phi_i p_i u_i)_k, and the (a,b,c) derivative of the local
+    polynomial at xbar is a! b! c! rho^-(a+b+c) times the coefficient of its
+    monomial.  Hence Psi^[a,b,c]_i = a! b! c! rho^-(a+b+c) Phi_i (M^{-1} p_i)_k
+    (M^{-1} p_i by a dense LU solve).  Returns {deriv: values aligned with idx};
+    SingularStencil when cond(M) > cond_max."""
+    phi = WEIGHTS[weight]
+    cnt = np.diff(ptr)
+    P = cnt.size
+    K = int(cnt.max()) if P else 0
+    pad = np.zeros((P, K), np.int64)
+    mask = np.arange(K)[None, :] < cnt[:, None]
+    pad[mask] = idx
+    q = np.asarray(q, np.float64)
+    rho = np.broadcast_to(np.asarray(rho, np.float64), (P,))
+    d = [min_image(pts[pad, k] - q[:, k, None], L[k]) / rho[:, None] for k in range(3)]
+    W = np.where(mask, phi(np.sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2])), 0.0)
+    Pm = basis3(*d) * mask[:, None, :]                      # [P, 10, K]
+    M = np.einsum("pak,pk,pbk->pab", Pm, W, Pm)
+    ev = np.linalg.eigvalsh(M)
+    cond = ev[:, -1] / np.maximum(ev[:, 0], 1e-300)
+    bad = np.nonzero(~(cond < cond_max))[0]
+    if bad.size:
+        raise SingularStencil(int(bad[0]), float(cond[bad[0]]))
+    Z = np.linalg.solve(M, Pm)
+    out = {}
+    for a in derivs:
+        k = DERIVS3.index(a)
+        fac = math.factorial(a[0]) * math.factorial(a[1]) * math.factorial(a[2]) / rho ** sum(a)
+        out[a] = (fac[:, None] * W * Z[:, k, :])[mask]
+    return out
+
+
+def _csr(rows, ptr, idx, val, N):
+    r = np.repeat(rows, np.diff(ptr))
+    return sp.csr_matrix((val, (r, idx)), shape=(N, N))
+
+
+class Operators3:
+    """Sparse FP64 operators of the 3D VIP build on a NodeSet3.
+
+    D[(a,b,c)]  node derivative approximants for NODE_DERIVS3 (N x N)
+    L           D^[2,0,0] + D^[0,2,0] + D^[0,0,2]
+    I[k]        interpolation Psi^[0,0,0](x_vip) to the six VIPs of interior nodes,
+                k in VIPS3 (rows of boundary nodes empty)
+    Gx, Gy, Gz  (u(x_e) - u(x_w))/|x_e - x_w|, (u(x_n) - u(x_s))/|x_n - x_s|,
+                (u(x_t) - u(x_b))/|x_t - x_b|
+    Nb          q_i - (4/3) q(x_i - h n_i) + (1/3) q(x_i - 2 h n_i) at boundary nodes
+    """
+
+    def __init__(self, ns, weight="cubic_spline", support=2.2):
+        pts = np.stack([ns.x, ns.y, ns.z], 1)
+        N = ns.n
+        L = (ns.Lx, ns.Ly, ns.Lz)
+        h = ns.h
+        rho = support * h
+        self.N, self.ns, self.pts, self.L3 = N, ns, pts, L
+        self.node_ptr, self.node_idx = neighbours3(pts, rho, pts, L)
+        wn = mls_weights3(pts, rho, self.node_ptr, self.node_idx, pts, L, weight)
+        every = np.arange(N)
+        self.D = {a: _csr(every, self.node_ptr, self.node_idx, wn[a], N) for a in NODE_DERIVS3}
+        self.L = ((self.D[(2, 0, 0)] + self.D[(0, 2, 0)]) + self.D[(0, 0, 2)]).tocsr()
+        ii = np.nonzero(ns.kind == KIND_INTERIOR)[0]
+        self.interior = ii
+        hh = 0.5 * h[ii]
+        self.vip = {}
+        for k, (ax, sgn) in zip(VIPS3, ((0, 1), (0, -1), (1, 1), (1, -1), (2, 1), (2, -1))):
+            v = pts[ii].copy()
+            v[:, ax] = v[:, ax] + hh if sgn > 0 else v[:, ax] - hh
+            self.vip[k] = v
+        self.vip_ptr, self.vip_idx, self.I = {}, {}, {}
+        for k, v in self.vip.items():
+            ptr, idx = neighbours3(v, rho[ii], pts, L)
+            w = mls_weights3(v, rho[ii], ptr, idx, pts, L, weight, derivs=((0, 0, 0),))[(0, 0, 0)]
+            self.vip_ptr[k], self.vip_idx[k] = ptr, idx
+            self.I[k] = _csr(ii, ptr, idx, w, N)
+        G = []
+        for ax, (p, m) in enumerate((("e", "w"), ("n", "s"), ("t", "b"))):
+            inv = np.zeros(N)
+            inv[ii] = 1.0 / np.abs(self.vip[p][:, ax] - self.vip[m][:, ax])
+            G.append((sp.diags(inv) @ (self.I[p] - self.I[m])).tocsr())
+        self.Gx, self.Gy, self.Gz = G
+        bb = np.nonzero(ns.kind != KIND_INTERIOR)[0]
+        self.boundary = bb
+        nrm = np.stack([ns.nx, ns.ny, ns.nz], 1)[bb]
+        self.probe = {s: pts[bb] - s * h[bb, None] * nrm for s in (1, 2)}
+        B = {}
+        for s, v in self.probe.items():
+            ptr, idx = neighbours3(v, rho[bb], pts, L)
+            w = mls_weights3(v, rho[bb], ptr, idx, pts, L, weight, derivs=((0, 0, 0),))[(0, 0, 0)]
+            B[s] = _csr(bb, ptr, idx, w, N)
+        self.B = B
+        sel = np.zeros(N)
+        sel[bb] = 1.0
+        self.Nb = (sp.diags(sel) - (4.0 / 3.0) * B[1] + (1.0 / 3.0) * B[2]).tocsr()

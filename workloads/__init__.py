@@ -16,3 +16,4 @@ from .geometry import (  # noqa: F401
     NodeSet, periodic_box, cavity, channel_body, triangle_cavity, wedge_cavity,
     triangle_batch, taylor_green, workload,
 )
+from .geometry3d import NodeSet3, box3d, sphere_in_box3d  # noqa: F401
