@@ -498,6 +498,89 @@ vip_status vip_bicgstab_static(int device, void* cuda_stream, int64_t n, const i
                                const int32_t* col, const double* val, const double* b, double* x,
                                double rtol, int32_t max_iters, int32_t* iters, double* relres);
 
+/* ---- three-dimensional operator build --------------------------------------
+ * The paper's introduction and Sec. 3 state that the method carries over to
+ * three dimensions with the quadratic basis of ten monomials
+ * [1, xi, eta, zeta, xi^2, xi eta, xi zeta, eta^2, eta zeta, zeta^2]; it shows no
+ * 3D flow.  These calls build the 3D counterparts of the 2D tables (neighbour
+ * search and MLS weights of Sec. 3, Eq. fmlsrk:2; the operators of Eq. vip:1 and
+ * Sec. 4.1) on the GPU, with the readings of the 2D build: strict support
+ * |x_i - xbar| < rho, rho = support * h of the point's own node; VIPs at half the
+ * node's spacing along each axis (six: east/west along x, north/south along y,
+ * top/bottom along z); at boundary nodes the zero-normal-derivative row
+ * q_i - (4/3) q(x_i - h n_i) + (1/3) q(x_i - 2 h n_i) with MLS values at the two
+ * normal points.  The 3D fractional step itself is not part of this library.
+ * A vip_3d handle has the conventions of vip_ctx (status returns, copied
+ * inputs, caller-owned outputs, host or device pointers, its own stream). */
+typedef struct vip_3d vip_3d; /* opaque, owned by the library */
+
+/* Tables of the 3D build, exported as CSR (rows = nodes, columns = nodes):
+ *   NBR               neighbour lists of the nodes, value = 1
+ *   D000 .. D002      node derivative approximants D^[a,b,c] for (0,0,0),
+ *                     (1,0,0), (0,1,0), (0,0,1), (2,0,0), (0,2,0), (0,0,2)
+ *   LAPLACE           D^[2,0,0] + D^[0,2,0] + D^[0,0,2]
+ *   VIP_E .. VIP_B    interpolation Psi^[0,0,0](x_vip) to the six VIPs of the
+ *                     interior nodes (empty rows for boundary nodes)
+ *   GX, GY, GZ        (q(x_e) - q(x_w)) / |x_e - x_w| and its y and z
+ *                     counterparts (interior rows)
+ *   NEUMANN           q_i - (4/3) q(x_i - h n_i) + (1/3) q(x_i - 2 h n_i)
+ *                     (boundary rows) */
+enum {
+    VIP3_OP_NBR = 0, VIP3_OP_D000 = 1, VIP3_OP_D100 = 2, VIP3_OP_D010 = 3, VIP3_OP_D001 = 4,
+    VIP3_OP_D200 = 5, VIP3_OP_D020 = 6, VIP3_OP_D002 = 7, VIP3_OP_LAPLACE = 8,
+    VIP3_OP_VIP_E = 9, VIP3_OP_VIP_W = 10, VIP3_OP_VIP_N = 11, VIP3_OP_VIP_S = 12,
+    VIP3_OP_VIP_T = 13, VIP3_OP_VIP_B = 14, VIP3_OP_GX = 15, VIP3_OP_GY = 16, VIP3_OP_GZ = 17,
+    VIP3_OP_NEUMANN = 18, VIP3_OP_COUNT = 19
+};
+
+/* Create a handle on `device` (work issued on cuda_stream, NULL = legacy default
+ * stream).  Errors: VIP_ERR_ARG, VIP_ERR_CUDA. */
+vip_status vip_3d_create(vip_3d** out, int device, void* cuda_stream);
+
+/* Node set: n nodes (1 <= n < 2^31 - 1) with coordinates x, y, z, kinds (the
+ * VIP_NODE_* codes; every non-interior kind gets a NEUMANN row), unit outward
+ * normals (nx, ny, nz; read at non-interior nodes only) and local spacing h > 0.
+ * Lx, Ly, Lz: periods, all three > 0 (periodic; coordinates in [0, L)) or all
+ * three 0.  Replaces an earlier node set and its tables.  Errors: VIP_ERR_ARG
+ * (sizes, non-finite or non-positive values, mixed periodicity, periodic
+ * coordinates outside [0, L), a non-interior node in a periodic set),
+ * VIP_ERR_CUDA, VIP_ERR_OOM. */
+vip_status vip_3d_set_nodes(vip_3d* b, int64_t n, const double* x, const double* y,
+                            const double* z, const uint8_t* kind, const double* nx,
+                            const double* ny, const double* nz, const double* h, double Lx,
+                            double Ly, double Lz);
+
+/* Weight function (VIP_W_*) and support ratio rho / h (> 1; default cubic
+ * spline, 2.2).  Errors: VIP_ERR_ARG. */
+vip_status vip_3d_set_mls(vip_3d* b, int weight, double support);
+
+/* Neighbour lists (at most 160 per point) and MLS weights of every node, VIP and
+ * normal point.  Synchronises.  Errors: VIP_ERR_ARG (no node set; a point with
+ * more than 160 neighbours), VIP_ERR_SINGULAR_STENCIL (a
+ * moment matrix failed its Cholesky test; vip_3d_last_error names the point),
+ * VIP_ERR_CUDA, VIP_ERR_OOM. */
+vip_status vip_3d_build(vip_3d* b);
+
+/* Row count (the node count) and entry count of table `which`.  Assembles the
+ * table on the device on first use.  Errors: VIP_ERR_ARG (not built, bad
+ * which), VIP_ERR_CUDA, VIP_ERR_OOM. */
+vip_status vip_3d_stencil_size(vip_3d* b, int which, int64_t* nrows, int64_t* nnz);
+
+/* Export table `which` as CSR: row_ptr[nrows+1], col[nnz] (ascending within a
+ * row), val[nnz]; host or device pointers.  Synchronises.  Errors as
+ * vip_3d_stencil_size. */
+vip_status vip_3d_get_stencil(vip_3d* b, int which, int64_t* row_ptr, int32_t* col, double* val);
+
+/* y = Op x in FP64 on the device for table `which` (x and y of the node count;
+ * host or device pointers).  Synchronises.  Errors as vip_3d_stencil_size. */
+vip_status vip_3d_apply(vip_3d* b, int which, const double* x, double* y);
+
+/* One-line diagnostic of the last error on this handle ("" if none). */
+const char* vip_3d_last_error(const vip_3d* b);
+
+/* Free the handle and its device memory.  NULL is allowed. */
+void vip_3d_destroy(vip_3d* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,7 +39,13 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout",
            "vip_multigrid_info", "vip_set_mg_shift", "vip_set_refinement", "vip_checkpoint_size",
            "vip_checkpoint", "vip_ws_adam", "vip_ws_extrapolation", "vip_ws_set_loss",
-           "vip_set_probes", "vip_set_pressure", "vip_set_inner_tolerance"]
+           "vip_set_probes", "vip_set_pressure", "vip_set_inner_tolerance",
+           "vip_3d_create", "vip_3d_destroy", "vip_3d_last_error", "vip_3d_set_nodes",
+           "vip_3d_set_mls", "vip_3d_build", "vip_3d_stencil_size", "vip_3d_get_stencil",
+           "vip_3d_apply"]
+OPS3 = ["NBR", "D000", "D100", "D010", "D001", "D200", "D020", "D002", "LAPLACE", "VIP_E", "VIP_W",
+        "VIP_N", "VIP_S", "VIP_T", "VIP_B", "GX", "GY", "GZ", "NEUMANN"]
+OP3 = {name: i for i, name in enumerate(OPS3)}
 VIP_TUNE_MAX = 16
 VIP_STATIC_MAX_ROWS = 131072
 PHASES = ["rhs", "helmholtz", "divergence", "poisson", "project"]
@@ -136,6 +142,15 @@ def lib(path: str | Path | None = None):
         "vip_multigrid_info": ([vp, C.POINTER(i32), C.POINTER(i64)], C.c_int),
         "vip_autotune": ([vp, C.POINTER(C.c_float), i32, C.POINTER(C.c_float), i32,
                           C.POINTER(TuneResult)], C.c_int),
+        "vip_3d_create": ([C.POINTER(vp), C.c_int, vp], C.c_int),
+        "vip_3d_destroy": ([vp], None),
+        "vip_3d_last_error": ([vp], C.c_char_p),
+        "vip_3d_set_nodes": ([vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, dbl, dbl, dbl], C.c_int),
+        "vip_3d_set_mls": ([vp, C.c_int, dbl], C.c_int),
+        "vip_3d_build": ([vp], C.c_int),
+        "vip_3d_stencil_size": ([vp, C.c_int, C.POINTER(i64), C.POINTER(i64)], C.c_int),
+        "vip_3d_get_stencil": ([vp, C.c_int, vp, vp, vp], C.c_int),
+        "vip_3d_apply": ([vp, C.c_int, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -163,6 +178,80 @@ def _f64(a):
     if hasattr(a, "data_ptr"):
         return a
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Build3D:
+    """Owns one vip_3d handle (the 3D operator build); methods call the C entry
+    points of the same name."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self.L = lib()
+        h = C.c_void_p()
+        st = self.L.vip_3d_create(C.byref(h), device, C.c_void_p(stream) if stream else None)
+        self.h = h
+        self._check(st)
+
+    def _check(self, st):
+        if st != VIP_OK:
+            msg = self.L.vip_3d_last_error(self.h) if self.h else b"no handle"
+            raise VipError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if self.h:
+            self.L.vip_3d_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vip_3d_set_nodes(self, x, y, z, kind, nx, ny, nz, h, Lx=0.0, Ly=0.0, Lz=0.0):
+        x, y, z, nx, ny, nz, h = map(_f64, (x, y, z, nx, ny, nz, h))
+        kind = kind if hasattr(kind, "data_ptr") else np.ascontiguousarray(kind, dtype=np.uint8)
+        n = x.numel() if hasattr(x, "numel") else x.size
+        self._check(self.L.vip_3d_set_nodes(self.h, n, _ptr(x), _ptr(y), _ptr(z), _ptr(kind),
+                                            _ptr(nx), _ptr(ny), _ptr(nz), _ptr(h), Lx, Ly, Lz))
+
+    def vip_3d_set_mls(self, weight=VIP_W_CUBIC_SPLINE, support=2.2):
+        self._check(self.L.vip_3d_set_mls(self.h, weight, support))
+
+    def vip_3d_build(self):
+        self._check(self.L.vip_3d_build(self.h))
+
+    def vip_3d_stencil_size(self, which):
+        w = OP3[which] if isinstance(which, str) else int(which)
+        nr, nz = C.c_int64(), C.c_int64()
+        self._check(self.L.vip_3d_stencil_size(self.h, w, C.byref(nr), C.byref(nz)))
+        return nr.value, nz.value
+
+    def vip_3d_get_stencil(self, which):
+        """Return (row_ptr, col, val) of a table as numpy arrays."""
+        w = OP3[which] if isinstance(which, str) else int(which)
+        nr, nz = self.vip_3d_stencil_size(w)
+        ptr = np.empty(nr + 1, np.int64)
+        col = np.empty(max(nz, 1), np.int32)
+        val = np.empty(max(nz, 1), np.float64)
+        self._check(self.L.vip_3d_get_stencil(self.h, w, _ptr(ptr), _ptr(col), _ptr(val)))
+        return ptr, col[:nz], val[:nz]
+
+    def vip_3d_apply(self, which, x, y=None):
+        w = OP3[which] if isinstance(which, str) else int(which)
+        x = _f64(x)
+        if y is None:
+            y = np.empty_like(x) if isinstance(x, np.ndarray) else None
+        self._check(self.L.vip_3d_apply(self.h, w, _ptr(x), _ptr(y)))
+        return y
+
+
+def build3d_for(ns, device=0, stream=None, weight=VIP_W_CUBIC_SPLINE, support=2.2) -> Build3D:
+    """Create a 3D build handle for a NodeSet3-like object and build it."""
+    b = Build3D(device, stream)
+    b.vip_3d_set_mls(weight, support)
+    b.vip_3d_set_nodes(ns.x, ns.y, ns.z, ns.kind, ns.nx, ns.ny, ns.nz, ns.h, ns.Lx, ns.Ly, ns.Lz)
+    b.vip_3d_build()
+    return b
 
 
 class Context:
