@@ -89,6 +89,11 @@ enum { VIP_IDENTITY_EXACT = 0, VIP_IDENTITY_MLS = 1 };
  * pressure term but Eq. 15 with p^n; these forms are readings of the pair):
  *   INCREMENTAL           r^n carries -G p^n, so phi is the pressure increment,
  *                         and p^{n+1} = p^n + phi - (dt/2Re) L phi at every node;
+ *                         the wall pressures are carried from step to step, and
+ *                         on some node sets the linearised step then has an
+ *                         eigenvalue slightly above 1 (the circle of radius 0.55
+ *                         at h = 1/128, Re 40, dt = 0.15 h: 1.0088, neutral at
+ *                         h = 1/64), so a long run there grows without bound;
  *   KIM_MOIN              r^n as printed (no pressure term), so phi is the whole
  *                         pseudo-pressure of Kim and Moin, and
  *                         p^{n+1} = phi - (dt/2Re) L phi (Eq. 15 without p^n); the
@@ -98,7 +103,9 @@ enum { VIP_IDENTITY_EXACT = 0, VIP_IDENTITY_MLS = 1 };
  *                         boundary node L is a one-sided MLS fit; on the 28.072
  *                         degree wedge of Sec. 5 the term there feeds a growing
  *                         wall-pressure mode (an eigenvalue of the linearised
- *                         step above 1), which this form does not have. */
+ *                         step above 1), which this form does not have (on the
+ *                         circle at h = 1/128 it has one too, 1.0024; KIM_MOIN,
+ *                         which carries no pressure, has none there). */
 enum { VIP_PRESSURE_INCREMENTAL = 0, VIP_PRESSURE_KIM_MOIN = 1, VIP_PRESSURE_INCREMENTAL_INTERIOR = 2 };
 
 /* Tables and operators that can be exported (vip_get_stencil) or applied
