@@ -516,7 +516,8 @@ vip_status vip_bicgstab_static(int device, void* cuda_stream, int64_t n, const i
  * node's spacing along each axis (six: east/west along x, north/south along y,
  * top/bottom along z); at boundary nodes the zero-normal-derivative row
  * q_i - (4/3) q(x_i - h n_i) + (1/3) q(x_i - 2 h n_i) with MLS values at the two
- * normal points.  The 3D fractional step itself is not part of this library.
+ * normal points.  The 3D fractional step (vip_3d_step below) runs on periodic
+ * node sets.
  * A vip_3d handle has the conventions of vip_ctx (status returns, copied
  * inputs, caller-owned outputs, host or device pointers, its own stream). */
 typedef struct vip_3d vip_3d; /* opaque, owned by the library */
@@ -581,6 +582,39 @@ vip_status vip_3d_get_stencil(vip_3d* b, int which, int64_t* row_ptr, int32_t* c
 /* y = Op x in FP64 on the device for table `which` (x and y of the node count;
  * host or device pointers).  Synchronises.  Errors as vip_3d_stencil_size. */
 vip_status vip_3d_apply(vip_3d* b, int which, const double* x, double* y);
+
+/* ---- the fractional step in 3D (Sec. 2, Eqs. 12-15), periodic node sets ----
+ * The step of the 2D library in three coordinates on a built periodic node set
+ * (every node interior): convection through the six VIPs of each node (Sec. 4.1
+ * item 1), Adams-Bashforth 2 (N^{-1} = N^0 on the first step), Crank-Nicolson
+ * viscous term with the exact identity, the incremental pressure reading (r^n
+ * carries -G p^n; p^{n+1} = p^n + phi - (dt/2Re) L phi), the MLS Laplacian in
+ * the Poisson equation.  The periodic Poisson system is singular: it is
+ * bordered by one unknown mu added to every row, node 0's own equation moved to
+ * an extra row and node 0's row replaced by (-6/h_0^2) phi_0 = 0.  Every solve
+ * is unpreconditioned FP64 BiCGSTAB to ||b - A x|| <= rtol ||b|| on the true
+ * residual, the Helmholtz solves starting from u^n, the Poisson solve from
+ * (phi^n, mu^n).  The 2D library's multigrid has no 3D counterpart, so the
+ * Poisson iterations grow with the node count.
+ *
+ * vip_3d_set_flow: Re > 0, dt > 0, rtol in (0, 1), max_iters >= 1 per solve.
+ * vip_3d_set_state: u, v, w, p of every node (host or device); phi, mu and the
+ *   Adams-Bashforth history are reset.
+ * vip_3d_step: nsteps steps; synchronous.  Errors: VIP_ERR_ARG (not built, no
+ *   flow or state, not periodic), VIP_ERR_NOT_CONVERGED, VIP_ERR_BREAKDOWN,
+ *   VIP_ERR_NONFINITE, VIP_ERR_CUDA, VIP_ERR_OOM.
+ * vip_3d_get_state: u, v, w, p, phi of every node into caller buffers (any may
+ *   be NULL).
+ * vip_3d_get_iters: steps taken since vip_3d_set_state, and of the last step the
+ *   Helmholtz iterations (three solves together), the Poisson iterations and
+ *   the Poisson solve's true relative residual (any pointer may be NULL). */
+vip_status vip_3d_set_flow(vip_3d* b, double Re, double dt, double rtol, int32_t max_iters);
+vip_status vip_3d_set_state(vip_3d* b, const double* u, const double* v, const double* w,
+                            const double* p);
+vip_status vip_3d_step(vip_3d* b, int32_t nsteps);
+vip_status vip_3d_get_state(vip_3d* b, double* u, double* v, double* w, double* p, double* phi);
+vip_status vip_3d_get_iters(vip_3d* b, int64_t* steps, int32_t* helm_iters, int32_t* poisson_iters,
+                            double* poisson_relres);
 
 /* One-line diagnostic of the last error on this handle ("" if none). */
 const char* vip_3d_last_error(const vip_3d* b);

@@ -185,3 +185,113 @@ class Operators3:
         sel = np.zeros(N)
         sel[bb] = 1.0
         self.Nb = (sp.diags(sel) - (4.0 / 3.0) * B[1] + (1.0 / 3.0) * B[2]).tocsr()
+
+
+# ---------------------------------------------------------------------------
+# The fractional step in three coordinates (Sec. 2, Eqs. 12-15), periodic sets
+# ---------------------------------------------------------------------------
+
+def convection3(ops: Operators3, u, v, w):
+    """Convection at every node of a periodic set via the six VIPs (Sec. 4.1 item 1
+    in three coordinates): the products of interpolated values, differenced across
+    each VIP pair and divided by the pair distance (the flux form of u . grad u)."""
+    I = ops.I
+    e = {k: (I[k] @ u, I[k] @ v, I[k] @ w) for k in VIPS3}
+    ii = ops.interior
+    inv = []
+    for ax, (p, m) in enumerate((("e", "w"), ("n", "s"), ("t", "b"))):
+        a = np.zeros(ops.N)
+        a[ii] = 1.0 / np.abs(ops.vip[p][:, ax] - ops.vip[m][:, ax])
+        inv.append(a)
+    out = []
+    for c in range(3):           # component c of the momentum flux
+        f = ((e["e"][0] * e["e"][c] - e["w"][0] * e["w"][c]) * inv[0]
+             + (e["n"][1] * e["n"][c] - e["s"][1] * e["s"][c]) * inv[1]
+             + (e["t"][2] * e["t"][c] - e["b"][2] * e["b"][c]) * inv[2])
+        out.append(f)
+    return out
+
+
+class FractionalStep3:
+    """The second-order fractional step of the 2D oracle in three coordinates, on
+    periodic node sets (every node interior): AB2 convection, Crank-Nicolson
+    viscous term, the incremental pressure reading (r^n carries -G p^n, phi the
+    increment, p^{n+1} = p^n + phi - (dt/2Re) L phi), exact identity, the MLS
+    Laplacian in the Poisson equation, unpreconditioned BiCGSTAB.  The periodic
+    Poisson system is singular; as in the 2D oracle it is bordered by one unknown
+    mu added to every row, node k0 = 0's own equation moved to the extra row and
+    its row replaced by (-6/h_k0^2) phi_k0 = 0 (in 3D the Laplacian's diagonal is
+    about -6/h^2)."""
+
+    def __init__(self, ops: Operators3, Re, dt, rtol=1e-8, maxit=200000):
+        if ops.boundary.size or not all(l > 0 for l in ops.L3):
+            raise ValueError("the 3D step takes periodic node sets (every node interior)")
+        from .vip_oracle import bicgstab
+        self._bicgstab = bicgstab
+        N = ops.N
+        self.ops, self.N = ops, N
+        self.Re, self.dt = float(Re), float(dt)
+        self.rtol, self.maxit = rtol, maxit
+        self.alpha = self.dt / (2.0 * self.Re)
+        Id = sp.identity(N, format="csr")
+        self.H = (Id - self.alpha * ops.L).tocsr()
+        self.Rm = (Id + self.alpha * ops.L).tocsr()
+        k0 = 0
+        self.pin = k0
+        pin_scale = -6.0 / ops.ns.h[k0] ** 2
+        Pb = sp.bmat([[ops.L, sp.csr_matrix(np.ones((N, 1)))],
+                      [sp.csr_matrix((1, N)), None]]).tolil()
+        rowk = Pb[k0].copy()
+        Pb[k0] = 0.0
+        Pb[k0, k0] = pin_scale
+        Pb[N] = rowk
+        self.P = Pb.tocsr()
+        self.u = np.zeros(N)
+        self.v = np.zeros(N)
+        self.w = np.zeros(N)
+        self.p = np.zeros(N)
+        self.phi = np.zeros(N)
+        self.mu = 0.0
+        self.N_prev = None
+        self.nstep = 0
+
+    def set_state(self, u, v, w, p):
+        self.u, self.v, self.w, self.p = (np.array(a, np.float64) for a in (u, v, w, p))
+        self.phi = np.zeros(self.N)
+        self.mu = 0.0
+        self.N_prev = None
+
+    def step(self):
+        ops, dt = self.ops, self.dt
+        vel = (self.u, self.v, self.w)
+        Nn = convection3(ops, *vel)
+        if self.N_prev is None:
+            self.N_prev = Nn
+        Nab = [1.5 * a - 0.5 * b for a, b in zip(Nn, self.N_prev)]
+        self.N_prev = Nn
+        G = (ops.Gx, ops.Gy, ops.Gz)
+        star = []
+        for c in range(3):        # Eq. (12) times dt, per component
+            r = self.Rm @ vel[c] - dt * (Nab[c] + G[c] @ self.p)
+            star.append(self._bicgstab(self.H, r, vel[c], self.rtol, self.maxit)[0])
+        b = (ops.Gx @ star[0] + ops.Gy @ star[1] + ops.Gz @ star[2]) / dt     # Eq. (13)
+        b = np.append(b, b[self.pin])
+        b[self.pin] = 0.0
+        sol = self._bicgstab(self.P, b, np.append(self.phi, self.mu), self.rtol, self.maxit)[0]
+        phi = sol[:self.N]
+        self.mu = float(sol[-1])
+        self.u, self.v, self.w = (star[c] - dt * (G[c] @ phi) for c in range(3))   # Eq. (14)
+        self.p = self.p + phi - self.alpha * (ops.L @ phi)                         # Eq. (15)
+        self.phi = phi
+        self.nstep += 1
+
+
+def abc_flow(x, y, z, t, Re, A=1.0, B=0.8, C=0.6):
+    """The Arnold-Beltrami-Childress field, an exact decaying Navier-Stokes solution
+    on the 2 pi periodic cube: curl u = u and Lap u = -u, so u . grad u =
+    grad(|u|^2 / 2) and u = U(x) exp(-t/Re), p = -|u|^2 / 2 (up to a constant)."""
+    f = np.exp(-t / Re)
+    u = (A * np.sin(z) + C * np.cos(y)) * f
+    v = (B * np.sin(x) + A * np.cos(z)) * f
+    w = (C * np.sin(y) + B * np.cos(x)) * f
+    return u, v, w, -0.5 * (u * u + v * v + w * w)

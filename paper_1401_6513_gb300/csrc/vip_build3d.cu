@@ -518,6 +518,192 @@ __global__ void k3_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t*
     if (i < n) out[i] += boff[i / SCAN_CHUNK];
 }
 
+// ---- the fractional step in 3D (Sec. 2, Eqs. 12-15), periodic node sets ----
+// Convection at every node (Sec. 4.1 item 1 in three coordinates): the products
+// of the six VIP interpolations of (u, v, w), differenced across each VIP pair
+// and divided by the pair distance.
+__global__ void k3_conv(Asm A, const double* __restrict__ u, const double* __restrict__ v,
+                        const double* __restrict__ w, double* __restrict__ Nu,
+                        double* __restrict__ Nv, double* __restrict__ Nw) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= A.a.N) return;
+    const int32_t i = A.ipos[r];
+    if (i < 0) { Nu[r] = Nv[r] = Nw[r] = 0.0; return; }
+    double val[6][3];
+    double inv[3];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int64_t p = A.a.N + (int64_t)k * A.a.Ni + i;
+        double su = 0.0, sv = 0.0, sw = 0.0;
+        for (int64_t s = A.pptr[p]; s < A.pptr[p + 1]; ++s) {
+            const double wt = A.w0[s - A.nnz_nodes];
+            const int32_t j = A.pidx[s];
+            su = fma(wt, u[j], su);
+            sv = fma(wt, v[j], sv);
+            sw = fma(wt, w[j], sw);
+        }
+        val[k][0] = su; val[k][1] = sv; val[k][2] = sw;
+    }
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        double qa[3], qb[3], rho;
+        int64_t owner;
+        point_of(A.a, A.a.N + (int64_t)(2 * ax) * A.a.Ni + i, qa, rho, owner);
+        point_of(A.a, A.a.N + (int64_t)(2 * ax + 1) * A.a.Ni + i, qb, rho, owner);
+        inv[ax] = 1.0 / fabs(qa[ax] - qb[ax]);
+    }
+    double out[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double f = 0.0;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+            f += (val[2 * ax][ax] * val[2 * ax][c] - val[2 * ax + 1][ax] * val[2 * ax + 1][c]) * inv[ax];
+        out[c] = f;
+    }
+    Nu[r] = out[0]; Nv[r] = out[1]; Nw[r] = out[2];
+}
+
+__device__ __forceinline__ double csr_row(const int64_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                          const double* __restrict__ val, int64_t r,
+                                          const double* __restrict__ x) {
+    double s = 0.0;
+    for (int64_t k = ptr[r]; k < ptr[r + 1]; ++k) s = fma(val[k], x[col[k]], s);
+    return s;
+}
+
+struct Tab3 { const int64_t* ptr; const int32_t* col; const double* val; };
+
+// Right-hand side of Eq. (12) times dt for one component:
+// (I + alpha L) u^n - dt (1.5 N^n - 0.5 N^{n-1} + G p^n).
+__global__ void k3_rhs(int64_t N, Tab3 L, Tab3 G, double alpha, double dt, const double* __restrict__ uc,
+                       const double* __restrict__ Ncur, const double* __restrict__ Nprev,
+                       const double* __restrict__ p, double* __restrict__ rhs) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const double Lu = csr_row(L.ptr, L.col, L.val, r, uc);
+    const double Gp = csr_row(G.ptr, G.col, G.val, r, p);
+    const double nab = 1.5 * Ncur[r] - 0.5 * Nprev[r];
+    rhs[r] = (uc[r] + alpha * Lu) - dt * (nab + Gp);
+}
+
+// Eq. (13) right-hand side, bordered: b_i = (Gx u* + Gy v* + Gz w*)_i / dt, then
+// b_N = b_k0 and b_k0 = 0.
+__global__ void k3_div(int64_t N, Tab3 Gx, Tab3 Gy, Tab3 Gz, double dt, int64_t k0,
+                       const double* __restrict__ us, const double* __restrict__ vs,
+                       const double* __restrict__ ws, double* __restrict__ b) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    double d = (csr_row(Gx.ptr, Gx.col, Gx.val, r, us) + csr_row(Gy.ptr, Gy.col, Gy.val, r, vs)
+                + csr_row(Gz.ptr, Gz.col, Gz.val, r, ws)) / dt;
+    if (r == k0) { b[N] = d; b[r] = 0.0; }
+    else b[r] = d;
+}
+
+// Eqs. (14)-(15): u = u* - dt G phi; p = p + phi - alpha L phi.
+__global__ void k3_project(int64_t N, Tab3 L, Tab3 Gx, Tab3 Gy, Tab3 Gz, double alpha, double dt,
+                           const double* __restrict__ phi, const double* __restrict__ us,
+                           const double* __restrict__ vs, const double* __restrict__ ws,
+                           double* __restrict__ u, double* __restrict__ v, double* __restrict__ w,
+                           double* __restrict__ p) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    u[r] = us[r] - dt * csr_row(Gx.ptr, Gx.col, Gx.val, r, phi);
+    v[r] = vs[r] - dt * csr_row(Gy.ptr, Gy.col, Gy.val, r, phi);
+    w[r] = ws[r] - dt * csr_row(Gz.ptr, Gz.col, Gz.val, r, phi);
+    p[r] = (p[r] + phi[r]) - alpha * csr_row(L.ptr, L.col, L.val, r, phi);
+}
+
+// The two systems of the step, applied matrix-free from L:
+//   HELM: y = x - alpha L x                                     (n = N)
+//   POIS: the bordered Poisson system (n = N + 1, x_N = mu):
+//         y_i = (L x)_i + mu (i != k0), y_k0 = pin x_k0, y_N = (L x)_k0 + mu.
+enum { OPK_HELM = 0, OPK_POIS = 1 };
+struct Op3 {
+    int kind;
+    int64_t n, N, k0;
+    double alpha, pin;
+    Tab3 L;
+};
+
+__global__ void k3_op(Op3 o, const double* __restrict__ x, double* __restrict__ y) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= o.n) return;
+    if (o.kind == OPK_HELM) {
+        y[r] = x[r] - o.alpha * csr_row(o.L.ptr, o.L.col, o.L.val, r, x);
+        return;
+    }
+    if (r == o.k0) { y[r] = o.pin * x[r]; return; }
+    const int64_t row = r == o.N ? o.k0 : r;
+    y[r] = csr_row(o.L.ptr, o.L.col, o.L.val, row, x) + x[o.N];
+}
+
+// Deterministic dot products: fixed grid, per-thread strided sums, a fixed tree
+// in each block, then one block sums the block partials in order.
+constexpr int DOT_B = 256, DOT_T = 256;
+
+__global__ void __launch_bounds__(DOT_T) k3_dot2(int64_t n, const double* __restrict__ a,
+                                                 const double* __restrict__ b, const double* __restrict__ c,
+                                                 const double* __restrict__ d, double* __restrict__ part) {
+    __shared__ double s0[DOT_T], s1[DOT_T];
+    double x0 = 0.0, x1 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * DOT_T + threadIdx.x; i < n; i += (int64_t)DOT_B * DOT_T) {
+        x0 = fma(a[i], b[i], x0);
+        if (c) x1 = fma(c[i], d[i], x1);
+    }
+    s0[threadIdx.x] = x0;
+    s1[threadIdx.x] = x1;
+    __syncthreads();
+    for (int o = DOT_T / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { s0[threadIdx.x] += s0[threadIdx.x + o]; s1[threadIdx.x] += s1[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = s0[0]; part[2 * blockIdx.x + 1] = s1[0]; }
+}
+
+__global__ void __launch_bounds__(DOT_B) k3_dot_final(const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double s0[DOT_B], s1[DOT_B];
+    s0[threadIdx.x] = part[2 * threadIdx.x];
+    s1[threadIdx.x] = part[2 * threadIdx.x + 1];
+    __syncthreads();
+    for (int o = DOT_B / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { s0[threadIdx.x] += s0[threadIdx.x + o]; s1[threadIdx.x] += s1[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = s0[0]; out[1] = s1[0]; }
+}
+
+// y = a x + b y' (elementwise vector updates of BiCGSTAB)
+__global__ void k3_lin2(int64_t n, double a, const double* __restrict__ x, double b,
+                        const double* __restrict__ y, double* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+// p = r + beta (p - omega v)
+__global__ void k3_pupd(int64_t n, double beta, double omega, const double* __restrict__ r,
+                        const double* __restrict__ v, double* __restrict__ p) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+}
+
+// x = x + alpha p + omega s; r = s - omega t
+__global__ void k3_xr(int64_t n, double alpha, double omega, const double* __restrict__ p,
+                      const double* __restrict__ s, const double* __restrict__ t, double* __restrict__ x,
+                      double* __restrict__ r) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        x[i] = x[i] + alpha * p[i] + omega * s[i];
+        r[i] = s[i] - omega * t[i];
+    }
+}
+
+// x = x + alpha p
+__global__ void k3_axpy(int64_t n, double alpha, const double* __restrict__ p, double* __restrict__ x) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = x[i] + alpha * p[i];
+}
+
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace
@@ -533,7 +719,7 @@ struct vip_3d {
     double support = 2.2;
     int64_t N = 0, Ni = 0, Nb = 0;
     double L[3] = {0, 0, 0};
-    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, hmax = 0.0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, hmax = 0.0, h0 = 0.0;
     std::vector<void*> node_bufs;     // freed on a new node set
     std::vector<void*> build_bufs;    // freed on a new build
     double *x = nullptr, *y = nullptr, *z = nullptr, *nx = nullptr, *ny = nullptr, *nz = nullptr,
@@ -548,6 +734,21 @@ struct vip_3d {
     double* w0 = nullptr;
     Csr tab[VIP3_OP_COUNT];
     bool have[VIP3_OP_COUNT] = {};
+    // the 3D step (vip_3d_set_flow, vip_3d_set_state, vip_3d_step)
+    bool flow = false, state = false, have_prev = false;
+    double Re = 0.0, dt = 0.0, rtol = 1e-8;
+    int32_t max_iters = 20000;
+    std::vector<void*> state_bufs;    // freed on a new node set
+    double* vel[3] = {nullptr, nullptr, nullptr};
+    double* star[3] = {nullptr, nullptr, nullptr};
+    double* Ncur[3] = {nullptr, nullptr, nullptr};
+    double* Nprev[3] = {nullptr, nullptr, nullptr};
+    double *p = nullptr, *phi = nullptr;          // phi: N + 1 (mu last)
+    double* kv[8] = {};                           // Krylov vectors, N + 1 each
+    double *dpart = nullptr, *dres = nullptr;     // dot partials and results
+    int64_t steps = 0;
+    int32_t last_helm = 0, last_poisson = 0;
+    double last_poisson_res = 0.0;
 };
 
 namespace {
@@ -668,6 +869,148 @@ vip_status assemble(vip_3d* b, int op) {
     return VIP_OK;
 }
 
+Tab3 tab3(const vip_3d* b, int op) {
+    return Tab3{b->tab[op].ptr, b->tab[op].col, b->tab[op].val};
+}
+
+// Two dot products (the second optional) of device vectors, read back to the host.
+vip_status dots(vip_3d* b, int64_t n, const double* a1, const double* b1, const double* a2,
+                const double* b2, double out[2]) {
+    k3_dot2<<<DOT_B, DOT_T, 0, b->stream>>>(n, a1, b1, a2, b2, b->dpart);
+    k3_dot_final<<<1, DOT_B, 0, b->stream>>>(b->dpart, b->dres);
+    V3_CUDA(cudaGetLastError());
+    V3_CUDA(cudaMemcpyAsync(out, b->dres, 2 * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    V3_CUDA(cudaStreamSynchronize(b->stream));
+    return VIP_OK;
+}
+
+#define V3_TRY(call)                          \
+    do {                                      \
+        vip_status s_ = (call);               \
+        if (s_ != VIP_OK) return s_;          \
+    } while (0)
+
+// Unpreconditioned BiCGSTAB (van der Vorst 1992) on o to ||rhs - A x|| <= rtol ||rhs||,
+// with the oracle's rules: restart with r_hat = r when |r_hat . r| or |r_hat . v|
+// falls below 1e-12 of the product of norms, and confirm convergence on the true
+// residual.  x holds the initial guess.
+vip_status krylov(vip_3d* b, const Op3& o, const double* rhs, double* x, int32_t* iters, double* relres) {
+    const int64_t n = o.n;
+    double *r = b->kv[0], *rhat = b->kv[1], *pp = b->kv[2], *v = b->kv[3], *sv = b->kv[4],
+           *t = b->kv[5], *y = b->kv[6];
+    const unsigned g = blocks_for(n, 256);
+    cudaStream_t st = b->stream;
+    auto apply = [&](const double* in, double* out) { k3_op<<<g, 256, 0, st>>>(o, in, out); };
+    double d[2];
+    V3_TRY(dots(b, n, rhs, rhs, nullptr, nullptr, d));
+    const double bnorm = std::sqrt(d[0]);
+    *iters = 0;
+    *relres = 0.0;
+    if (!std::isfinite(bnorm)) return fail(b, VIP_ERR_NONFINITE, "non-finite right-hand side");
+    if (bnorm == 0.0) {
+        V3_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+        return VIP_OK;
+    }
+    const double tol = b->rtol * bnorm, brk = 1e-12;
+    int32_t it = 0, restarts = 0;
+    while (it < b->max_iters) {
+        apply(x, y);
+        k3_lin2<<<g, 256, 0, st>>>(n, 1.0, rhs, -1.0, y, r);
+        V3_TRY(dots(b, n, r, r, nullptr, nullptr, d));
+        if (!std::isfinite(d[0])) return fail(b, VIP_ERR_NONFINITE, "non-finite residual");
+        if (std::sqrt(d[0]) <= tol) break;
+        if (++restarts > 1000) return fail(b, VIP_ERR_BREAKDOWN, "BiCGSTAB: no progress after 1000 restarts");
+        V3_CUDA(cudaMemcpyAsync(rhat, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        const double rhat_norm = std::sqrt(d[0]);
+        double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        V3_CUDA(cudaMemsetAsync(v, 0, n * sizeof(double), st));
+        V3_CUDA(cudaMemsetAsync(pp, 0, n * sizeof(double), st));
+        while (it < b->max_iters) {
+            V3_TRY(dots(b, n, rhat, r, r, r, d));
+            const double rho = d[0];
+            if (std::fabs(rho) <= brk * rhat_norm * std::sqrt(d[1])) break;
+            ++it;
+            const double beta = (rho / rho_old) * (alpha / omega);
+            k3_pupd<<<g, 256, 0, st>>>(n, beta, omega, r, v, pp);
+            apply(pp, v);
+            V3_TRY(dots(b, n, rhat, v, v, v, d));
+            if (std::fabs(d[0]) <= brk * rhat_norm * std::sqrt(d[1])) break;
+            alpha = rho / d[0];
+            k3_lin2<<<g, 256, 0, st>>>(n, 1.0, r, -alpha, v, sv);
+            V3_TRY(dots(b, n, sv, sv, nullptr, nullptr, d));
+            if (std::sqrt(d[0]) <= tol) {
+                k3_axpy<<<g, 256, 0, st>>>(n, alpha, pp, x);
+                break;
+            }
+            apply(sv, t);
+            V3_TRY(dots(b, n, t, t, t, sv, d));
+            if (d[0] == 0.0) {
+                k3_axpy<<<g, 256, 0, st>>>(n, alpha, pp, x);
+                break;
+            }
+            omega = d[1] / d[0];
+            k3_xr<<<g, 256, 0, st>>>(n, alpha, omega, pp, sv, t, x, r);
+            V3_TRY(dots(b, n, r, r, nullptr, nullptr, d));
+            if (!std::isfinite(d[0])) return fail(b, VIP_ERR_NONFINITE, "non-finite residual");
+            if (std::sqrt(d[0]) <= tol || omega == 0.0) break;
+            rho_old = rho;
+        }
+    }
+    apply(x, y);
+    k3_lin2<<<g, 256, 0, st>>>(n, 1.0, rhs, -1.0, y, r);
+    V3_TRY(dots(b, n, r, r, nullptr, nullptr, d));
+    *iters = it;
+    *relres = std::sqrt(d[0]) / bnorm;
+    if (!std::isfinite(*relres)) return fail(b, VIP_ERR_NONFINITE, "non-finite solution");
+    if (*relres > b->rtol) return fail(b, VIP_ERR_NOT_CONVERGED, "BiCGSTAB hit its iteration limit");
+    return VIP_OK;
+}
+
+// One fractional step (Eqs. 12-15) on a built periodic node set.
+vip_status step_once(vip_3d* b) {
+    const int64_t N = b->N;
+    const unsigned g = blocks_for(N, 128);
+    cudaStream_t st = b->stream;
+    const double alpha = b->dt / (2.0 * b->Re), dt = b->dt;
+    const Tab3 L = tab3(b, VIP3_OP_LAPLACE);
+    const Tab3 G[3] = {tab3(b, VIP3_OP_GX), tab3(b, VIP3_OP_GY), tab3(b, VIP3_OP_GZ)};
+    k3_conv<<<g, 128, 0, st>>>(asm_view(b), b->vel[0], b->vel[1], b->vel[2], b->Ncur[0], b->Ncur[1],
+                               b->Ncur[2]);
+    V3_CUDA(cudaGetLastError());
+    if (!b->have_prev)
+        for (int c = 0; c < 3; ++c)
+            V3_CUDA(cudaMemcpyAsync(b->Nprev[c], b->Ncur[c], N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double* rhs = b->kv[7];
+    int32_t helm = 0;
+    for (int c = 0; c < 3; ++c) {
+        k3_rhs<<<g, 128, 0, st>>>(N, L, G[c], alpha, dt, b->vel[c], b->Ncur[c], b->Nprev[c], b->p, rhs);
+        V3_CUDA(cudaGetLastError());
+        V3_CUDA(cudaMemcpyAsync(b->star[c], b->vel[c], N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        const Op3 oh{OPK_HELM, N, N, 0, alpha, 0.0, L};
+        int32_t it = 0;
+        double res = 0.0;
+        V3_TRY(krylov(b, oh, rhs, b->star[c], &it, &res));
+        helm += it;
+    }
+    for (int c = 0; c < 3; ++c) std::swap(b->Ncur[c], b->Nprev[c]);
+    b->have_prev = true;
+    k3_div<<<g, 128, 0, st>>>(N, G[0], G[1], G[2], dt, 0, b->star[0], b->star[1], b->star[2], rhs);
+    V3_CUDA(cudaGetLastError());
+    const Op3 op{OPK_POIS, N + 1, N, 0, alpha, -6.0 / (b->h0 * b->h0), L};
+    int32_t itp = 0;
+    double resp = 0.0;
+    V3_TRY(krylov(b, op, rhs, b->phi, &itp, &resp));
+    k3_project<<<g, 128, 0, st>>>(N, L, G[0], G[1], G[2], alpha, dt, b->phi, b->star[0], b->star[1],
+                                  b->star[2], b->vel[0], b->vel[1], b->vel[2], b->p);
+    V3_CUDA(cudaGetLastError());
+    V3_CUDA(cudaStreamSynchronize(st));
+    b->last_helm = helm;
+    b->last_poisson = itp;
+    b->last_poisson_res = resp;
+    ++b->steps;
+    return VIP_OK;
+}
+
 bool finite_all(const std::vector<double>& v) {
     for (double d : v) if (!std::isfinite(d)) return false;
     return true;
@@ -701,6 +1044,7 @@ void vip_3d_destroy(vip_3d* b) {
     DeviceScope ds(b->device);
     free_all(b->build_bufs);
     free_all(b->node_bufs);
+    free_all(b->state_bufs);
     delete b;
 }
 
@@ -764,6 +1108,12 @@ vip_status vip_3d_set_nodes(vip_3d* b, int64_t n, const double* x, const double*
     }
     reset_build(b);
     free_all(b->node_bufs);
+    free_all(b->state_bufs);
+    for (int c = 0; c < 3; ++c) b->vel[c] = b->star[c] = b->Ncur[c] = b->Nprev[c] = nullptr;
+    for (double*& q : b->kv) q = nullptr;
+    b->p = b->phi = b->dpart = b->dres = nullptr;
+    b->state = b->have_prev = false;
+    b->steps = 0;
     b->N = 0;
     double** dptr[7] = {&b->x, &b->y, &b->z, &b->nx, &b->ny, &b->nz, &b->h};
     for (int i = 0; i < 7; ++i) {
@@ -785,6 +1135,7 @@ vip_status vip_3d_set_nodes(vip_3d* b, int64_t n, const double* x, const double*
     b->Nb = (int64_t)boundary.size();
     for (int k = 0; k < 3; ++k) { b->L[k] = Ls[k]; b->lo[k] = lo[k]; b->hi[k] = hi[k]; }
     b->hmax = hmax;
+    b->h0 = hh[0];
     return VIP_OK;
 }
 
@@ -941,6 +1292,87 @@ vip_status vip_3d_apply(vip_3d* b, int which, const double* x, double* y) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     free_all(tmp);
     V3_CUDA(e);
+    return VIP_OK;
+}
+
+vip_status vip_3d_set_flow(vip_3d* b, double Re, double dt, double rtol, int32_t max_iters) {
+    if (!b) return VIP_ERR_ARG;
+    if (!(Re > 0.0) || !(dt > 0.0) || !std::isfinite(Re) || !std::isfinite(dt))
+        return fail(b, VIP_ERR_ARG, "Re and dt must be finite and > 0");
+    if (!(rtol > 0.0 && rtol < 1.0)) return fail(b, VIP_ERR_ARG, "rtol must lie in (0, 1)");
+    if (max_iters < 1) return fail(b, VIP_ERR_ARG, "max_iters must be >= 1");
+    b->Re = Re;
+    b->dt = dt;
+    b->rtol = rtol;
+    b->max_iters = max_iters;
+    b->flow = true;
+    return VIP_OK;
+}
+
+vip_status vip_3d_set_state(vip_3d* b, const double* u, const double* v, const double* w, const double* p) {
+    if (!b) return VIP_ERR_ARG;
+    if (b->N < 1) return fail(b, VIP_ERR_ARG, "no node set");
+    if (!u || !v || !w || !p) return fail(b, VIP_ERR_ARG, "null array");
+    DeviceScope ds(b->device);
+    const int64_t N = b->N;
+    if (!b->p) {
+        for (int c = 0; c < 3; ++c) {
+            V3_CUDA(alloc(b->state_bufs, &b->vel[c], N));
+            V3_CUDA(alloc(b->state_bufs, &b->star[c], N));
+            V3_CUDA(alloc(b->state_bufs, &b->Ncur[c], N));
+            V3_CUDA(alloc(b->state_bufs, &b->Nprev[c], N));
+        }
+        V3_CUDA(alloc(b->state_bufs, &b->p, N));
+        V3_CUDA(alloc(b->state_bufs, &b->phi, N + 1));
+        for (int k = 0; k < 8; ++k) V3_CUDA(alloc(b->state_bufs, &b->kv[k], N + 1));
+        V3_CUDA(alloc(b->state_bufs, &b->dpart, 2 * DOT_B));
+        V3_CUDA(alloc(b->state_bufs, &b->dres, 2));
+    }
+    const double* src[4] = {u, v, w, p};
+    double* dst[4] = {b->vel[0], b->vel[1], b->vel[2], b->p};
+    for (int k = 0; k < 4; ++k)
+        V3_CUDA(cudaMemcpyAsync(dst[k], src[k], N * sizeof(double), cudaMemcpyDefault, b->stream));
+    V3_CUDA(cudaMemsetAsync(b->phi, 0, (N + 1) * sizeof(double), b->stream));
+    V3_CUDA(cudaStreamSynchronize(b->stream));
+    b->have_prev = false;
+    b->state = true;
+    b->steps = 0;
+    return VIP_OK;
+}
+
+vip_status vip_3d_step(vip_3d* b, int32_t nsteps) {
+    if (!b) return VIP_ERR_ARG;
+    if (!b->built) return fail(b, VIP_ERR_ARG, "not built");
+    if (!b->flow || !b->state) return fail(b, VIP_ERR_ARG, "vip_3d_set_flow and vip_3d_set_state first");
+    if (b->Nb != 0 || !(b->L[0] > 0.0)) return fail(b, VIP_ERR_ARG, "the 3D step takes periodic node sets");
+    if (nsteps < 0) return fail(b, VIP_ERR_ARG, "nsteps must be >= 0");
+    DeviceScope ds(b->device);
+    const int need[4] = {VIP3_OP_LAPLACE, VIP3_OP_GX, VIP3_OP_GY, VIP3_OP_GZ};
+    for (int op : need) V3_TRY(assemble(b, op));
+    for (int k = 0; k < nsteps; ++k) V3_TRY(step_once(b));
+    return VIP_OK;
+}
+
+vip_status vip_3d_get_state(vip_3d* b, double* u, double* v, double* w, double* p, double* phi) {
+    if (!b) return VIP_ERR_ARG;
+    if (!b->state) return fail(b, VIP_ERR_ARG, "no state");
+    DeviceScope ds(b->device);
+    const int64_t N = b->N;
+    double* dst[5] = {u, v, w, p, phi};
+    const double* src[5] = {b->vel[0], b->vel[1], b->vel[2], b->p, b->phi};
+    for (int k = 0; k < 5; ++k)
+        if (dst[k]) V3_CUDA(cudaMemcpyAsync(dst[k], src[k], N * sizeof(double), cudaMemcpyDefault, b->stream));
+    V3_CUDA(cudaStreamSynchronize(b->stream));
+    return VIP_OK;
+}
+
+vip_status vip_3d_get_iters(vip_3d* b, int64_t* steps, int32_t* helm_iters, int32_t* poisson_iters,
+                            double* poisson_relres) {
+    if (!b) return VIP_ERR_ARG;
+    if (steps) *steps = b->steps;
+    if (helm_iters) *helm_iters = b->last_helm;
+    if (poisson_iters) *poisson_iters = b->last_poisson;
+    if (poisson_relres) *poisson_relres = b->last_poisson_res;
     return VIP_OK;
 }
 

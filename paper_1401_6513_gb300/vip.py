@@ -42,7 +42,8 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_set_probes", "vip_set_pressure", "vip_set_inner_tolerance",
            "vip_3d_create", "vip_3d_destroy", "vip_3d_last_error", "vip_3d_set_nodes",
            "vip_3d_set_mls", "vip_3d_build", "vip_3d_stencil_size", "vip_3d_get_stencil",
-           "vip_3d_apply"]
+           "vip_3d_apply", "vip_3d_set_flow", "vip_3d_set_state", "vip_3d_step",
+           "vip_3d_get_state", "vip_3d_get_iters"]
 OPS3 = ["NBR", "D000", "D100", "D010", "D001", "D200", "D020", "D002", "LAPLACE", "VIP_E", "VIP_W",
         "VIP_N", "VIP_S", "VIP_T", "VIP_B", "GX", "GY", "GZ", "NEUMANN"]
 OP3 = {name: i for i, name in enumerate(OPS3)}
@@ -151,6 +152,12 @@ def lib(path: str | Path | None = None):
         "vip_3d_stencil_size": ([vp, C.c_int, C.POINTER(i64), C.POINTER(i64)], C.c_int),
         "vip_3d_get_stencil": ([vp, C.c_int, vp, vp, vp], C.c_int),
         "vip_3d_apply": ([vp, C.c_int, vp, vp], C.c_int),
+        "vip_3d_set_flow": ([vp, dbl, dbl, dbl, i32], C.c_int),
+        "vip_3d_set_state": ([vp, vp, vp, vp, vp], C.c_int),
+        "vip_3d_step": ([vp, i32], C.c_int),
+        "vip_3d_get_state": ([vp, vp, vp, vp, vp, vp], C.c_int),
+        "vip_3d_get_iters": ([vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)],
+                             C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -243,6 +250,30 @@ class Build3D:
             y = np.empty_like(x) if isinstance(x, np.ndarray) else None
         self._check(self.L.vip_3d_apply(self.h, w, _ptr(x), _ptr(y)))
         return y
+
+    def vip_3d_set_flow(self, Re, dt, rtol=1e-8, max_iters=20000):
+        self._check(self.L.vip_3d_set_flow(self.h, Re, dt, rtol, max_iters))
+
+    def vip_3d_set_state(self, u, v, w, p):
+        u, v, w, p = map(_f64, (u, v, w, p))
+        self._check(self.L.vip_3d_set_state(self.h, _ptr(u), _ptr(v), _ptr(w), _ptr(p)))
+
+    def vip_3d_step(self, nsteps=1):
+        self._check(self.L.vip_3d_step(self.h, int(nsteps)))
+
+    def vip_3d_get_state(self):
+        """Return (u, v, w, p, phi) as numpy arrays."""
+        nr, _ = self.vip_3d_stencil_size(0)
+        out = [np.empty(nr, np.float64) for _ in range(5)]
+        self._check(self.L.vip_3d_get_state(self.h, *(_ptr(a) for a in out)))
+        return tuple(out)
+
+    def vip_3d_get_iters(self):
+        """(steps, Helmholtz iterations, Poisson iterations, Poisson relative residual)
+        of the last step."""
+        st, hi, pi, pr = C.c_int64(), C.c_int32(), C.c_int32(), C.c_double()
+        self._check(self.L.vip_3d_get_iters(self.h, C.byref(st), C.byref(hi), C.byref(pi), C.byref(pr)))
+        return st.value, hi.value, pi.value, pr.value
 
 
 def build3d_for(ns, device=0, stream=None, weight=VIP_W_CUBIC_SPLINE, support=2.2) -> Build3D:

@@ -1,4 +1,4 @@
-"""The 3D operator build (vip_3d_*) through the C ABI against the 3D oracle.
+"""The 3D operator build and 3D step (vip_3d_*) through the C ABI against the 3D oracle.
 
 Parity on seeded 3D node sets (jittered boxes with walls, a jittered periodic box,
 a sphere in a box), from a few hundred nodes to 15k (several hundred CTAs of the
@@ -123,4 +123,79 @@ def test_3d_argument_errors(vip):
     b.vip_3d_build()
     with pytest.raises(vip.VipError):
         b.vip_3d_stencil_size(19)                          # no such table
+    b.close()
+
+
+# ---- the 3D fractional step (periodic node sets) ----------------------------
+STEP_CASES = {
+    "cube8_jitter": lambda: w.box3d(8, periodic=True, length=2 * np.pi, jitter=0.2, seed=21),
+    "cube12": lambda: w.box3d(12, periodic=True, length=2 * np.pi),
+}
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("name", list(STEP_CASES))
+def test_3d_steps_match_oracle(vip, name):
+    """Ten steps of the ABC flow (Re 10, dt 0.02) with every solve at 1e-13 on both
+    sides: u, v, w, p and phi within 1e-10 relative L2 of the oracle."""
+    ns = STEP_CASES[name]()
+    Re, dt = 10.0, 0.02
+    u0 = o3.abc_flow(ns.x, ns.y, ns.z, 0.0, Re)
+    fs = o3.FractionalStep3(o3.Operators3(ns), Re, dt, rtol=1e-13)
+    fs.set_state(*u0)
+    b = vip.build3d_for(ns)
+    b.vip_3d_set_flow(Re, dt, 1e-13, 50000)
+    b.vip_3d_set_state(*u0)
+    for k in range(10):
+        fs.step()
+    b.vip_3d_step(10)
+    steps, hi, pi, pr = b.vip_3d_get_iters()
+    assert steps == 10 and pr <= 1e-13
+    got = b.vip_3d_get_state()
+    for g, o, f in zip(got, (fs.u, fs.v, fs.w, fs.p, fs.phi), ("u", "v", "w", "p", "phi")):
+        e = rel(g, o)
+        assert e <= 1e-10, (f, e)
+    print(name, ns.n, "nodes; last step: Helmholtz", hi, "Poisson", pi, "iterations")
+    b.close()
+
+
+def test_3d_steps_converge_to_the_abc_flow_at_32_cubed(vip):
+    """32^3 nodes, ten steps at rtol 1e-10: the errors against the exact ABC flow are
+    those of the oracle's run of the same case (u, v, w 1.1e-4, 1.3e-4, 9.8e-5; p up
+    to its mean 2.1e-3, there dominated by the splitting error of order dt), bars at
+    about twice those."""
+    ns = w.box3d(32, periodic=True, length=2 * np.pi)
+    Re, dt = 10.0, 0.02
+    b = vip.build3d_for(ns)
+    b.vip_3d_set_flow(Re, dt, 1e-10, 50000)
+    b.vip_3d_set_state(*o3.abc_flow(ns.x, ns.y, ns.z, 0.0, Re))
+    t0 = time.perf_counter()
+    b.vip_3d_step(10)
+    ms = (time.perf_counter() - t0) * 100.0
+    u, v, wv, p, _ = b.vip_3d_get_state()
+    ue, ve, we, pe = o3.abc_flow(ns.x, ns.y, ns.z, 0.2, Re)
+    dp = p - pe
+    dp -= dp.mean()
+    err = [np.abs(u - ue).max(), np.abs(v - ve).max(), np.abs(wv - we).max(), np.abs(dp).max()]
+    assert max(err[:3]) <= 2.5e-4 and err[3] <= 4e-3, err
+    print("cube32:", ns.n, "nodes,", round(ms, 2), "ms per step, iterations", b.vip_3d_get_iters(), err)
+    b.close()
+
+
+def test_3d_step_argument_errors(vip):
+    ns = w.box3d(6, jitter=0.3, seed=5)              # walls: not periodic
+    b = vip.build3d_for(ns)
+    with pytest.raises(vip.VipError):
+        b.vip_3d_set_flow(-1.0, 0.01)
+    b.vip_3d_set_flow(10.0, 0.01)
+    z = np.zeros(ns.n)
+    with pytest.raises(vip.VipError):
+        b.vip_3d_step(1)                              # no state yet
+    b.vip_3d_set_state(z, z, z, z)
+    with pytest.raises(vip.VipError) as e:
+        b.vip_3d_step(1)                              # not periodic
+    assert e.value.status == vip.VIP_ERR_ARG
     b.close()
