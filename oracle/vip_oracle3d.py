@@ -25,7 +25,10 @@ Pins (tests/test_oracle_3d.py, all CPU):
   * L 1 = 0, L (x^2 + y^2 + z^2) = 6, Gx, Gy, Gz exact on quadratics at interior
     nodes, the Neumann rows equal (2/3) h dq/dn on quadratics;
   * L and G are second order on a smooth periodic field (observed order >= 1.8);
-  * planted mistakes (a dropped factorial, a swapped VIP pair) fail the pins.
+  * planted mistakes (a dropped factorial, a swapped VIP pair) fail the pins;
+  * the 3D step (FractionalStep3, periodic sets) is second order on the exact ABC
+    flow (velocity and pressure), and a convection of the wrong sign or a dropped
+    z-difference fails that pin.
 """
 from __future__ import annotations
 

@@ -8,7 +8,10 @@ oracle's largest entry (the two sides factor the 10 x 10 moment matrices
 differently: Cholesky against LU).  At 275k nodes, where the oracle would take
 minutes, the tables are checked through properties that hold at any size: L maps
 x^2 + y^2 + z^2 to 6 and constants to 0, Gx, Gy, Gz are exact on quadratics, and
-the Neumann rows give (2/3) h dq/dn.  Argument errors return VIP_ERR_ARG.
+the Neumann rows give (2/3) h dq/dn.  The 3D step on periodic cubes (ABC flow)
+matches the oracle's steps to 1e-10 in u, v, w, p and phi, and at 32^3 nodes its
+errors against the exact flow are the oracle's.  Argument errors return
+VIP_ERR_ARG.
 """
 import time
 
