@@ -516,8 +516,8 @@ vip_status vip_bicgstab_static(int device, void* cuda_stream, int64_t n, const i
  * node's spacing along each axis (six: east/west along x, north/south along y,
  * top/bottom along z); at boundary nodes the zero-normal-derivative row
  * q_i - (4/3) q(x_i - h n_i) + (1/3) q(x_i - 2 h n_i) with MLS values at the two
- * normal points.  The 3D fractional step (vip_3d_step below) runs on periodic
- * node sets.
+ * normal points.  The 3D fractional step (vip_3d_step below) runs on node sets
+ * of interior and wall nodes, periodic or not.
  * A vip_3d handle has the conventions of vip_ctx (status returns, copied
  * inputs, caller-owned outputs, host or device pointers, its own stream). */
 typedef struct vip_3d vip_3d; /* opaque, owned by the library */
@@ -583,16 +583,19 @@ vip_status vip_3d_get_stencil(vip_3d* b, int which, int64_t* row_ptr, int32_t* c
  * host or device pointers).  Synchronises.  Errors as vip_3d_stencil_size. */
 vip_status vip_3d_apply(vip_3d* b, int which, const double* x, double* y);
 
-/* ---- the fractional step in 3D (Sec. 2, Eqs. 12-15), periodic node sets ----
- * The step of the 2D library in three coordinates on a built periodic node set
- * (every node interior): convection through the six VIPs of each node (Sec. 4.1
- * item 1), Adams-Bashforth 2 (N^{-1} = N^0 on the first step), Crank-Nicolson
- * viscous term with the exact identity, the incremental pressure reading (r^n
- * carries -G p^n; p^{n+1} = p^n + phi - (dt/2Re) L phi), the MLS Laplacian in
- * the Poisson equation.  The periodic Poisson system is singular: it is
- * bordered by one unknown mu added to every row, node 0's own equation moved to
- * an extra row and node 0's row replaced by (-6/h_0^2) phi_0 = 0.  Every solve
- * is unpreconditioned FP64 BiCGSTAB to ||b - A x|| <= rtol ||b|| on the true
+/* ---- the fractional step in 3D (Sec. 2, Eqs. 12-15) ------------------------
+ * The step of the 2D library in three coordinates on a built node set of
+ * interior and wall nodes (VIP_NODE_WALL: velocity Dirichlet, holding the value
+ * of the last vip_3d_set_state; pressure increment with zero normal derivative
+ * through the NEUMANN rows, scaled by -6/h^2): convection through the six VIPs
+ * of each interior node (Sec. 4.1 item 1), Adams-Bashforth 2 (N^{-1} = N^0 on the
+ * first step), Crank-Nicolson viscous term with the exact identity, the
+ * incremental pressure reading (r^n carries -G p^n; p^{n+1} = p^n + phi -
+ * (dt/2Re) L phi at every node), the MLS Laplacian in the Poisson equation.  No
+ * node fixes phi, so the Poisson system is bordered by one unknown mu added to
+ * the interior rows, the first interior node k0's own equation moved to an extra
+ * row and its row replaced by (-6/h_k0^2) phi_k0 = 0.  Every solve is
+ * unpreconditioned FP64 BiCGSTAB to ||b - A x|| <= rtol ||b|| on the true
  * residual, the Helmholtz solves starting from u^n, the Poisson solve from
  * (phi^n, mu^n).  The 2D library's multigrid has no 3D counterpart, so the
  * Poisson iterations grow with the node count.
@@ -601,7 +604,8 @@ vip_status vip_3d_apply(vip_3d* b, int which, const double* x, double* y);
  * vip_3d_set_state: u, v, w, p of every node (host or device); phi, mu and the
  *   Adams-Bashforth history are reset.
  * vip_3d_step: nsteps steps; synchronous.  Errors: VIP_ERR_ARG (not built, no
- *   flow or state, not periodic), VIP_ERR_NOT_CONVERGED, VIP_ERR_BREAKDOWN,
+ *   flow or state, SLIP or OUTLET nodes, no interior node), VIP_ERR_NOT_CONVERGED,
+ *   VIP_ERR_BREAKDOWN,
  *   VIP_ERR_NONFINITE, VIP_ERR_CUDA, VIP_ERR_OOM.
  * vip_3d_get_state: u, v, w, p, phi of every node into caller buffers (any may
  *   be NULL).

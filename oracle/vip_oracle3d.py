@@ -191,11 +191,11 @@ class Operators3:
 
 
 # ---------------------------------------------------------------------------
-# The fractional step in three coordinates (Sec. 2, Eqs. 12-15), periodic sets
+# The fractional step in three coordinates (Sec. 2, Eqs. 12-15)
 # ---------------------------------------------------------------------------
 
 def convection3(ops: Operators3, u, v, w):
-    """Convection at every node of a periodic set via the six VIPs (Sec. 4.1 item 1
+    """Convection at the interior nodes (zero at wall nodes) via the six VIPs (Sec. 4.1 item 1
     in three coordinates): the products of interpolated values, differenced across
     each VIP pair and divided by the pair distance (the flux form of u . grad u)."""
     I = ops.I
@@ -216,19 +216,22 @@ def convection3(ops: Operators3, u, v, w):
 
 
 class FractionalStep3:
-    """The second-order fractional step of the 2D oracle in three coordinates, on
-    periodic node sets (every node interior): AB2 convection, Crank-Nicolson
-    viscous term, the incremental pressure reading (r^n carries -G p^n, phi the
-    increment, p^{n+1} = p^n + phi - (dt/2Re) L phi), exact identity, the MLS
-    Laplacian in the Poisson equation, unpreconditioned BiCGSTAB.  The periodic
-    Poisson system is singular; as in the 2D oracle it is bordered by one unknown
-    mu added to every row, node k0 = 0's own equation moved to the extra row and
-    its row replaced by (-6/h_k0^2) phi_k0 = 0 (in 3D the Laplacian's diagonal is
-    about -6/h^2)."""
+    """The second-order fractional step of the 2D oracle in three coordinates:
+    AB2 convection, Crank-Nicolson viscous term, the incremental pressure reading
+    (r^n carries -G p^n, phi the increment, p^{n+1} = p^n + phi - (dt/2Re) L phi at
+    every node), exact identity, the MLS Laplacian in the Poisson equation,
+    unpreconditioned BiCGSTAB.  Node kinds: interior, and wall (velocity
+    Dirichlet, holding the node's initial value; pressure-increment zero normal
+    derivative through the Neumann rows, scaled by -6/h^2 so that their diagonal
+    has the sign and size of the 3D Laplacian rows).  Every 3D problem here has no
+    Dirichlet row for phi, so, as in the 2D oracle, the Poisson system is bordered
+    by one unknown mu added to the interior rows, the first interior node k0's own
+    equation moved to an extra row and its row replaced by (-6/h_k0^2) phi_k0 = 0."""
 
     def __init__(self, ops: Operators3, Re, dt, rtol=1e-8, maxit=200000):
-        if ops.boundary.size or not all(l > 0 for l in ops.L3):
-            raise ValueError("the 3D step takes periodic node sets (every node interior)")
+        kind = ops.ns.kind
+        if np.any((kind != KIND_INTERIOR) & (kind != 1)):
+            raise ValueError("the 3D step takes interior and wall nodes only")
         from .vip_oracle import bicgstab
         self._bicgstab = bicgstab
         N = ops.N
@@ -236,17 +239,21 @@ class FractionalStep3:
         self.Re, self.dt = float(Re), float(dt)
         self.rtol, self.maxit = rtol, maxit
         self.alpha = self.dt / (2.0 * self.Re)
+        inner = kind == KIND_INTERIOR
+        self.inner = inner
+        S = lambda m: sp.diags(m.astype(np.float64))  # noqa: E731  row selection
         Id = sp.identity(N, format="csr")
-        self.H = (Id - self.alpha * ops.L).tocsr()
+        self.H = (S(inner) @ (Id - self.alpha * ops.L) + S(~inner) @ Id).tocsr()
         self.Rm = (Id + self.alpha * ops.L).tocsr()
-        k0 = 0
+        pin_scale = -6.0 / ops.ns.h ** 2
+        P = (S(inner) @ ops.L + sp.diags(~inner * pin_scale) @ ops.Nb).tocsr()
+        k0 = int(np.nonzero(inner)[0][0])
         self.pin = k0
-        pin_scale = -6.0 / ops.ns.h[k0] ** 2
-        Pb = sp.bmat([[ops.L, sp.csr_matrix(np.ones((N, 1)))],
+        Pb = sp.bmat([[P, sp.csr_matrix(inner.astype(np.float64)[:, None])],
                       [sp.csr_matrix((1, N)), None]]).tolil()
         rowk = Pb[k0].copy()
         Pb[k0] = 0.0
-        Pb[k0, k0] = pin_scale
+        Pb[k0, k0] = pin_scale[k0]
         Pb[N] = rowk
         self.P = Pb.tocsr()
         self.u = np.zeros(N)
@@ -255,17 +262,21 @@ class FractionalStep3:
         self.p = np.zeros(N)
         self.phi = np.zeros(N)
         self.mu = 0.0
+        self.bc = (np.zeros(N),) * 3
         self.N_prev = None
         self.nstep = 0
 
     def set_state(self, u, v, w, p):
+        """Fields at every node; the wall nodes' velocities become their boundary
+        values."""
         self.u, self.v, self.w, self.p = (np.array(a, np.float64) for a in (u, v, w, p))
+        self.bc = (self.u.copy(), self.v.copy(), self.w.copy())
         self.phi = np.zeros(self.N)
         self.mu = 0.0
         self.N_prev = None
 
     def step(self):
-        ops, dt = self.ops, self.dt
+        ops, dt, inner = self.ops, self.dt, self.inner
         vel = (self.u, self.v, self.w)
         Nn = convection3(ops, *vel)
         if self.N_prev is None:
@@ -274,17 +285,18 @@ class FractionalStep3:
         self.N_prev = Nn
         G = (ops.Gx, ops.Gy, ops.Gz)
         star = []
-        for c in range(3):        # Eq. (12) times dt, per component
-            r = self.Rm @ vel[c] - dt * (Nab[c] + G[c] @ self.p)
+        for c in range(3):        # Eq. (12) times dt, per component; walls hold their values
+            r = np.where(inner, self.Rm @ vel[c] - dt * (Nab[c] + G[c] @ self.p), self.bc[c])
             star.append(self._bicgstab(self.H, r, vel[c], self.rtol, self.maxit)[0])
-        b = (ops.Gx @ star[0] + ops.Gy @ star[1] + ops.Gz @ star[2]) / dt     # Eq. (13)
-        b = np.append(b, b[self.pin])
+        b = np.where(inner, (ops.Gx @ star[0] + ops.Gy @ star[1] + ops.Gz @ star[2]) / dt, 0.0)
+        b = np.append(b, b[self.pin])                                        # Eq. (13)
         b[self.pin] = 0.0
         sol = self._bicgstab(self.P, b, np.append(self.phi, self.mu), self.rtol, self.maxit)[0]
         phi = sol[:self.N]
         self.mu = float(sol[-1])
-        self.u, self.v, self.w = (star[c] - dt * (G[c] @ phi) for c in range(3))   # Eq. (14)
-        self.p = self.p + phi - self.alpha * (ops.L @ phi)                         # Eq. (15)
+        self.u, self.v, self.w = (np.where(inner, star[c] - dt * (G[c] @ phi), star[c])
+                                  for c in range(3))                          # Eq. (14)
+        self.p = self.p + phi - self.alpha * (ops.L @ phi)                   # Eq. (15)
         self.phi = phi
         self.nstep += 1
 

@@ -518,7 +518,7 @@ __global__ void k3_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t*
     if (i < n) out[i] += boff[i / SCAN_CHUNK];
 }
 
-// ---- the fractional step in 3D (Sec. 2, Eqs. 12-15), periodic node sets ----
+// ---- the fractional step in 3D (Sec. 2, Eqs. 12-15) ----------------------
 // Convection at every node (Sec. 4.1 item 1 in three coordinates): the products
 // of the six VIP interpolations of (u, v, w), differenced across each VIP pair
 // and divided by the pair distance.
@@ -574,66 +574,84 @@ __device__ __forceinline__ double csr_row(const int64_t* __restrict__ ptr, const
 
 struct Tab3 { const int64_t* ptr; const int32_t* col; const double* val; };
 
-// Right-hand side of Eq. (12) times dt for one component:
-// (I + alpha L) u^n - dt (1.5 N^n - 0.5 N^{n-1} + G p^n).
-__global__ void k3_rhs(int64_t N, Tab3 L, Tab3 G, double alpha, double dt, const double* __restrict__ uc,
+// Right-hand side of Eq. (12) times dt for one component at interior rows:
+// (I + alpha L) u^n - dt (1.5 N^n - 0.5 N^{n-1} + G p^n); wall rows: the node's
+// boundary value.
+__global__ void k3_rhs(int64_t N, Tab3 L, Tab3 G, double alpha, double dt, const int32_t* __restrict__ ipos,
+                       const double* __restrict__ bc, const double* __restrict__ uc,
                        const double* __restrict__ Ncur, const double* __restrict__ Nprev,
                        const double* __restrict__ p, double* __restrict__ rhs) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
+    if (ipos[r] < 0) { rhs[r] = bc[r]; return; }      // wall: the boundary value
     const double Lu = csr_row(L.ptr, L.col, L.val, r, uc);
     const double Gp = csr_row(G.ptr, G.col, G.val, r, p);
     const double nab = 1.5 * Ncur[r] - 0.5 * Nprev[r];
     rhs[r] = (uc[r] + alpha * Lu) - dt * (nab + Gp);
 }
 
-// Eq. (13) right-hand side, bordered: b_i = (Gx u* + Gy v* + Gz w*)_i / dt, then
-// b_N = b_k0 and b_k0 = 0.
+// Eq. (13) right-hand side, bordered: b_i = (Gx u* + Gy v* + Gz w*)_i / dt at
+// interior rows, 0 at wall rows, then b_N = b_k0 and b_k0 = 0 (k0 the first
+// interior node).
 __global__ void k3_div(int64_t N, Tab3 Gx, Tab3 Gy, Tab3 Gz, double dt, int64_t k0,
-                       const double* __restrict__ us, const double* __restrict__ vs,
-                       const double* __restrict__ ws, double* __restrict__ b) {
+                       const int32_t* __restrict__ ipos, const double* __restrict__ us,
+                       const double* __restrict__ vs, const double* __restrict__ ws,
+                       double* __restrict__ b) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
+    if (ipos[r] < 0) { b[r] = 0.0; return; }          // wall rows: zero normal derivative = 0
     double d = (csr_row(Gx.ptr, Gx.col, Gx.val, r, us) + csr_row(Gy.ptr, Gy.col, Gy.val, r, vs)
                 + csr_row(Gz.ptr, Gz.col, Gz.val, r, ws)) / dt;
     if (r == k0) { b[N] = d; b[r] = 0.0; }
     else b[r] = d;
 }
 
-// Eqs. (14)-(15): u = u* - dt G phi; p = p + phi - alpha L phi.
+// Eqs. (14)-(15): u = u* - dt G phi at interior rows; p = p + phi - alpha L phi
+// at every node.
 __global__ void k3_project(int64_t N, Tab3 L, Tab3 Gx, Tab3 Gy, Tab3 Gz, double alpha, double dt,
-                           const double* __restrict__ phi, const double* __restrict__ us,
-                           const double* __restrict__ vs, const double* __restrict__ ws,
-                           double* __restrict__ u, double* __restrict__ v, double* __restrict__ w,
-                           double* __restrict__ p) {
+                           const int32_t* __restrict__ ipos, const double* __restrict__ phi,
+                           const double* __restrict__ us, const double* __restrict__ vs,
+                           const double* __restrict__ ws, double* __restrict__ u, double* __restrict__ v,
+                           double* __restrict__ w, double* __restrict__ p) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
-    u[r] = us[r] - dt * csr_row(Gx.ptr, Gx.col, Gx.val, r, phi);
-    v[r] = vs[r] - dt * csr_row(Gy.ptr, Gy.col, Gy.val, r, phi);
-    w[r] = ws[r] - dt * csr_row(Gz.ptr, Gz.col, Gz.val, r, phi);
+    if (ipos[r] >= 0) {
+        u[r] = us[r] - dt * csr_row(Gx.ptr, Gx.col, Gx.val, r, phi);
+        v[r] = vs[r] - dt * csr_row(Gy.ptr, Gy.col, Gy.val, r, phi);
+        w[r] = ws[r] - dt * csr_row(Gz.ptr, Gz.col, Gz.val, r, phi);
+    } else {                                          // walls keep their values
+        u[r] = us[r]; v[r] = vs[r]; w[r] = ws[r];
+    }
     p[r] = (p[r] + phi[r]) - alpha * csr_row(L.ptr, L.col, L.val, r, phi);
 }
 
 // The two systems of the step, applied matrix-free from L:
-//   HELM: y = x - alpha L x                                     (n = N)
-//   POIS: the bordered Poisson system (n = N + 1, x_N = mu):
-//         y_i = (L x)_i + mu (i != k0), y_k0 = pin x_k0, y_N = (L x)_k0 + mu.
+//   HELM: y = x - alpha L x at interior rows, y = x at wall rows      (n = N)
+//   POIS: the bordered Poisson system (n = N + 1, x_N = mu): interior rows
+//         y_i = (L x)_i + mu, wall rows y_i = (-6/h_i^2) (Nb x)_i, y_k0 =
+//         (-6/h_k0^2) x_k0, y_N = (L x)_k0 + mu.
 enum { OPK_HELM = 0, OPK_POIS = 1 };
 struct Op3 {
     int kind;
     int64_t n, N, k0;
-    double alpha, pin;
-    Tab3 L;
+    double alpha;
+    Tab3 L, Nb;
+    const int32_t* ipos;
+    const double* h;
 };
 
 __global__ void k3_op(Op3 o, const double* __restrict__ x, double* __restrict__ y) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= o.n) return;
     if (o.kind == OPK_HELM) {
-        y[r] = x[r] - o.alpha * csr_row(o.L.ptr, o.L.col, o.L.val, r, x);
+        y[r] = o.ipos[r] >= 0 ? x[r] - o.alpha * csr_row(o.L.ptr, o.L.col, o.L.val, r, x) : x[r];
         return;
     }
-    if (r == o.k0) { y[r] = o.pin * x[r]; return; }
+    if (r == o.k0) { y[r] = (-6.0 / (o.h[r] * o.h[r])) * x[r]; return; }
+    if (r < o.N && o.ipos[r] < 0) {
+        y[r] = (-6.0 / (o.h[r] * o.h[r])) * csr_row(o.Nb.ptr, o.Nb.col, o.Nb.val, r, x);
+        return;
+    }
     const int64_t row = r == o.N ? o.k0 : r;
     y[r] = csr_row(o.L.ptr, o.L.col, o.L.val, row, x) + x[o.N];
 }
@@ -743,7 +761,10 @@ struct vip_3d {
     double* star[3] = {nullptr, nullptr, nullptr};
     double* Ncur[3] = {nullptr, nullptr, nullptr};
     double* Nprev[3] = {nullptr, nullptr, nullptr};
+    double* bc[3] = {nullptr, nullptr, nullptr};  // wall values (the state set last)
     double *p = nullptr, *phi = nullptr;          // phi: N + 1 (mu last)
+    int64_t k0 = -1;                              // first interior node
+    bool other_kinds = false;                     // SLIP or OUTLET nodes present
     double* kv[8] = {};                           // Krylov vectors, N + 1 each
     double *dpart = nullptr, *dres = nullptr;     // dot partials and results
     int64_t steps = 0;
@@ -966,13 +987,14 @@ vip_status krylov(vip_3d* b, const Op3& o, const double* rhs, double* x, int32_t
     return VIP_OK;
 }
 
-// One fractional step (Eqs. 12-15) on a built periodic node set.
+// One fractional step (Eqs. 12-15) on a built node set of interior and wall nodes.
 vip_status step_once(vip_3d* b) {
     const int64_t N = b->N;
     const unsigned g = blocks_for(N, 128);
     cudaStream_t st = b->stream;
     const double alpha = b->dt / (2.0 * b->Re), dt = b->dt;
     const Tab3 L = tab3(b, VIP3_OP_LAPLACE);
+    const Tab3 Nb = b->Nb ? tab3(b, VIP3_OP_NEUMANN) : Tab3{nullptr, nullptr, nullptr};
     const Tab3 G[3] = {tab3(b, VIP3_OP_GX), tab3(b, VIP3_OP_GY), tab3(b, VIP3_OP_GZ)};
     k3_conv<<<g, 128, 0, st>>>(asm_view(b), b->vel[0], b->vel[1], b->vel[2], b->Ncur[0], b->Ncur[1],
                                b->Ncur[2]);
@@ -983,10 +1005,11 @@ vip_status step_once(vip_3d* b) {
     double* rhs = b->kv[7];
     int32_t helm = 0;
     for (int c = 0; c < 3; ++c) {
-        k3_rhs<<<g, 128, 0, st>>>(N, L, G[c], alpha, dt, b->vel[c], b->Ncur[c], b->Nprev[c], b->p, rhs);
+        k3_rhs<<<g, 128, 0, st>>>(N, L, G[c], alpha, dt, b->ipos, b->bc[c], b->vel[c], b->Ncur[c],
+                                  b->Nprev[c], b->p, rhs);
         V3_CUDA(cudaGetLastError());
         V3_CUDA(cudaMemcpyAsync(b->star[c], b->vel[c], N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        const Op3 oh{OPK_HELM, N, N, 0, alpha, 0.0, L};
+        const Op3 oh{OPK_HELM, N, N, b->k0, alpha, L, Nb, b->ipos, b->h};
         int32_t it = 0;
         double res = 0.0;
         V3_TRY(krylov(b, oh, rhs, b->star[c], &it, &res));
@@ -994,14 +1017,15 @@ vip_status step_once(vip_3d* b) {
     }
     for (int c = 0; c < 3; ++c) std::swap(b->Ncur[c], b->Nprev[c]);
     b->have_prev = true;
-    k3_div<<<g, 128, 0, st>>>(N, G[0], G[1], G[2], dt, 0, b->star[0], b->star[1], b->star[2], rhs);
+    k3_div<<<g, 128, 0, st>>>(N, G[0], G[1], G[2], dt, b->k0, b->ipos, b->star[0], b->star[1], b->star[2],
+                              rhs);
     V3_CUDA(cudaGetLastError());
-    const Op3 op{OPK_POIS, N + 1, N, 0, alpha, -6.0 / (b->h0 * b->h0), L};
+    const Op3 op{OPK_POIS, N + 1, N, b->k0, alpha, L, Nb, b->ipos, b->h};
     int32_t itp = 0;
     double resp = 0.0;
     V3_TRY(krylov(b, op, rhs, b->phi, &itp, &resp));
-    k3_project<<<g, 128, 0, st>>>(N, L, G[0], G[1], G[2], alpha, dt, b->phi, b->star[0], b->star[1],
-                                  b->star[2], b->vel[0], b->vel[1], b->vel[2], b->p);
+    k3_project<<<g, 128, 0, st>>>(N, L, G[0], G[1], G[2], alpha, dt, b->ipos, b->phi, b->star[0],
+                                  b->star[1], b->star[2], b->vel[0], b->vel[1], b->vel[2], b->p);
     V3_CUDA(cudaGetLastError());
     V3_CUDA(cudaStreamSynchronize(st));
     b->last_helm = helm;
@@ -1109,7 +1133,7 @@ vip_status vip_3d_set_nodes(vip_3d* b, int64_t n, const double* x, const double*
     reset_build(b);
     free_all(b->node_bufs);
     free_all(b->state_bufs);
-    for (int c = 0; c < 3; ++c) b->vel[c] = b->star[c] = b->Ncur[c] = b->Nprev[c] = nullptr;
+    for (int c = 0; c < 3; ++c) b->vel[c] = b->star[c] = b->Ncur[c] = b->Nprev[c] = b->bc[c] = nullptr;
     for (double*& q : b->kv) q = nullptr;
     b->p = b->phi = b->dpart = b->dres = nullptr;
     b->state = b->have_prev = false;
@@ -1136,6 +1160,10 @@ vip_status vip_3d_set_nodes(vip_3d* b, int64_t n, const double* x, const double*
     for (int k = 0; k < 3; ++k) { b->L[k] = Ls[k]; b->lo[k] = lo[k]; b->hi[k] = hi[k]; }
     b->hmax = hmax;
     b->h0 = hh[0];
+    b->k0 = interior.empty() ? -1 : interior[0];
+    b->other_kinds = false;
+    for (int64_t i = 0; i < n; ++i)
+        if (hk[i] == VIP_NODE_SLIP || hk[i] == VIP_NODE_OUTLET) b->other_kinds = true;
     return VIP_OK;
 }
 
@@ -1321,6 +1349,7 @@ vip_status vip_3d_set_state(vip_3d* b, const double* u, const double* v, const d
             V3_CUDA(alloc(b->state_bufs, &b->star[c], N));
             V3_CUDA(alloc(b->state_bufs, &b->Ncur[c], N));
             V3_CUDA(alloc(b->state_bufs, &b->Nprev[c], N));
+            V3_CUDA(alloc(b->state_bufs, &b->bc[c], N));
         }
         V3_CUDA(alloc(b->state_bufs, &b->p, N));
         V3_CUDA(alloc(b->state_bufs, &b->phi, N + 1));
@@ -1332,6 +1361,8 @@ vip_status vip_3d_set_state(vip_3d* b, const double* u, const double* v, const d
     double* dst[4] = {b->vel[0], b->vel[1], b->vel[2], b->p};
     for (int k = 0; k < 4; ++k)
         V3_CUDA(cudaMemcpyAsync(dst[k], src[k], N * sizeof(double), cudaMemcpyDefault, b->stream));
+    for (int c = 0; c < 3; ++c)
+        V3_CUDA(cudaMemcpyAsync(b->bc[c], b->vel[c], N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream));
     V3_CUDA(cudaMemsetAsync(b->phi, 0, (N + 1) * sizeof(double), b->stream));
     V3_CUDA(cudaStreamSynchronize(b->stream));
     b->have_prev = false;
@@ -1344,10 +1375,11 @@ vip_status vip_3d_step(vip_3d* b, int32_t nsteps) {
     if (!b) return VIP_ERR_ARG;
     if (!b->built) return fail(b, VIP_ERR_ARG, "not built");
     if (!b->flow || !b->state) return fail(b, VIP_ERR_ARG, "vip_3d_set_flow and vip_3d_set_state first");
-    if (b->Nb != 0 || !(b->L[0] > 0.0)) return fail(b, VIP_ERR_ARG, "the 3D step takes periodic node sets");
+    if (b->other_kinds) return fail(b, VIP_ERR_ARG, "the 3D step takes interior and wall nodes only");
+    if (b->k0 < 0) return fail(b, VIP_ERR_ARG, "the 3D step needs an interior node");
     if (nsteps < 0) return fail(b, VIP_ERR_ARG, "nsteps must be >= 0");
     DeviceScope ds(b->device);
-    const int need[4] = {VIP3_OP_LAPLACE, VIP3_OP_GX, VIP3_OP_GY, VIP3_OP_GZ};
+    const int need[5] = {VIP3_OP_LAPLACE, VIP3_OP_GX, VIP3_OP_GY, VIP3_OP_GZ, VIP3_OP_NEUMANN};
     for (int op : need) V3_TRY(assemble(b, op));
     for (int k = 0; k < nsteps; ++k) V3_TRY(step_once(b));
     return VIP_OK;

@@ -9,8 +9,9 @@ differently: Cholesky against LU).  At 275k nodes, where the oracle would take
 minutes, the tables are checked through properties that hold at any size: L maps
 x^2 + y^2 + z^2 to 6 and constants to 0, Gx, Gy, Gz are exact on quadratics, and
 the Neumann rows give (2/3) h dq/dn.  The 3D step on periodic cubes (ABC flow)
-matches the oracle's steps to 1e-10 in u, v, w, p and phi, and at 32^3 nodes its
-errors against the exact flow are the oracle's.  Argument errors return
+and on the walled lid-driven cube matches the oracle's steps to 1e-10 in u, v, w,
+p and phi; at 32^3 nodes its errors against the exact ABC flow are the oracle's,
+and at 25^3 walled nodes plane Poiseuille flow stays a fixed point.  Argument errors return
 VIP_ERR_ARG.
 """
 import time
@@ -136,6 +137,57 @@ STEP_CASES = {
 }
 
 
+def lid_state(ns):
+    """The lid-driven cube: u = 1 on the face z = 1, rest elsewhere, p = 0."""
+    u = np.where(np.isclose(ns.z, 1.0), 1.0, 0.0)
+    z = np.zeros(ns.n)
+    return u, z, z, z
+
+
+@pytest.mark.parametrize("n", [6, 8])
+def test_3d_walled_steps_match_oracle(vip, n):
+    """The lid-driven unit cube (walls on every face, jittered interior, Re 100, dt
+    0.01): ten steps with every solve at 1e-13 on both sides, u, v, w, p and phi
+    within 1e-10 relative L2 of the oracle."""
+    ns = w.box3d(n, jitter=0.25, seed=13)
+    Re, dt = 100.0, 0.01
+    st0 = lid_state(ns)
+    fs = o3.FractionalStep3(o3.Operators3(ns), Re, dt, rtol=1e-13)
+    fs.set_state(*st0)
+    b = vip.build3d_for(ns)
+    b.vip_3d_set_flow(Re, dt, 1e-13, 50000)
+    b.vip_3d_set_state(*st0)
+    for _ in range(10):
+        fs.step()
+    b.vip_3d_step(10)
+    got = b.vip_3d_get_state()
+    for g, o, f in zip(got, (fs.u, fs.v, fs.w, fs.p, fs.phi), ("u", "v", "w", "p", "phi")):
+        e = rel(g, o)
+        assert e <= 1e-10, (f, e)
+    print("lid cube", n, ns.n, "nodes; last step:", b.vip_3d_get_iters())
+    b.close()
+
+
+def test_3d_walled_poiseuille_is_kept_at_24_cubed(vip):
+    """Plane Poiseuille flow u = y (1 - y), p = -2x/Re in the walled unit cube at 25^3
+    nodes (jittered interior): a fixed point of the step up to rounding (the oracle
+    keeps it to 1e-14 at 9^3); after 20 steps at rtol 1e-11 within 1e-9."""
+    ns = w.box3d(24, jitter=0.25, seed=14)
+    x, y = ns.x, ns.y
+    Re = 10.0
+    u0 = y * (1 - y)
+    b = vip.build3d_for(ns)
+    b.vip_3d_set_flow(Re, 0.01, 1e-11, 50000)
+    b.vip_3d_set_state(u0, 0 * u0, 0 * u0, -2 * x / Re)
+    b.vip_3d_step(20)
+    u, v, wv, p, _ = b.vip_3d_get_state()
+    dp = p + 2 * x / Re
+    drift = max(np.abs(u - u0).max(), np.abs(v).max(), np.abs(wv).max(), np.abs(dp - dp.mean()).max())
+    assert drift <= 1e-9, drift
+    print("Poiseuille 25^3:", ns.n, "nodes, drift", drift, b.vip_3d_get_iters())
+    b.close()
+
+
 def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
@@ -189,7 +241,7 @@ def test_3d_steps_converge_to_the_abc_flow_at_32_cubed(vip):
 
 
 def test_3d_step_argument_errors(vip):
-    ns = w.box3d(6, jitter=0.3, seed=5)              # walls: not periodic
+    ns = w.box3d(6, jitter=0.3, seed=5)
     b = vip.build3d_for(ns)
     with pytest.raises(vip.VipError):
         b.vip_3d_set_flow(-1.0, 0.01)
@@ -197,8 +249,15 @@ def test_3d_step_argument_errors(vip):
     z = np.zeros(ns.n)
     with pytest.raises(vip.VipError):
         b.vip_3d_step(1)                              # no state yet
+    b.close()
+    kind = ns.kind.copy()
+    kind[kind == vip.VIP_NODE_WALL] = vip.VIP_NODE_OUTLET
+    b = vip.Build3D()
+    b.vip_3d_set_nodes(ns.x, ns.y, ns.z, kind, ns.nx, ns.ny, ns.nz, ns.h)
+    b.vip_3d_build()
+    b.vip_3d_set_flow(10.0, 0.01)
     b.vip_3d_set_state(z, z, z, z)
     with pytest.raises(vip.VipError) as e:
-        b.vip_3d_step(1)                              # not periodic
+        b.vip_3d_step(1)                              # outlet nodes: not in the 3D step
     assert e.value.status == vip.VIP_ERR_ARG
     b.close()
