@@ -603,7 +603,9 @@ vip_status vip_3d_apply(vip_3d* b, int which, const double* x, double* y);
  * vip_3d_set_flow: Re > 0, dt > 0, rtol in (0, 1), max_iters >= 1 per solve.
  * vip_3d_set_state: u, v, w, p of every node (host or device); phi, mu and the
  *   Adams-Bashforth history are reset.
- * vip_3d_step: nsteps steps; synchronous.  Errors: VIP_ERR_ARG (not built, no
+ * vip_3d_step: nsteps steps; synchronous.  After an error other than
+ *   VIP_ERR_ARG the fields and the Adams-Bashforth history are partly updated:
+ *   set the state again before stepping on.  Errors: VIP_ERR_ARG (not built, no
  *   flow or state, SLIP or OUTLET nodes, no interior node), VIP_ERR_NOT_CONVERGED,
  *   VIP_ERR_BREAKDOWN,
  *   VIP_ERR_NONFINITE, VIP_ERR_CUDA, VIP_ERR_OOM.
