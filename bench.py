@@ -82,6 +82,8 @@ def parse():
                          "initial fields under each of the four (untimed setup)")
     ap.add_argument("--ws-samples", type=int, default=24)
     ap.add_argument("--ws-epochs", type=int, default=20)
+    ap.add_argument("--no-developed", action="store_true",
+                    help="skip the second timed window after the flow has developed")
     return ap.parse_args()
 
 
@@ -411,6 +413,45 @@ def form_run(vip, ctx, stream, ckpt, k, prec, ws_mode=None):
             "last_poisson_relres": s1.poisson_relres, "status": s1.status}
 
 
+# Steps from the impulsive start before the second, developed-flow window.
+DEVELOP_STEPS = 200
+
+
+def developed_window(vip, ctx, stream, ckpt, prec, ws_mode, args, N, ws):
+    """The timed measurement again, later in the flow: from the checkpoint of the first
+    window, untimed steps until DEVELOP_STEPS steps have passed since the impulsive
+    start, the warm start refitted on the solves just before (as for the first
+    window), two untimed steps, then the same number of timed steps (CUDA events on
+    the library's stream, max over ranks)."""
+    start = args.warmup + (args.ws_samples + 2 if ws_mode else 0)
+    ctx.vip_set_solver(prec, 1e-8, 50000, vip.VIP_IDENTITY_EXACT)
+    ctx.vip_ws_enable(0)
+    ctx.vip_checkpoint(False, ckpt)
+    ctx.vip_step(max(0, DEVELOP_STEPS - start))
+    out = {}
+    if ws_mode:
+        ctx.vip_ws_collect(True, args.ws_samples)
+        ctx.vip_step(args.ws_samples)
+        ctx.vip_ws_collect(False)
+        tc = ctx.vip_ws_train(epochs=args.ws_epochs if ws_mode == 1 else 1, lr=1e-3, seed=7)
+        ctx.vip_ws_enable(ws_mode)
+        out["extrapolation_coefficient"] = tc.extrap
+    ctx.vip_step(2)
+    first = max(DEVELOP_STEPS, start) + (args.ws_samples if ws_mode else 0) + 2
+    s0 = ctx.vip_get_stats()
+    barrier(ws)
+    ms = timed_steps(ctx, stream, args.steps)
+    barrier(ws)
+    ms = max_over_ranks(ms, ws)
+    s1 = ctx.vip_get_stats()
+    out.update({"window": f"steps {first + 1}-{first + args.steps} from the impulsive start",
+                "value": N * args.steps * ws / (ms / 1e3), "unit": UNIT,
+                "ms_per_step": ms / args.steps,
+                "poisson_iters_per_step": (s1.total_poisson_iters - s0.total_poisson_iters) / args.steps,
+                "last_poisson_relres": s1.poisson_relres, "status": s1.status})
+    return out
+
+
 def ALL_FORMS(vip):
     return (vip.VIP_PREC_MIXED, vip.VIP_PREC_FP64, vip.VIP_PREC_MG32)
 
@@ -627,6 +668,9 @@ def main():
         prev_cmp = form_run(vip, ctx, stream, ckpt, args.steps, prec, ws_mode=0)
         prev_cmp["node_updates_per_s"] = N / (prev_cmp["ms_per_step"] / 1e3)
         prev_cmp["chosen_over_previous_guess"] = value / ws / prev_cmp["node_updates_per_s"]
+    developed = None
+    if not args.no_developed:
+        developed = developed_window(vip, ctx, stream, ckpt, prec, ws_mode, args, N, ws)
     ctx.close()
     batch = None
     if ws == 1 and not args.no_batch and args.workload != "triangles64":
@@ -677,6 +721,8 @@ def main():
             # extrapolation alone its gather
             "gpu_launches": (6 + {0: 0, 1: 9, 2: 1}[ws_mode]) * args.steps,
             "clocks": clk}
+    if developed is not None:
+        line["developed_window"] = developed
     if fp64_cmp is not None:
         line["fp64_same_steps"] = fp64_cmp
     if prev_cmp is not None:
