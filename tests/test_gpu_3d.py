@@ -261,3 +261,21 @@ def test_3d_step_argument_errors(vip):
         b.vip_3d_step(1)                              # outlet nodes: not in the 3D step
     assert e.value.status == vip.VIP_ERR_ARG
     b.close()
+
+
+def test_3d_tables_with_the_printed_weight(vip):
+    """The printed weight of Sec. 3 on a jittered periodic cube (10^3 nodes).  Its
+    steep fall towards the support's edge makes the moment matrices less well
+    conditioned (condition numbers up to 5.4e6 here; at the corners of a walled box
+    the 11-point stencils are singular to 1.8e13, where the oracle refuses them), so
+    the two factorisations (Cholesky, LU) are compared at 1e-8, about ten times
+    cond x eps.  Neighbour lists stay exact."""
+    ns = w.box3d(10, periodic=True, jitter=0.25, seed=9)
+    ops = o3.Operators3(ns, weight="paper")
+    b = vip.build3d_for(ns, weight=vip.VIP_W_PAPER)
+    ptr, col, _ = b.vip_3d_get_stencil("NBR")
+    assert np.array_equal(ptr, ops.node_ptr) and np.array_equal(col.astype(np.int64), ops.node_idx)
+    for t in TABLES:
+        d = rel_diff(gpu_csr(b, t, ns.n), oracle_table(ops, t))
+        assert d <= 1e-8, (t, d)
+    b.close()
