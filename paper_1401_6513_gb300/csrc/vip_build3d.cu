@@ -640,7 +640,9 @@ struct Op3 {
     const double* h;
 };
 
-__global__ void k3_op(Op3 o, const double* __restrict__ x, double* __restrict__ y) {
+__global__ void k3_op(Op3 o, const double* __restrict__ x, double* __restrict__ y,
+                      const int32_t* __restrict__ run) {
+    if (run && *run != 0) return;   // the inner loop has stopped (KS state)
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= o.n) return;
     if (o.kind == OPK_HELM) {
@@ -698,28 +700,101 @@ __global__ void k3_lin2(int64_t n, double a, const double* __restrict__ x, doubl
     if (i < n) out[i] = a * x[i] + b * y[i];
 }
 
-// p = r + beta (p - omega v)
-__global__ void k3_pupd(int64_t n, double beta, double omega, const double* __restrict__ r,
-                        const double* __restrict__ v, double* __restrict__ p) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+// Device-resident scalars of one BiCGSTAB inner loop.  The single-thread kernels
+// below apply the same IEEE operations the host would, so the iterates do not
+// depend on where the scalars live; every vector kernel does nothing once the
+// state has left "running".
+enum { KS_RUN = 0, KS_LEAVE = 1, KS_RESTART = 2, KS_ADD_LEAVE = 3 };
+struct KS {
+    double rho, rho_old, alpha, omega, beta, rhat_norm, tol, brk;
+    double d[2];            // results of the last pair of dot products
+    int32_t it, max_it, state, pad;
+};
+
+__global__ void k3_dot_final_ks(const double* __restrict__ part, KS* __restrict__ K) {
+    __shared__ double s0[DOT_B], s1[DOT_B];
+    s0[threadIdx.x] = part[2 * threadIdx.x];
+    s1[threadIdx.x] = part[2 * threadIdx.x + 1];
+    __syncthreads();
+    for (int o = DOT_B / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { s0[threadIdx.x] += s0[threadIdx.x + o]; s1[threadIdx.x] += s1[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { K->d[0] = s0[0]; K->d[1] = s1[0]; }
 }
 
-// x = x + alpha p + omega s; r = s - omega t
-__global__ void k3_xr(int64_t n, double alpha, double omega, const double* __restrict__ p,
+// after (r_hat . r, r . r): breakdown test, iteration count, beta
+__global__ void ks_top(KS* K) {
+    if (K->state != KS_RUN) return;
+    if (K->it >= K->max_it) { K->state = KS_LEAVE; return; }
+    const double rho = K->d[0];
+    if (fabs(rho) <= K->brk * K->rhat_norm * sqrt(K->d[1])) { K->state = KS_RESTART; return; }
+    K->rho = rho;
+    K->it += 1;
+    K->beta = (rho / K->rho_old) * (K->alpha / K->omega);
+}
+
+// after (r_hat . v, v . v): breakdown test, alpha
+__global__ void ks_alpha(KS* K) {
+    if (K->state != KS_RUN) return;
+    if (fabs(K->d[0]) <= K->brk * K->rhat_norm * sqrt(K->d[1])) { K->state = KS_RESTART; return; }
+    K->alpha = K->rho / K->d[0];
+}
+
+// after (s . s): converged on s -> x += alpha p, leave
+__global__ void ks_s(KS* K) {
+    if (K->state != KS_RUN) return;
+    if (sqrt(K->d[0]) <= K->tol) K->state = KS_ADD_LEAVE;
+}
+
+// after (t . t, t . s): omega (t = 0 -> x += alpha p, leave)
+__global__ void ks_omega(KS* K) {
+    if (K->state != KS_RUN) return;
+    if (K->d[0] == 0.0) { K->state = KS_ADD_LEAVE; return; }
+    K->omega = K->d[1] / K->d[0];
+}
+
+// after (r . r): converged or omega = 0 -> leave
+__global__ void ks_end(KS* K) {
+    if (K->state != KS_RUN) return;
+    if (sqrt(K->d[0]) <= K->tol || K->omega == 0.0) { K->state = KS_LEAVE; return; }
+    K->rho_old = K->rho;
+}
+
+__global__ void ks_added(KS* K) {
+    if (K->state == KS_ADD_LEAVE) K->state = KS_LEAVE;
+}
+
+__global__ void kd_pupd(int64_t n, const KS* __restrict__ K, const double* __restrict__ r,
+                        const double* __restrict__ v, double* __restrict__ p) {
+    if (K->state != KS_RUN) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = r[i] + K->beta * (p[i] - K->omega * v[i]);
+}
+
+__global__ void kd_s(int64_t n, const KS* __restrict__ K, const double* __restrict__ r,
+                     const double* __restrict__ v, double* __restrict__ s) {
+    if (K->state != KS_RUN) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) s[i] = r[i] - K->alpha * v[i];
+}
+
+__global__ void kd_axpy_add(int64_t n, const KS* __restrict__ K, const double* __restrict__ p,
+                            double* __restrict__ x) {
+    if (K->state != KS_ADD_LEAVE) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = x[i] + K->alpha * p[i];
+}
+
+__global__ void kd_xr(int64_t n, const KS* __restrict__ K, const double* __restrict__ p,
                       const double* __restrict__ s, const double* __restrict__ t, double* __restrict__ x,
                       double* __restrict__ r) {
+    if (K->state != KS_RUN) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        x[i] = x[i] + alpha * p[i] + omega * s[i];
-        r[i] = s[i] - omega * t[i];
+        x[i] = x[i] + K->alpha * p[i] + K->omega * s[i];
+        r[i] = s[i] - K->omega * t[i];
     }
-}
-
-// x = x + alpha p
-__global__ void k3_axpy(int64_t n, double alpha, const double* __restrict__ p, double* __restrict__ x) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] = x[i] + alpha * p[i];
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -767,6 +842,7 @@ struct vip_3d {
     bool other_kinds = false;                     // SLIP or OUTLET nodes present
     double* kv[8] = {};                           // Krylov vectors, N + 1 each
     double *dpart = nullptr, *dres = nullptr;     // dot partials and results
+    void* ks = nullptr;                           // device BiCGSTAB scalars (KS)
     int64_t steps = 0;
     int32_t last_helm = 0, last_poisson = 0;
     double last_poisson_res = 0.0;
@@ -919,9 +995,17 @@ vip_status krylov(vip_3d* b, const Op3& o, const double* rhs, double* x, int32_t
     const int64_t n = o.n;
     double *r = b->kv[0], *rhat = b->kv[1], *pp = b->kv[2], *v = b->kv[3], *sv = b->kv[4],
            *t = b->kv[5], *y = b->kv[6];
+    KS* K = static_cast<KS*>(b->ks);
+    const int32_t* run = &K->state;
     const unsigned g = blocks_for(n, 256);
     cudaStream_t st = b->stream;
-    auto apply = [&](const double* in, double* out) { k3_op<<<g, 256, 0, st>>>(o, in, out); };
+    auto apply = [&](const double* in, double* out, const int32_t* guard) {
+        k3_op<<<g, 256, 0, st>>>(o, in, out, guard);
+    };
+    auto dots_ks = [&](const double* a1, const double* b1, const double* a2, const double* b2) {
+        k3_dot2<<<DOT_B, DOT_T, 0, st>>>(n, a1, b1, a2, b2, b->dpart);
+        k3_dot_final_ks<<<1, DOT_B, 0, st>>>(b->dpart, K);
+    };
     double d[2];
     V3_TRY(dots(b, n, rhs, rhs, nullptr, nullptr, d));
     const double bnorm = std::sqrt(d[0]);
@@ -932,52 +1016,61 @@ vip_status krylov(vip_3d* b, const Op3& o, const double* rhs, double* x, int32_t
         V3_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
         return VIP_OK;
     }
-    const double tol = b->rtol * bnorm, brk = 1e-12;
+    const double tol = b->rtol * bnorm;
+    // inner iterations launched between host reads: 1, 2, 4, ... 16, so that a solve
+    // of a few iterations (the Helmholtz ones) launches few that do nothing
+    constexpr int CHUNK_MAX = 16;
     int32_t it = 0, restarts = 0;
     while (it < b->max_iters) {
-        apply(x, y);
+        apply(x, y, nullptr);
         k3_lin2<<<g, 256, 0, st>>>(n, 1.0, rhs, -1.0, y, r);
         V3_TRY(dots(b, n, r, r, nullptr, nullptr, d));
         if (!std::isfinite(d[0])) return fail(b, VIP_ERR_NONFINITE, "non-finite residual");
         if (std::sqrt(d[0]) <= tol) break;
         if (++restarts > 1000) return fail(b, VIP_ERR_BREAKDOWN, "BiCGSTAB: no progress after 1000 restarts");
         V3_CUDA(cudaMemcpyAsync(rhat, r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        const double rhat_norm = std::sqrt(d[0]);
-        double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        KS h{};
+        h.rho_old = h.alpha = h.omega = 1.0;
+        h.rhat_norm = std::sqrt(d[0]);
+        h.tol = tol;
+        h.brk = 1e-12;
+        h.it = it;
+        h.max_it = b->max_iters;
+        h.state = KS_RUN;
+        V3_CUDA(cudaMemcpyAsync(K, &h, sizeof(KS), cudaMemcpyHostToDevice, st));
         V3_CUDA(cudaMemsetAsync(v, 0, n * sizeof(double), st));
         V3_CUDA(cudaMemsetAsync(pp, 0, n * sizeof(double), st));
-        while (it < b->max_iters) {
-            V3_TRY(dots(b, n, rhat, r, r, r, d));
-            const double rho = d[0];
-            if (std::fabs(rho) <= brk * rhat_norm * std::sqrt(d[1])) break;
-            ++it;
-            const double beta = (rho / rho_old) * (alpha / omega);
-            k3_pupd<<<g, 256, 0, st>>>(n, beta, omega, r, v, pp);
-            apply(pp, v);
-            V3_TRY(dots(b, n, rhat, v, v, v, d));
-            if (std::fabs(d[0]) <= brk * rhat_norm * std::sqrt(d[1])) break;
-            alpha = rho / d[0];
-            k3_lin2<<<g, 256, 0, st>>>(n, 1.0, r, -alpha, v, sv);
-            V3_TRY(dots(b, n, sv, sv, nullptr, nullptr, d));
-            if (std::sqrt(d[0]) <= tol) {
-                k3_axpy<<<g, 256, 0, st>>>(n, alpha, pp, x);
-                break;
+        for (int chunk = 1;; chunk = std::min(2 * chunk, CHUNK_MAX)) {
+            for (int c = 0; c < chunk; ++c) {
+                dots_ks(rhat, r, r, r);
+                ks_top<<<1, 1, 0, st>>>(K);
+                kd_pupd<<<g, 256, 0, st>>>(n, K, r, v, pp);
+                apply(pp, v, run);
+                dots_ks(rhat, v, v, v);
+                ks_alpha<<<1, 1, 0, st>>>(K);
+                kd_s<<<g, 256, 0, st>>>(n, K, r, v, sv);
+                dots_ks(sv, sv, nullptr, nullptr);
+                ks_s<<<1, 1, 0, st>>>(K);
+                kd_axpy_add<<<g, 256, 0, st>>>(n, K, pp, x);
+                ks_added<<<1, 1, 0, st>>>(K);
+                apply(sv, t, run);
+                dots_ks(t, t, t, sv);
+                ks_omega<<<1, 1, 0, st>>>(K);
+                kd_axpy_add<<<g, 256, 0, st>>>(n, K, pp, x);
+                ks_added<<<1, 1, 0, st>>>(K);
+                kd_xr<<<g, 256, 0, st>>>(n, K, pp, sv, t, x, r);
+                dots_ks(r, r, nullptr, nullptr);
+                ks_end<<<1, 1, 0, st>>>(K);
             }
-            apply(sv, t);
-            V3_TRY(dots(b, n, t, t, t, sv, d));
-            if (d[0] == 0.0) {
-                k3_axpy<<<g, 256, 0, st>>>(n, alpha, pp, x);
-                break;
-            }
-            omega = d[1] / d[0];
-            k3_xr<<<g, 256, 0, st>>>(n, alpha, omega, pp, sv, t, x, r);
-            V3_TRY(dots(b, n, r, r, nullptr, nullptr, d));
-            if (!std::isfinite(d[0])) return fail(b, VIP_ERR_NONFINITE, "non-finite residual");
-            if (std::sqrt(d[0]) <= tol || omega == 0.0) break;
-            rho_old = rho;
+            V3_CUDA(cudaGetLastError());
+            V3_CUDA(cudaMemcpyAsync(&h, K, sizeof(KS), cudaMemcpyDeviceToHost, st));
+            V3_CUDA(cudaStreamSynchronize(st));
+            it = h.it;
+            if (!std::isfinite(h.d[0])) return fail(b, VIP_ERR_NONFINITE, "non-finite residual");
+            if (h.state != KS_RUN) break;
         }
     }
-    apply(x, y);
+    apply(x, y, nullptr);
     k3_lin2<<<g, 256, 0, st>>>(n, 1.0, rhs, -1.0, y, r);
     V3_TRY(dots(b, n, r, r, nullptr, nullptr, d));
     *iters = it;
@@ -1136,6 +1229,7 @@ vip_status vip_3d_set_nodes(vip_3d* b, int64_t n, const double* x, const double*
     for (int c = 0; c < 3; ++c) b->vel[c] = b->star[c] = b->Ncur[c] = b->Nprev[c] = b->bc[c] = nullptr;
     for (double*& q : b->kv) q = nullptr;
     b->p = b->phi = b->dpart = b->dres = nullptr;
+    b->ks = nullptr;
     b->state = b->have_prev = false;
     b->steps = 0;
     b->N = 0;
@@ -1356,6 +1450,9 @@ vip_status vip_3d_set_state(vip_3d* b, const double* u, const double* v, const d
         for (int k = 0; k < 8; ++k) V3_CUDA(alloc(b->state_bufs, &b->kv[k], N + 1));
         V3_CUDA(alloc(b->state_bufs, &b->dpart, 2 * DOT_B));
         V3_CUDA(alloc(b->state_bufs, &b->dres, 2));
+        KS* ksp = nullptr;
+        V3_CUDA(alloc(b->state_bufs, &ksp, 1));
+        b->ks = ksp;
     }
     const double* src[4] = {u, v, w, p};
     double* dst[4] = {b->vel[0], b->vel[1], b->vel[2], b->p};
