@@ -843,6 +843,12 @@ struct vip_3d {
     double* kv[8] = {};                           // Krylov vectors, N + 1 each
     double *dpart = nullptr, *dres = nullptr;     // dot partials and results
     void* ks = nullptr;                           // device BiCGSTAB scalars (KS)
+    // one BiCGSTAB inner iteration as a CUDA graph per (system, solution vector),
+    // captured on a private stream and replayed on `stream`; dropped whenever a
+    // table, the flow parameters or the step's buffers change
+    struct IterGraph { int kind; const double* x; cudaGraphExec_t exec; };
+    std::vector<IterGraph> graphs;
+    cudaStream_t cap = nullptr;
     int64_t steps = 0;
     int32_t last_helm = 0, last_poisson = 0;
     double last_poisson_res = 0.0;
@@ -879,7 +885,13 @@ void free_all(std::vector<void*>& v) {
     v.clear();
 }
 
+void drop_graphs(vip_3d* b) {
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+}
+
 void reset_build(vip_3d* b) {
+    drop_graphs(b);
     free_all(b->build_bufs);
     b->built = false;
     for (int i = 0; i < VIP3_OP_COUNT; ++i) { b->tab[i] = Csr{}; b->have[i] = false; }
@@ -1002,10 +1014,46 @@ vip_status krylov(vip_3d* b, const Op3& o, const double* rhs, double* x, int32_t
     auto apply = [&](const double* in, double* out, const int32_t* guard) {
         k3_op<<<g, 256, 0, st>>>(o, in, out, guard);
     };
-    auto dots_ks = [&](const double* a1, const double* b1, const double* a2, const double* b2) {
-        k3_dot2<<<DOT_B, DOT_T, 0, st>>>(n, a1, b1, a2, b2, b->dpart);
-        k3_dot_final_ks<<<1, DOT_B, 0, st>>>(b->dpart, K);
+    // one inner iteration, enqueued on stream q (captured once into a graph)
+    auto iteration = [&](cudaStream_t q) {
+        auto dots_ks = [&](const double* a1, const double* b1, const double* a2, const double* b2) {
+            k3_dot2<<<DOT_B, DOT_T, 0, q>>>(n, a1, b1, a2, b2, b->dpart);
+            k3_dot_final_ks<<<1, DOT_B, 0, q>>>(b->dpart, K);
+        };
+        dots_ks(rhat, r, r, r);
+        ks_top<<<1, 1, 0, q>>>(K);
+        kd_pupd<<<g, 256, 0, q>>>(n, K, r, v, pp);
+        k3_op<<<g, 256, 0, q>>>(o, pp, v, run);
+        dots_ks(rhat, v, v, v);
+        ks_alpha<<<1, 1, 0, q>>>(K);
+        kd_s<<<g, 256, 0, q>>>(n, K, r, v, sv);
+        dots_ks(sv, sv, nullptr, nullptr);
+        ks_s<<<1, 1, 0, q>>>(K);
+        kd_axpy_add<<<g, 256, 0, q>>>(n, K, pp, x);
+        ks_added<<<1, 1, 0, q>>>(K);
+        k3_op<<<g, 256, 0, q>>>(o, sv, t, run);
+        dots_ks(t, t, t, sv);
+        ks_omega<<<1, 1, 0, q>>>(K);
+        kd_axpy_add<<<g, 256, 0, q>>>(n, K, pp, x);
+        ks_added<<<1, 1, 0, q>>>(K);
+        kd_xr<<<g, 256, 0, q>>>(n, K, pp, sv, t, x, r);
+        dots_ks(r, r, nullptr, nullptr);
+        ks_end<<<1, 1, 0, q>>>(K);
     };
+    cudaGraphExec_t exec = nullptr;
+    for (const auto& gr : b->graphs)
+        if (gr.kind == o.kind && gr.x == x) exec = gr.exec;
+    if (!exec) {
+        if (!b->cap) V3_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        V3_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        iteration(b->cap);
+        cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        V3_CUDA(ce);
+        b->graphs.push_back({o.kind, x, exec});
+    }
     double d[2];
     V3_TRY(dots(b, n, rhs, rhs, nullptr, nullptr, d));
     const double bnorm = std::sqrt(d[0]);
@@ -1041,27 +1089,7 @@ vip_status krylov(vip_3d* b, const Op3& o, const double* rhs, double* x, int32_t
         V3_CUDA(cudaMemsetAsync(v, 0, n * sizeof(double), st));
         V3_CUDA(cudaMemsetAsync(pp, 0, n * sizeof(double), st));
         for (int chunk = 1;; chunk = std::min(2 * chunk, CHUNK_MAX)) {
-            for (int c = 0; c < chunk; ++c) {
-                dots_ks(rhat, r, r, r);
-                ks_top<<<1, 1, 0, st>>>(K);
-                kd_pupd<<<g, 256, 0, st>>>(n, K, r, v, pp);
-                apply(pp, v, run);
-                dots_ks(rhat, v, v, v);
-                ks_alpha<<<1, 1, 0, st>>>(K);
-                kd_s<<<g, 256, 0, st>>>(n, K, r, v, sv);
-                dots_ks(sv, sv, nullptr, nullptr);
-                ks_s<<<1, 1, 0, st>>>(K);
-                kd_axpy_add<<<g, 256, 0, st>>>(n, K, pp, x);
-                ks_added<<<1, 1, 0, st>>>(K);
-                apply(sv, t, run);
-                dots_ks(t, t, t, sv);
-                ks_omega<<<1, 1, 0, st>>>(K);
-                kd_axpy_add<<<g, 256, 0, st>>>(n, K, pp, x);
-                ks_added<<<1, 1, 0, st>>>(K);
-                kd_xr<<<g, 256, 0, st>>>(n, K, pp, sv, t, x, r);
-                dots_ks(r, r, nullptr, nullptr);
-                ks_end<<<1, 1, 0, st>>>(K);
-            }
+            for (int c = 0; c < chunk; ++c) V3_CUDA(cudaGraphLaunch(exec, st));
             V3_CUDA(cudaGetLastError());
             V3_CUDA(cudaMemcpyAsync(&h, K, sizeof(KS), cudaMemcpyDeviceToHost, st));
             V3_CUDA(cudaStreamSynchronize(st));
@@ -1159,6 +1187,8 @@ vip_status vip_3d_create(vip_3d** out, int device, void* cuda_stream) {
 void vip_3d_destroy(vip_3d* b) {
     if (!b) return;
     DeviceScope ds(b->device);
+    drop_graphs(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
     free_all(b->build_bufs);
     free_all(b->node_bufs);
     free_all(b->state_bufs);
@@ -1423,6 +1453,7 @@ vip_status vip_3d_set_flow(vip_3d* b, double Re, double dt, double rtol, int32_t
         return fail(b, VIP_ERR_ARG, "Re and dt must be finite and > 0");
     if (!(rtol > 0.0 && rtol < 1.0)) return fail(b, VIP_ERR_ARG, "rtol must lie in (0, 1)");
     if (max_iters < 1) return fail(b, VIP_ERR_ARG, "max_iters must be >= 1");
+    drop_graphs(b);
     b->Re = Re;
     b->dt = dt;
     b->rtol = rtol;
