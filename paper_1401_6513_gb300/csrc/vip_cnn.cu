@@ -385,6 +385,7 @@ struct Cnn {
     bool collect = false, enable = false;
     bool net = true;                // the guess uses the network (false: extrapolation only)
     int loss_kind = 1;              // 0: mean squared error; 1: residual proxy (k_rloss1/2)
+    int32_t fit_window = 0;         // samples of the extrapolation fit: the last ones (0: all)
     double loss_lam = 0.01;         // weight of the squared error in the residual proxy
     float* lq = nullptr;            // [cells] q of the residual proxy
     __nv_bfloat16* s_in = nullptr;
@@ -809,16 +810,18 @@ vip_status vip_ws_train(vip_ctx* c, vip_train_cfg* cfg) {
     const int64_t nc = N.ncells;
     const CnnImage* img = N.img;
     const int nimg = (int)N.himg.size();
-    // the extrapolation coefficient: least squares over every collected sample's
-    // interior lattice nodes, a = sum t d / sum d d (t the increment change, d the
-    // previous one, both / S); the network then learns what a d leaves of t
+    // the extrapolation coefficient: least squares over the collected samples'
+    // interior lattice nodes (every sample, or the last fit_window), a = sum t d /
+    // sum d d (t the increment change, d the previous one, both / S); the network
+    // then learns what a d leaves of t
     {
         const int fb = 256;
         DeviceScratch d_part;
         VIP_CUDA(cudaMalloc(&d_part.p, 2 * fb * sizeof(double)));
         std::vector<double> part(2 * fb);
         double num = 0.0, den = 0.0;
-        for (int k = 0; k < N.nsamples; ++k) {
+        const int kfirst = N.fit_window > 0 ? std::max(0, N.nsamples - N.fit_window) : 0;
+        for (int k = kfirst; k < N.nsamples; ++k) {
             k_ws_fit<<<fb, 256, 0, s>>>(nc, N.s_tgt + (int64_t)k * nc, N.s_dprev + (int64_t)k * nc,
                                         N.s_mask + (int64_t)k * nc, static_cast<double*>(d_part.p));
             VIP_CUDA(cudaGetLastError());
@@ -902,6 +905,14 @@ vip_status vip_ws_set_loss(vip_ctx* c, int kind, double lam) {
     Cnn& N = *cnn_of(c);
     N.loss_kind = kind;
     N.loss_lam = lam;
+    return VIP_OK;
+}
+
+vip_status vip_ws_set_fit_window(vip_ctx* c, int32_t window) {
+    if (!c) return VIP_ERR_ARG;
+    if (!c->built || !c->cnn) return fail(c, VIP_ERR_ARG, "vip_ws_set_fit_window before vip_build");
+    if (window < 0) return fail(c, VIP_ERR_ARG, "vip_ws_set_fit_window: window must be >= 0");
+    cnn_of(c)->fit_window = window;
     return VIP_OK;
 }
 

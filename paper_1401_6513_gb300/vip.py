@@ -39,7 +39,7 @@ EXPORTS = ["vip_create", "vip_destroy", "vip_last_error", "vip_add_nodes", "vip_
            "vip_set_multigrid", "vip_autotune", "vip_get_geometry_iters", "vip_operator_layout",
            "vip_multigrid_info", "vip_set_mg_shift", "vip_set_refinement", "vip_checkpoint_size",
            "vip_checkpoint", "vip_ws_adam", "vip_ws_extrapolation", "vip_ws_set_loss",
-           "vip_set_probes", "vip_set_pressure", "vip_set_inner_tolerance",
+           "vip_set_probes", "vip_set_pressure", "vip_set_inner_tolerance", "vip_ws_set_fit_window",
            "vip_3d_create", "vip_3d_destroy", "vip_3d_last_error", "vip_3d_set_nodes",
            "vip_3d_set_mls", "vip_3d_build", "vip_3d_stencil_size", "vip_3d_get_stencil",
            "vip_3d_apply", "vip_3d_set_flow", "vip_3d_set_state", "vip_3d_step",
@@ -110,6 +110,7 @@ def lib(path: str | Path | None = None):
         "vip_ws_adam": ([vp, dbl], C.c_int),
         "vip_ws_extrapolation": ([vp, C.c_int, C.POINTER(dbl)], C.c_int),
         "vip_ws_set_loss": ([vp, C.c_int, dbl], C.c_int),
+        "vip_ws_set_fit_window": ([vp, i32], C.c_int),
         "vip_build": ([vp], C.c_int),
         "vip_set_state": ([vp, vp, vp, vp], C.c_int),
         "vip_step": ([vp, i32], C.c_int),
@@ -430,6 +431,10 @@ class Context:
     def vip_ws_set_loss(self, kind=1, lam=0.01):
         """Network loss: 0 mean squared error, 1 residual proxy (lattice Laplacian)."""
         self._check(self.L.vip_ws_set_loss(self.h, int(kind), float(lam)))
+
+    def vip_ws_set_fit_window(self, window=0):
+        """Fit the extrapolation coefficient on the last `window` samples (0: all)."""
+        self._check(self.L.vip_ws_set_fit_window(self.h, int(window)))
 
     def vip_ws_extrapolation(self, a=None):
         """Read the warm start's extrapolation coefficient, or set it to a."""

@@ -123,3 +123,34 @@ def test_network_gains_with_thousands_of_samples(vip):
     print("cavity_256, 2000 samples:", {k: (v[0], round(v[1], 3)) for k, v in res.items()})
     assert res["extrapolation+network"][0] < res["extrapolation"][0] < res["previous"][0], res
     ctx.close()
+
+
+def test_fit_window_fits_the_recent_flow(vip):
+    """The h = 1/32 cylinder with 400 collected solves from step 30, the impulsive
+    start's large increments among them: the extrapolation coefficient fitted on the
+    last 40 samples (vip_ws_set_fit_window) differs from the all-sample fit and needs
+    no more Poisson iterations over 20 held-out steps from one checkpoint (2,000
+    samples: 335 against 440 iterations over 40 steps)."""
+    ns = cases()["cylinder_h32"]
+    ctx = vip.solver_for(ns, precision=vip.VIP_PREC_FP64, rtol=1e-8, max_iters=50000)
+    ctx.vip_set_multigrid(1.0, 1.8)
+    with pytest.raises(vip.VipError):
+        ctx.vip_ws_set_fit_window(-1)
+    ctx.vip_step(W)
+    ctx.vip_ws_collect(True, 400)
+    ctx.vip_step(400)
+    ctx.vip_ws_collect(False)
+    ck = ctx.vip_checkpoint(True)
+    res = {}
+    for window in (0, 40):
+        ctx.vip_ws_set_fit_window(window)
+        cfg = ctx.vip_ws_train(epochs=1, lr=1e-3, seed=11)
+        ctx.vip_ws_enable(2)
+        ctx.vip_checkpoint(False, ck)
+        ctx.vip_step(1)
+        ctx.vip_checkpoint(False, ck)
+        res[window] = (cfg.extrap, poisson_run(ctx, 20)[0])
+    print("cylinder_h32, 400 samples: (a, held-out iterations) by fit window", res)
+    assert res[40][0] != res[0][0]
+    assert res[40][1] <= res[0][1], res
+    ctx.close()
