@@ -26,8 +26,10 @@ Pins (tests/test_oracle_3d.py, all CPU):
     nodes, the Neumann rows equal (2/3) h dq/dn on quadratics;
   * L and G are second order on a smooth periodic field (observed order >= 1.8);
   * planted mistakes (a dropped factorial, a swapped VIP pair) fail the pins;
-  * the 3D step (FractionalStep3) is second order on the exact ABC flow (velocity
-    and pressure), and a convection of the wrong sign or a dropped z-difference
+  * the 3D step (FractionalStep3) is second order in space on the exact ABC flow
+    (velocity and pressure), and a convection of the wrong sign or a dropped
+    z-difference fails that pin; in time the velocity is second order and the
+    pressure first order (self-convergence), and a backward-Euler viscous term
     fails that pin; with walls, plane Poiseuille flow is a fixed point to 1e-12,
     and a wrong-signed Crank-Nicolson term or walls solved as interior rows move it.
 """
