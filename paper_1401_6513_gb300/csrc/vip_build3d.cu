@@ -640,22 +640,32 @@ struct Op3 {
     const double* h;
 };
 
-__global__ void k3_op(Op3 o, const double* __restrict__ x, double* __restrict__ y,
-                      const int32_t* __restrict__ run) {
-    if (run && *run != 0) return;   // the inner loop has stopped (KS state)
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= o.n) return;
-    if (o.kind == OPK_HELM) {
-        y[r] = o.ipos[r] >= 0 ? x[r] - o.alpha * csr_row(o.L.ptr, o.L.col, o.L.val, r, x) : x[r];
-        return;
-    }
-    if (r == o.k0) { y[r] = (-6.0 / (o.h[r] * o.h[r])) * x[r]; return; }
-    if (r < o.N && o.ipos[r] < 0) {
-        y[r] = (-6.0 / (o.h[r] * o.h[r])) * csr_row(o.Nb.ptr, o.Nb.col, o.Nb.val, r, x);
-        return;
-    }
+__device__ __forceinline__ double op_row(const Op3& o, int64_t r, const double* __restrict__ x) {
+    if (o.kind == OPK_HELM)
+        return o.ipos[r] >= 0 ? x[r] - o.alpha * csr_row(o.L.ptr, o.L.col, o.L.val, r, x) : x[r];
+    if (r == o.k0) return (-6.0 / (o.h[r] * o.h[r])) * x[r];
+    if (r < o.N && o.ipos[r] < 0)
+        return (-6.0 / (o.h[r] * o.h[r])) * csr_row(o.Nb.ptr, o.Nb.col, o.Nb.val, r, x);
     const int64_t row = r == o.N ? o.k0 : r;
-    y[r] = csr_row(o.L.ptr, o.L.col, o.L.val, row, x) + x[o.N];
+    return csr_row(o.L.ptr, o.L.col, o.L.val, row, x) + x[o.N];
+}
+
+__global__ void k3_op(Op3 o, const double* __restrict__ x, double* __restrict__ y) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < o.n) y[r] = op_row(o, r, x);
+}
+
+// Sum of two values over a 256-thread block, in a fixed tree; thread 0 writes them.
+__device__ __forceinline__ void block_sum2(double a, double b, double* __restrict__ out) {
+    __shared__ double s0[256], s1[256];
+    s0[threadIdx.x] = a;
+    s1[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { s0[threadIdx.x] += s0[threadIdx.x + o]; s1[threadIdx.x] += s1[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { out[0] = s0[0]; out[1] = s1[0]; }
 }
 
 // Deterministic dot products: fixed grid, per-thread strided sums, a fixed tree
@@ -711,18 +721,6 @@ struct KS {
     int32_t it, max_it, state, pad;
 };
 
-__global__ void k3_dot_final_ks(const double* __restrict__ part, KS* __restrict__ K) {
-    __shared__ double s0[DOT_B], s1[DOT_B];
-    s0[threadIdx.x] = part[2 * threadIdx.x];
-    s1[threadIdx.x] = part[2 * threadIdx.x + 1];
-    __syncthreads();
-    for (int o = DOT_B / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) { s0[threadIdx.x] += s0[threadIdx.x + o]; s1[threadIdx.x] += s1[threadIdx.x + o]; }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) { K->d[0] = s0[0]; K->d[1] = s1[0]; }
-}
-
 // after (r_hat . r, r . r): breakdown test, iteration count, beta
 __global__ void ks_top(KS* K) {
     if (K->state != KS_RUN) return;
@@ -732,33 +730,6 @@ __global__ void ks_top(KS* K) {
     K->rho = rho;
     K->it += 1;
     K->beta = (rho / K->rho_old) * (K->alpha / K->omega);
-}
-
-// after (r_hat . v, v . v): breakdown test, alpha
-__global__ void ks_alpha(KS* K) {
-    if (K->state != KS_RUN) return;
-    if (fabs(K->d[0]) <= K->brk * K->rhat_norm * sqrt(K->d[1])) { K->state = KS_RESTART; return; }
-    K->alpha = K->rho / K->d[0];
-}
-
-// after (s . s): converged on s -> x += alpha p, leave
-__global__ void ks_s(KS* K) {
-    if (K->state != KS_RUN) return;
-    if (sqrt(K->d[0]) <= K->tol) K->state = KS_ADD_LEAVE;
-}
-
-// after (t . t, t . s): omega (t = 0 -> x += alpha p, leave)
-__global__ void ks_omega(KS* K) {
-    if (K->state != KS_RUN) return;
-    if (K->d[0] == 0.0) { K->state = KS_ADD_LEAVE; return; }
-    K->omega = K->d[1] / K->d[0];
-}
-
-// after (r . r): converged or omega = 0 -> leave
-__global__ void ks_end(KS* K) {
-    if (K->state != KS_RUN) return;
-    if (sqrt(K->d[0]) <= K->tol || K->omega == 0.0) { K->state = KS_LEAVE; return; }
-    K->rho_old = K->rho;
 }
 
 __global__ void ks_added(KS* K) {
@@ -772,13 +743,6 @@ __global__ void kd_pupd(int64_t n, const KS* __restrict__ K, const double* __res
     if (i < n) p[i] = r[i] + K->beta * (p[i] - K->omega * v[i]);
 }
 
-__global__ void kd_s(int64_t n, const KS* __restrict__ K, const double* __restrict__ r,
-                     const double* __restrict__ v, double* __restrict__ s) {
-    if (K->state != KS_RUN) return;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) s[i] = r[i] - K->alpha * v[i];
-}
-
 __global__ void kd_axpy_add(int64_t n, const KS* __restrict__ K, const double* __restrict__ p,
                             double* __restrict__ x) {
     if (K->state != KS_ADD_LEAVE) return;
@@ -786,14 +750,88 @@ __global__ void kd_axpy_add(int64_t n, const KS* __restrict__ K, const double* _
     if (i < n) x[i] = x[i] + K->alpha * p[i];
 }
 
-__global__ void kd_xr(int64_t n, const KS* __restrict__ K, const double* __restrict__ p,
-                      const double* __restrict__ s, const double* __restrict__ t, double* __restrict__ x,
-                      double* __restrict__ r) {
+// The fused kernels below write per-block partial sums of two dot products
+// (part[2 b], part[2 b + 1]); k3_final reduces them in block order and then takes
+// the iteration's scalar step.  All are launched with 256-thread blocks.
+// v = A p (mode 0: partials of r_hat . v and v . v) or t = A s (mode 1: t . t and
+// s . t); c is r_hat (mode 0) or s (mode 1).
+__global__ void __launch_bounds__(256) k3_op_dot(Op3 o, const double* __restrict__ x, double* __restrict__ y,
+                                                 const KS* __restrict__ K, const double* __restrict__ c,
+                                                 int mode, double* __restrict__ part) {
     if (K->state != KS_RUN) return;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double p0 = 0.0, p1 = 0.0;
+    if (r < o.n) {
+        const double yv = op_row(o, r, x);
+        y[r] = yv;
+        const double cy = c[r] * yv, yy = yv * yv;
+        p0 = mode == 0 ? cy : yy;
+        p1 = mode == 0 ? yy : cy;
+    }
+    block_sum2(p0, p1, part + 2 * blockIdx.x);
+}
+
+// s = r - alpha v; partials of s . s
+__global__ void __launch_bounds__(256) kd_s_dot(int64_t n, const KS* __restrict__ K, const double* __restrict__ r,
+                                                const double* __restrict__ v, double* __restrict__ s,
+                                                double* __restrict__ part) {
+    if (K->state != KS_RUN) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double p0 = 0.0;
+    if (i < n) {
+        const double sv = r[i] - K->alpha * v[i];
+        s[i] = sv;
+        p0 = sv * sv;
+    }
+    block_sum2(p0, 0.0, part + 2 * blockIdx.x);
+}
+
+// x = x + alpha p + omega s; r = s - omega t; partials of r_hat . r and r . r
+__global__ void __launch_bounds__(256) kd_xr_dot(int64_t n, const KS* __restrict__ K, const double* __restrict__ p,
+                                                 const double* __restrict__ s, const double* __restrict__ t,
+                                                 const double* __restrict__ rhat, double* __restrict__ x,
+                                                 double* __restrict__ r, double* __restrict__ part) {
+    if (K->state != KS_RUN) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double p0 = 0.0, p1 = 0.0;
     if (i < n) {
         x[i] = x[i] + K->alpha * p[i] + K->omega * s[i];
-        r[i] = s[i] - K->omega * t[i];
+        const double rv = s[i] - K->omega * t[i];
+        r[i] = rv;
+        p0 = rhat[i] * rv;
+        p1 = rv * rv;
+    }
+    block_sum2(p0, p1, part + 2 * blockIdx.x);
+}
+
+// Reduce nblk pairs of partials in block order into K->d, then the scalar step:
+//   ALPHA  (r_hat . v, v . v): breakdown test, alpha = rho / r_hat . v
+//   S      (s . s): converged on s -> x += alpha p, leave
+//   OMEGA  (t . t, s . t): omega (t = 0 -> x += alpha p, leave)
+//   END    (r_hat . r, r . r): converged or omega = 0 -> leave, else rho_old = rho
+// (the next iteration's ks_top reads r_hat . r and r . r from K->d).
+enum { FIN_ALPHA = 0, FIN_S = 1, FIN_OMEGA = 2, FIN_END = 3 };
+__global__ void __launch_bounds__(256) k3_final(const double* __restrict__ part, int nblk, KS* __restrict__ K,
+                                                int which) {
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += 256) { a += part[2 * k]; b += part[2 * k + 1]; }
+    __shared__ double d[2];
+    block_sum2(a, b, d);
+    __syncthreads();
+    if (threadIdx.x != 0 || K->state != KS_RUN) return;
+    K->d[0] = d[0];
+    K->d[1] = d[1];
+    if (which == FIN_ALPHA) {
+        if (fabs(d[0]) <= K->brk * K->rhat_norm * sqrt(d[1])) { K->state = KS_RESTART; return; }
+        K->alpha = K->rho / d[0];
+    } else if (which == FIN_S) {
+        if (sqrt(d[0]) <= K->tol) K->state = KS_ADD_LEAVE;
+    } else if (which == FIN_OMEGA) {
+        if (d[0] == 0.0) { K->state = KS_ADD_LEAVE; return; }
+        K->omega = d[1] / d[0];
+    } else {
+        if (sqrt(d[1]) <= K->tol || K->omega == 0.0) { K->state = KS_LEAVE; return; }
+        K->rho_old = K->rho;
     }
 }
 
@@ -1008,37 +1046,28 @@ vip_status krylov(vip_3d* b, const Op3& o, const double* rhs, double* x, int32_t
     double *r = b->kv[0], *rhat = b->kv[1], *pp = b->kv[2], *v = b->kv[3], *sv = b->kv[4],
            *t = b->kv[5], *y = b->kv[6];
     KS* K = static_cast<KS*>(b->ks);
-    const int32_t* run = &K->state;
     const unsigned g = blocks_for(n, 256);
     cudaStream_t st = b->stream;
-    auto apply = [&](const double* in, double* out, const int32_t* guard) {
-        k3_op<<<g, 256, 0, st>>>(o, in, out, guard);
-    };
-    // one inner iteration, enqueued on stream q (captured once into a graph)
+    auto apply = [&](const double* in, double* out) { k3_op<<<g, 256, 0, st>>>(o, in, out); };
+    // one inner iteration, enqueued on stream q (captured once into a graph): 14
+    // kernels, the dot products fused into the operator and vector kernels
+    const int nblk = (int)g;
+    double* part = b->dpart;
     auto iteration = [&](cudaStream_t q) {
-        auto dots_ks = [&](const double* a1, const double* b1, const double* a2, const double* b2) {
-            k3_dot2<<<DOT_B, DOT_T, 0, q>>>(n, a1, b1, a2, b2, b->dpart);
-            k3_dot_final_ks<<<1, DOT_B, 0, q>>>(b->dpart, K);
-        };
-        dots_ks(rhat, r, r, r);
         ks_top<<<1, 1, 0, q>>>(K);
         kd_pupd<<<g, 256, 0, q>>>(n, K, r, v, pp);
-        k3_op<<<g, 256, 0, q>>>(o, pp, v, run);
-        dots_ks(rhat, v, v, v);
-        ks_alpha<<<1, 1, 0, q>>>(K);
-        kd_s<<<g, 256, 0, q>>>(n, K, r, v, sv);
-        dots_ks(sv, sv, nullptr, nullptr);
-        ks_s<<<1, 1, 0, q>>>(K);
+        k3_op_dot<<<g, 256, 0, q>>>(o, pp, v, K, rhat, 0, part);
+        k3_final<<<1, 256, 0, q>>>(part, nblk, K, FIN_ALPHA);
+        kd_s_dot<<<g, 256, 0, q>>>(n, K, r, v, sv, part);
+        k3_final<<<1, 256, 0, q>>>(part, nblk, K, FIN_S);
         kd_axpy_add<<<g, 256, 0, q>>>(n, K, pp, x);
         ks_added<<<1, 1, 0, q>>>(K);
-        k3_op<<<g, 256, 0, q>>>(o, sv, t, run);
-        dots_ks(t, t, t, sv);
-        ks_omega<<<1, 1, 0, q>>>(K);
+        k3_op_dot<<<g, 256, 0, q>>>(o, sv, t, K, sv, 1, part);
+        k3_final<<<1, 256, 0, q>>>(part, nblk, K, FIN_OMEGA);
         kd_axpy_add<<<g, 256, 0, q>>>(n, K, pp, x);
         ks_added<<<1, 1, 0, q>>>(K);
-        kd_xr<<<g, 256, 0, q>>>(n, K, pp, sv, t, x, r);
-        dots_ks(r, r, nullptr, nullptr);
-        ks_end<<<1, 1, 0, q>>>(K);
+        kd_xr_dot<<<g, 256, 0, q>>>(n, K, pp, sv, t, rhat, x, r, part);
+        k3_final<<<1, 256, 0, q>>>(part, nblk, K, FIN_END);
     };
     cudaGraphExec_t exec = nullptr;
     for (const auto& gr : b->graphs)
@@ -1070,7 +1099,7 @@ vip_status krylov(vip_3d* b, const Op3& o, const double* rhs, double* x, int32_t
     constexpr int CHUNK_MAX = 16;
     int32_t it = 0, restarts = 0;
     while (it < b->max_iters) {
-        apply(x, y, nullptr);
+        apply(x, y);
         k3_lin2<<<g, 256, 0, st>>>(n, 1.0, rhs, -1.0, y, r);
         V3_TRY(dots(b, n, r, r, nullptr, nullptr, d));
         if (!std::isfinite(d[0])) return fail(b, VIP_ERR_NONFINITE, "non-finite residual");
@@ -1085,6 +1114,7 @@ vip_status krylov(vip_3d* b, const Op3& o, const double* rhs, double* x, int32_t
         h.it = it;
         h.max_it = b->max_iters;
         h.state = KS_RUN;
+        h.d[0] = h.d[1] = d[0];       // r_hat . r and r . r, with r_hat = r
         V3_CUDA(cudaMemcpyAsync(K, &h, sizeof(KS), cudaMemcpyHostToDevice, st));
         V3_CUDA(cudaMemsetAsync(v, 0, n * sizeof(double), st));
         V3_CUDA(cudaMemsetAsync(pp, 0, n * sizeof(double), st));
@@ -1098,7 +1128,7 @@ vip_status krylov(vip_3d* b, const Op3& o, const double* rhs, double* x, int32_t
             if (h.state != KS_RUN) break;
         }
     }
-    apply(x, y, nullptr);
+    apply(x, y);
     k3_lin2<<<g, 256, 0, st>>>(n, 1.0, rhs, -1.0, y, r);
     V3_TRY(dots(b, n, r, r, nullptr, nullptr, d));
     *iters = it;
@@ -1479,7 +1509,7 @@ vip_status vip_3d_set_state(vip_3d* b, const double* u, const double* v, const d
         V3_CUDA(alloc(b->state_bufs, &b->p, N));
         V3_CUDA(alloc(b->state_bufs, &b->phi, N + 1));
         for (int k = 0; k < 8; ++k) V3_CUDA(alloc(b->state_bufs, &b->kv[k], N + 1));
-        V3_CUDA(alloc(b->state_bufs, &b->dpart, 2 * DOT_B));
+        V3_CUDA(alloc(b->state_bufs, &b->dpart, 2 * std::max<int64_t>(DOT_B, (N + 1 + 255) / 256)));
         V3_CUDA(alloc(b->state_bufs, &b->dres, 2));
         KS* ksp = nullptr;
         V3_CUDA(alloc(b->state_bufs, &ksp, 1));
